@@ -1,0 +1,190 @@
+/*
+ * iugkp.h -- C ABI of the GB300 (sm_103a) implementation of the implicit unified
+ * gas-kinetic particle (IUGKP) steady-state solver for the gray / band-resolved
+ * phonon BGK equation (Liu, Yang, Zhang, Ji, Xu, arXiv 2506.09465).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * - Every function returns iugkp_status; none aborts, throws or exits. On failure
+ *   iugkp_last_error(ctx) returns a message (valid until the next call on ctx).
+ * - Deviational temperature T (T_ref = 0, Sec. 2, Eq. "derivation final
+ *   equilibrium"): all temperatures, sources and tallies are linear in T.
+ * - Grids are uniform and structured on [0, lx] x [0, ly] x [0, lz]. Cells are
+ *   numbered x fastest: i = ix + nx (iy + ny iz). Unused axes have n = 1 and length 1,
+ *   so 1D quantities are per unit area and 2D ones per unit depth.
+ * - Faces: all x-faces first ((nx+1) ny nz of them, index fx + (nx+1)(iy + ny iz)),
+ *   then y-faces (nx (ny+1) nz), then z-faces (nx ny (nz+1)); a dimension's faces
+ *   exist only for axes < dim. Boundary faces are included.
+ * - Walls: 2*dim per instance in the order -x, +x, -y, +y, -z, +z.
+ * - A context holds n_inst >= 1 instances (same dim and band table, any sizes).
+ *   Per-cell device arrays are the instances' arrays concatenated; per-(band, cell)
+ *   arrays are [instance][band][cell]; faces and walls likewise per instance. Use
+ *   iugkp_get_layout() for the offsets.
+ * - Pointers named *_dev are caller-owned device memory (contiguous, FP64 unless
+ *   stated), read or written on the caller's stream `cuda_stream` (a cudaStream_t;
+ *   NULL = the legacy default stream). Host pointers are read during the call only.
+ *   Nothing retains a caller pointer after the call returns.
+ * - Thread safety: calls on one context must be serialised by the caller; distinct
+ *   contexts are independent.
+ */
+#ifndef IUGKP_H
+#define IUGKP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  IUGKP_OK = 0,
+  IUGKP_EINVAL = 1,   /* invalid argument (sizes, tau <= 0 or not finite, NULL, ...) */
+  IUGKP_ENOMEM = 2,   /* device or host allocation failed */
+  IUGKP_ECUDA = 3,    /* a CUDA runtime call failed (message has the CUDA error) */
+  IUGKP_ENOCONV = 4,  /* an iteration hit its limit before its tolerance */
+  IUGKP_EBUDGET = 5,  /* a particle exceeded the per-particle step budget (dropped) */
+  IUGKP_EDEVICE = 6   /* a device-side check failed (index out of range, bad state) */
+} iugkp_status;
+
+typedef struct iugkp_ctx iugkp_ctx; /* opaque; owned by the library */
+
+/* Uniform structured grid: dim in {1, 2, 3}; n >= 1 and l > 0 on used axes. */
+typedef struct {
+  int dim, nx, ny, nz;
+  double lx, ly, lz;
+} iugkp_grid;
+
+/* Band-branch table (host arrays of nb entries): volumetric specific heat C_b > 0
+ * and group speed v_b > 0. Gray = one band. (Sec. 2: energy density form; band sums
+ * of Eq. "derivation function".) */
+typedef struct {
+  int nb;
+  const double *C;
+  const double *v;
+} iugkp_bands;
+
+enum { IUGKP_TRACK_FP64 = 0, IUGKP_TRACK_FP32 = 1 };
+enum { IUGKP_TALLY_FP64 = 0, IUGKP_TALLY_STAGED = 1 };
+enum { IUGKP_DRAWS_FRESH = 0, IUGKP_DRAWS_FROZEN = 1 };
+enum { IUGKP_SCHED_PLAIN = 0, IUGKP_SCHED_PERSISTENT = 1 };
+
+typedef struct {
+  int precision;      /* IUGKP_TRACK_FP64: positions, directions and paths in FP64;
+                         IUGKP_TRACK_FP32: in FP32 (weights and tallies stay FP64). */
+  int tally;          /* IUGKP_TALLY_FP64: every face / deposit tally is a global FP64
+                         atomic; IUGKP_TALLY_STAGED: face tallies are accumulated per
+                         block in shared memory (FP32) and flushed to FP64. */
+  int draws;          /* IUGKP_DRAWS_FRESH: epoch = epoch0 + iteration;
+                         IUGKP_DRAWS_FROZEN: epoch = epoch0 every iteration. */
+  int newton;         /* 0: plain iteration; 1: inexact-Newton diffusion correction. */
+  int schedule;       /* IUGKP_SCHED_PLAIN: one thread per particle;
+                         IUGKP_SCHED_PERSISTENT: persistent warps that refill lanes. */
+  long long particles_per_cell;       /* N_cell >= nb; split over bands (largest remainder) */
+  long long particles_per_wall_face;  /* >= nb; split over bands by C_b v_b */
+  unsigned long long seed;            /* Philox key (low, high words) */
+  unsigned epoch0;                    /* first epoch (24 bits used) */
+  unsigned instance_base;             /* instance k of a batch draws with id base + k */
+  double cg_rtol;                     /* PCG relative tolerance (Newton step) */
+  int cg_maxit;                       /* PCG iteration cap -> IUGKP_ENOCONV */
+  long long step_budget;              /* max crossings + candidates per particle */
+  int block_threads;                  /* threads per block of the trace kernel (0 = auto) */
+  int blocks_per_sm;                  /* persistent blocks per SM (0 = auto) */
+} iugkp_options;
+
+/* Fills *o with defaults: FP32 tracking, staged tallies, frozen draws, Newton on,
+ * persistent schedule, 1024 particles per cell and per wall face, seed 0,
+ * cg_rtol 1e-10, cg_maxit 5000, step budget 2^24. */
+void iugkp_default_options(iugkp_options *o);
+
+/* Creates a context for one instance (Sec. 4 problem setup).
+ *   tau     host [nb][ncells], relaxation time per band and cell, finite and > 0;
+ *   wall_T  host [2*dim] deviational wall temperatures;
+ *   source  host [ncells] heat source power density, or NULL for none.
+ * Device memory for all internal fields is allocated here (cudaMalloc on the
+ * current device). EINVAL on bad input, ENOMEM / ECUDA on allocation failure. */
+iugkp_status iugkp_create(const iugkp_grid *g, const double *tau, const iugkp_bands *b,
+                          const double *wall_T, const double *source, const iugkp_options *o,
+                          iugkp_ctx **out);
+
+/* Creates one context holding n instances (same dim and bands); g[k], tau[k],
+ * wall_T[k], source[k] (source may be NULL or have NULL entries). Instance k uses
+ * Philox id instance_base + k, so it draws exactly what it would draw alone. */
+iugkp_status iugkp_create_batch(int n, const iugkp_grid *g, const double *const *tau,
+                                const iugkp_bands *b, const double *const *wall_T,
+                                const double *const *source, const iugkp_options *o,
+                                iugkp_ctx **out);
+
+void iugkp_destroy(iugkp_ctx *ctx);
+
+const char *iugkp_last_error(const iugkp_ctx *ctx);
+
+/* Sizes and offsets of the concatenated arrays. Each array argument may be NULL;
+ * *_off arrays have n_inst + 1 entries (prefix sums). */
+typedef struct {
+  int n_inst, dim, nb;
+  long long total_cells, total_faces, total_walls; /* walls = 2*dim per instance */
+  long long total_particles;                       /* per sweep, every emitter counted */
+} iugkp_layout;
+iugkp_status iugkp_get_layout(const iugkp_ctx *ctx, iugkp_layout *lay, long long *cell_off,
+                              long long *face_off);
+
+/* Replaces a field. which: IUGKP_FIELD_SOURCE ([total_cells] power density),
+ * IUGKP_FIELD_WALL_T ([total_walls]). `data` is host memory unless on_device != 0. */
+enum { IUGKP_FIELD_SOURCE = 0, IUGKP_FIELD_WALL_T = 1 };
+iugkp_status iugkp_set_field(iugkp_ctx *ctx, int which, const double *data, int on_device,
+                             void *cuda_stream);
+
+/* One sweep (Sec. 3.1 steps (1)-(3) with the null collisions of Sec. 3.2): every
+ * cell emits particles from its equilibrium at T_in_dev (+ source), every wall from
+ * its temperature; each particle is traced cell by cell through null candidates to a
+ * real collision or a wall. Outputs (overwritten; any may be NULL except R_dev):
+ *   R_dev        [inst][band][cell] real-collision power (the paper's W^h);
+ *   W_dev        [inst][band][cell] candidate estimator of energy (the paper's W);
+ *   F_dev        [total_faces] net power across each face in the +axis direction;
+ *   wall_dev     [total_walls] power absorbed by each wall;
+ *   counters_dev [6] u64: flights, candidates, real collisions, cell crossings,
+ *                wall exits, dropped (step budget).
+ * epoch selects the draws (24 bits). Asynchronous on cuda_stream except for the
+ * device-error check, which synchronises the stream (EBUDGET / EDEVICE). */
+iugkp_status iugkp_sweep(iugkp_ctx *ctx, const double *T_in_dev, unsigned epoch, double *R_dev,
+                         double *W_dev, double *F_dev, double *wall_dev,
+                         unsigned long long *counters_dev, void *cuda_stream);
+
+/* Macro update (Sec. 3.1 step (3)): T_half = sum_b R_b / (V sum_b C_b / tau_b) and,
+ * if T_E_dev != NULL and W_dev != NULL, T_E = sum_b W_b / (V sum_b C_b). */
+iugkp_status iugkp_macro(iugkp_ctx *ctx, const double *R_dev, const double *W_dev,
+                         double *T_half_dev, double *T_E_dev, void *cuda_stream);
+
+/* Inexact-Newton correction (Sec. 3.3): s = (sum_b R_b - sum_b C_b T_n V / tau_b) / V,
+ * solves -div(kappa grad dT) = s by Jacobi-preconditioned CG (FP64) and sets
+ * T_half += theta dT (theta = min(1, 1.5 / cell optical thickness)). Synchronises
+ * the stream to read the CG status; *cg_iters_out (may be NULL) gets the largest
+ * iteration count over instances. ENOCONV if cg_maxit is reached. */
+iugkp_status iugkp_newton_step(iugkp_ctx *ctx, const double *T_n_dev, double *T_half_inout_dev,
+                               const double *R_dev, void *cuda_stream, int *cg_iters_out);
+
+/* Steady driver: from the initial T_inout_dev, repeats sweep -> macro -> [Newton]
+ * until res = ||T^{n+1} - T^n|| / max(||T^{n+1}||, dT_ref sqrt(ncells)) <= tol over
+ * all instances (dT_ref = the wall-temperature span, or max |T_w|, or 1).
+ * Writes the final iterate to T_inout_dev; *iters_out, *res_out may be NULL.
+ * ENOCONV if max_iter is reached first. */
+iugkp_status iugkp_solve_steady(iugkp_ctx *ctx, double *T_inout_dev, double tol, int max_iter,
+                                int *iters_out, double *res_out, void *cuda_stream);
+
+/* Adjoint of the frozen-draw steady state (the sweep is linear, Sec. 2 Eq. "sum-g"):
+ * with J = sum_i g_i T*_i, solves lambda = A^T lambda + g by re-tracing every
+ * particle of epoch epoch0 and gathering lambda at its real-collision cell, with the
+ * transposed diffusion correction, to tolerance tol. Outputs:
+ *   grad_source_dev [total_cells] dJ/dQ_i (Q = source power density);
+ *   grad_wall_dev   [total_walls] dJ/dT_w;
+ *   lambda_dev      [total_cells] the adjoint solution (may be NULL).
+ * T_star_dev is accepted for interface symmetry and unused (the problem is linear). */
+iugkp_status iugkp_adjoint(iugkp_ctx *ctx, const double *T_star_dev, const double *g_dev,
+                           double tol, int max_iter, double *grad_source_dev,
+                           double *grad_wall_dev, double *lambda_dev, void *cuda_stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* IUGKP_H */

@@ -1,0 +1,768 @@
+// C ABI of the IUGKP CUDA library (declared in include/iugkp.h): context set-up
+// (geometry, band split, per-(band, cell) coefficients, diffusion stencil), and the
+// host loops of the steady and adjoint iterations (arXiv 2506.09465 Sec. 3-4).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <numeric>
+#include <string>
+#include <vector>
+
+#include "internal.h"
+
+using namespace iugkp;
+
+struct iugkp_ctx {
+  Ctx c;
+};
+
+namespace iugkp {
+
+static thread_local std::string g_create_error;
+
+iugkp_status fail(Ctx* c, iugkp_status s, const std::string& msg) {
+  if (c) c->err = msg;
+  else g_create_error = msg;
+  return s;
+}
+
+iugkp_status cuda_fail(Ctx* c, cudaError_t e, const char* what) {
+  std::string m = std::string(what) + ": " + cudaGetErrorName(e) + " (" + cudaGetErrorString(e) + ")";
+  return fail(c, IUGKP_ECUDA, m);
+}
+
+}  // namespace iugkp
+
+#define CK(call, what)                                         \
+  do {                                                         \
+    cudaError_t e_ = (call);                                   \
+    if (e_ != cudaSuccess) return cuda_fail(c, e_, what);      \
+  } while (0)
+
+namespace {
+
+// Largest-remainder split of N over weights r (r > 0, N >= nb): one particle per band
+// first, the remaining N - nb in proportion to r, leftovers to the largest fractional
+// parts (lower band first on ties).
+bool split_counts(long long N, const std::vector<double>& r, std::vector<long long>& out) {
+  const int nb = (int)r.size();
+  if (nb < 1 || N < nb) return false;
+  double rs = 0.0;
+  for (double x : r) {
+    if (!(x > 0.0) || !std::isfinite(x)) return false;
+    rs += x;
+  }
+  const long long rest = N - nb;
+  out.assign(nb, 1);
+  std::vector<double> frac(nb);
+  long long given = 0;
+  for (int b = 0; b < nb; ++b) {
+    double share = (double)rest * r[b] / rs;
+    long long whole = (long long)std::floor(share);
+    out[b] += whole;
+    frac[b] = share - (double)whole;
+    given += whole;
+  }
+  std::vector<int> order(nb);
+  std::iota(order.begin(), order.end(), 0);
+  std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return frac[x] > frac[y]; });
+  for (long long k = 0; k < rest - given; ++k) out[order[(size_t)(k % nb)]] += 1;
+  return true;
+}
+
+template <typename T>
+iugkp_status dalloc(Ctx* c, T** p, size_t count) {
+  *p = nullptr;
+  if (count == 0) count = 1;
+  cudaError_t e = cudaMalloc((void**)p, count * sizeof(T));
+  if (e != cudaSuccess) {
+    *p = nullptr;
+    cudaGetLastError();
+    return fail(c, e == cudaErrorMemoryAllocation ? IUGKP_ENOMEM : IUGKP_ECUDA,
+                std::string("cudaMalloc failed: ") + cudaGetErrorString(e));
+  }
+  return IUGKP_OK;
+}
+
+template <typename T>
+iugkp_status upload(Ctx* c, T** p, const std::vector<T>& h) {
+  iugkp_status s = dalloc(c, p, h.size());
+  if (s != IUGKP_OK) return s;
+  CK(cudaMemcpy(*p, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice), "upload");
+  return IUGKP_OK;
+}
+
+void free_all(Ctx* c) {
+  void* ptrs[] = {c->d_inst, c->d_groups_all, c->d_groups_fwd, c->d_coef, c->d_ratio64, c->d_ratio32, c->d_taumaj,
+                  c->d_v, c->d_wcoef, c->d_wallT, c->d_srcshift, c->d_source, c->d_m, c->d_Vm, c->d_invVm, c->d_VC,
+                  c->d_theta, c->d_theta_m, c->d_diag, c->d_cx, c->d_cy, c->d_cz, c->d_pcg, c->d_work, c->d_T2,
+                  c->d_R, c->d_W, c->d_F, c->d_wall, c->d_red, c->d_counters, c->d_work_counter, c->d_err,
+                  c->d_pcg_iters, c->d_scalar, c->d_adj};
+  for (void* p : ptrs)
+    if (p) cudaFree(p);
+  if (c->h_pinned) cudaFreeHost(c->h_pinned);
+}
+
+bool grid_ok(const iugkp_grid& g, int dim) {
+  if (g.dim != dim || dim < 1 || dim > 3) return false;
+  const int n[3] = {g.nx, g.ny, g.nz};
+  const double l[3] = {g.lx, g.ly, g.lz};
+  long long cells = 1;
+  for (int a = 0; a < dim; ++a) {
+    if (n[a] < 1 || !(l[a] > 0.0) || !std::isfinite(l[a])) return false;
+    cells *= n[a];
+  }
+  return cells < (1ll << 30);
+}
+
+// Emission temperature shift Q / m for every cell of every instance (or clears it).
+iugkp_status set_source(Ctx* c, const std::vector<double>& Q, const std::vector<double>& m) {
+  bool any = false;
+  for (double q : Q) any |= (q != 0.0);
+  if (!any) {
+    if (c->d_srcshift) cudaFree(c->d_srcshift);
+    c->d_srcshift = nullptr;
+    return IUGKP_OK;
+  }
+  std::vector<double> shift(Q.size());
+  for (size_t i = 0; i < Q.size(); ++i) shift[i] = Q[i] / m[i];
+  if (!c->d_srcshift) {
+    iugkp_status s = dalloc(c, &c->d_srcshift, shift.size());
+    if (s != IUGKP_OK) return s;
+  }
+  CK(cudaMemcpy(c->d_srcshift, shift.data(), shift.size() * sizeof(double), cudaMemcpyHostToDevice), "source");
+  return IUGKP_OK;
+}
+
+// Forward groups leave out walls at zero temperature (their particles weigh zero).
+iugkp_status rebuild_forward_groups(Ctx* c) {
+  c->h_groups_fwd.clear();
+  long long off = 0;
+  for (const Group& g0 : c->h_groups_all) {
+    if (g0.kind > 0) {
+      const InstDesc& in = c->h_inst[g0.inst];
+      if (c->h_wallT[in.wall_off + g0.kind - 1] == 0.0) continue;
+    }
+    Group g = g0;
+    g.first_particle = off;
+    off += (long long)g.n_emitters * g.per_emitter;
+    c->h_groups_fwd.push_back(g);
+  }
+  if (c->h_groups_fwd.empty()) {  // keep one (all-zero) group so kernels see a valid table
+    Group g = c->h_groups_all[0];
+    g.first_particle = 0;
+    c->h_groups_fwd.push_back(g);
+    off = 0;
+  }
+  c->fwd_particles = off;
+  if (c->d_groups_fwd) cudaFree(c->d_groups_fwd);
+  c->d_groups_fwd = nullptr;
+  return upload(c, &c->d_groups_fwd, c->h_groups_fwd);
+}
+
+}  // namespace
+
+extern "C" {
+
+void iugkp_default_options(iugkp_options* o) {
+  if (!o) return;
+  std::memset(o, 0, sizeof(*o));
+  o->precision = IUGKP_TRACK_FP32;
+  o->tally = IUGKP_TALLY_STAGED;
+  o->draws = IUGKP_DRAWS_FROZEN;
+  o->newton = 1;
+  o->schedule = IUGKP_SCHED_PERSISTENT;
+  o->particles_per_cell = 1024;
+  o->particles_per_wall_face = 1024;
+  o->seed = 0;
+  o->epoch0 = 0;
+  o->instance_base = 0;
+  o->cg_rtol = 1e-10;
+  o->cg_maxit = 5000;
+  o->step_budget = 1ll << 24;
+  o->block_threads = 0;
+  o->blocks_per_sm = 0;
+}
+
+const char* iugkp_last_error(const iugkp_ctx* ctx) {
+  return ctx ? ctx->c.err.c_str() : g_create_error.c_str();
+}
+
+iugkp_status iugkp_create_batch(int n, const iugkp_grid* g, const double* const* tau, const iugkp_bands* b,
+                                const double* const* wall_T, const double* const* source, const iugkp_options* o,
+                                iugkp_ctx** out) {
+  Ctx* c = nullptr;
+  if (!out) return fail(nullptr, IUGKP_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (n < 1 || !g || !tau || !b || !wall_T || !o) return fail(nullptr, IUGKP_EINVAL, "NULL argument or n < 1");
+  if (b->nb < 1 || b->nb > 255 || !b->C || !b->v) return fail(nullptr, IUGKP_EINVAL, "bands: need 1 <= nb <= 255");
+  for (int k = 0; k < b->nb; ++k)
+    if (!(b->C[k] > 0.0) || !(b->v[k] > 0.0) || !std::isfinite(b->C[k]) || !std::isfinite(b->v[k]))
+      return fail(nullptr, IUGKP_EINVAL, "bands: C and v must be finite and > 0");
+  const int dim = g[0].dim;
+  for (int k = 0; k < n; ++k)
+    if (!grid_ok(g[k], dim) || !tau[k] || !wall_T[k])
+      return fail(nullptr, IUGKP_EINVAL, "grid " + std::to_string(k) + " invalid (dim, sizes, lengths) or NULL field");
+  if (o->precision != IUGKP_TRACK_FP32 && o->precision != IUGKP_TRACK_FP64)
+    return fail(nullptr, IUGKP_EINVAL, "options.precision");
+  if (o->tally != IUGKP_TALLY_FP64 && o->tally != IUGKP_TALLY_STAGED) return fail(nullptr, IUGKP_EINVAL, "options.tally");
+  if (o->particles_per_cell < b->nb || o->particles_per_wall_face < b->nb || o->particles_per_cell > (1ll << 31) ||
+      o->particles_per_wall_face > (1ll << 31))
+    return fail(nullptr, IUGKP_EINVAL, "particles per cell / wall face must be in [nb, 2^31]");
+  if (!(o->cg_rtol > 0.0) || o->cg_maxit < 1 || o->step_budget < 1) return fail(nullptr, IUGKP_EINVAL, "cg / budget options");
+
+  iugkp_ctx* ctx = new (std::nothrow) iugkp_ctx();
+  if (!ctx) return fail(nullptr, IUGKP_ENOMEM, "host allocation failed");
+  c = &ctx->c;
+  c->opt = *o;
+  c->n_inst = n;
+  c->dim = dim;
+  c->nb = b->nb;
+  c->h_C.assign(b->C, b->C + b->nb);
+  c->h_v.assign(b->v, b->v + b->nb);
+  const int nb = b->nb;
+  auto bail = [&](iugkp_status s) {
+    g_create_error = c->err;
+    free_all(c);
+    delete ctx;
+    return s;
+  };
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+    cudaGetLastError();
+    fail(c, IUGKP_ECUDA, "no CUDA device");
+    return bail(IUGKP_ECUDA);
+  }
+  int optin = 0;
+  cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  c->smem_optin = (size_t)optin;
+
+  // Geometry and offsets.
+  long long cell_off = 0, face_off = 0;
+  for (int k = 0; k < n; ++k) {
+    InstDesc in;
+    std::memset(&in, 0, sizeof(in));
+    in.dim = dim;
+    const int nn[3] = {g[k].nx, g[k].ny, g[k].nz};
+    const double ll[3] = {g[k].lx, g[k].ly, g[k].lz};
+    for (int a = 0; a < 3; ++a) {
+      in.n[a] = a < dim ? nn[a] : 1;
+      in.h[a] = a < dim ? ll[a] / nn[a] : 1.0;
+    }
+    in.ncells = in.n[0] * in.n[1] * in.n[2];
+    in.V = in.h[0] * in.h[1] * in.h[2];
+    in.cell_off = cell_off;
+    in.bc_off = (long long)nb * cell_off;
+    in.face_off = face_off;
+    long long fo = 0;
+    for (int a = 0; a < 3; ++a) {
+      in.fax_off[a] = fo;
+      if (a < dim) {
+        long long m = 1;
+        for (int d = 0; d < 3; ++d) m *= (d == a) ? in.n[d] + 1 : in.n[d];
+        fo += m;
+      }
+    }
+    in.nfaces = fo;
+    in.wall_off = 2 * dim * k;
+    in.inst_id = o->instance_base + (unsigned)k;
+    c->h_inst.push_back(in);
+    cell_off += in.ncells;
+    face_off += fo;
+    c->max_inst_cells = std::max(c->max_inst_cells, in.ncells);
+    c->max_inst_faces = (int)std::max<long long>(c->max_inst_faces, fo);
+  }
+  c->total_cells = cell_off;
+  c->total_faces = face_off;
+  c->total_walls = 2LL * dim * n;
+
+  // Per (instance, band, cell) and per-cell coefficients.
+  std::vector<double> coef((size_t)nb * cell_off), r64((size_t)nb * cell_off), taumaj((size_t)n * nb);
+  std::vector<float> r32((size_t)nb * cell_off);
+  std::vector<double> m(cell_off, 0.0), Vm(cell_off), invVm(cell_off), VC(cell_off), kap(cell_off, 0.0);
+  std::vector<double> wcoef((size_t)n * nb * 6, 0.0), wallTv(c->total_walls), Qv(cell_off, 0.0);
+  std::vector<double> diag(cell_off, 0.0), cx(cell_off, 0.0), cy(cell_off, 0.0), cz(cell_off, 0.0), theta_m(cell_off);
+  double csum = 0.0, cvsum = 0.0;
+  for (int bb = 0; bb < nb; ++bb) {
+    csum += c->h_C[bb];
+    cvsum += c->h_C[bb] * c->h_v[bb];
+  }
+  std::vector<double> rwall(nb);
+  for (int bb = 0; bb < nb; ++bb) rwall[bb] = c->h_C[bb] * c->h_v[bb];
+  std::vector<long long> nwall;
+  if (!split_counts(o->particles_per_wall_face, rwall, nwall)) {
+    fail(c, IUGKP_EINVAL, "wall particle split");
+    return bail(IUGKP_EINVAL);
+  }
+  long long total_particles = 0;
+  for (int k = 0; k < n; ++k) {
+    const InstDesc& in = c->h_inst[k];
+    const long long nc = in.ncells;
+    std::vector<double> rb(nb, 0.0);
+    for (int bb = 0; bb < nb; ++bb) {
+      double tmin = INFINITY, inv_sum = 0.0;
+      for (long long i = 0; i < nc; ++i) {
+        const double t = tau[k][(size_t)bb * nc + i];
+        if (!(t > 0.0) || !std::isfinite(t)) {
+          fail(c, IUGKP_EINVAL, "tau must be finite and > 0 (instance " + std::to_string(k) + ")");
+          return bail(IUGKP_EINVAL);
+        }
+        tmin = std::min(tmin, t);
+        inv_sum += 1.0 / t;
+      }
+      taumaj[(size_t)k * nb + bb] = tmin;
+      rb[bb] = c->h_C[bb] * (inv_sum / (double)nc);
+    }
+    std::vector<long long> nband;
+    if (!split_counts(o->particles_per_cell, rb, nband)) {
+      fail(c, IUGKP_EINVAL, "band particle split");
+      return bail(IUGKP_EINVAL);
+    }
+    for (int bb = 0; bb < nb; ++bb) {
+      for (long long i = 0; i < nc; ++i) {
+        const size_t j = (size_t)in.bc_off + (size_t)bb * nc + i;
+        const double t = tau[k][(size_t)bb * nc + i];
+        coef[j] = c->h_C[bb] * in.V / (t * (double)nband[bb]);
+        r64[j] = taumaj[(size_t)k * nb + bb] / t;
+        r32[j] = (float)r64[j];
+        m[in.cell_off + i] += c->h_C[bb] / t;
+        kap[in.cell_off + i] += c->h_C[bb] * c->h_v[bb] * c->h_v[bb] * t / 3.0;
+      }
+      for (int w = 0; w < 2 * dim; ++w) {
+        const int a = w >> 1;
+        const double A = (a == 0 ? in.h[1] * in.h[2] : (a == 1 ? in.h[0] * in.h[2] : in.h[0] * in.h[1]));
+        wcoef[((size_t)k * nb + bb) * 6 + w] = c->h_C[bb] * c->h_v[bb] * A / (4.0 * (double)nwall[bb]);
+      }
+    }
+    for (int w = 0; w < 2 * dim; ++w) {
+      const double tw = wall_T[k][w];
+      if (!std::isfinite(tw)) {
+        fail(c, IUGKP_EINVAL, "wall temperature not finite");
+        return bail(IUGKP_EINVAL);
+      }
+      wallTv[in.wall_off + w] = tw;
+    }
+    if (source && source[k]) {
+      for (long long i = 0; i < nc; ++i) {
+        if (!std::isfinite(source[k][i])) {
+          fail(c, IUGKP_EINVAL, "source not finite");
+          return bail(IUGKP_EINVAL);
+        }
+        Qv[in.cell_off + i] = source[k][i];
+      }
+    }
+    // Cell sums and the diffusion stencil (Sec. 3.3): face kappa harmonic; walls take
+    // the half-cell conduction in series with the vacuum condition (flux = cv/2 dT).
+    double hmin = in.h[0];
+    for (int a = 1; a < dim; ++a) hmin = std::min(hmin, in.h[a]);
+    double tmax = 0.0;
+    const long long sx = 1, sy = in.n[0], sz = (long long)in.n[0] * in.n[1];
+    const long long strides[3] = {sx, sy, sz};
+    for (long long i = 0; i < nc; ++i) {
+      const long long gi = in.cell_off + i;
+      Vm[gi] = in.V * m[gi];
+      invVm[gi] = 1.0 / Vm[gi];
+      VC[gi] = in.V * csum;
+      tmax = std::max(tmax, hmin / std::sqrt(3.0 * kap[gi] / m[gi]));
+      const int idx[3] = {(int)(i % in.n[0]), (int)((i / in.n[0]) % in.n[1]), (int)(i / sz)};
+      double d = 0.0;
+      for (int a = 0; a < dim; ++a) {
+        const double hh = in.h[a] * in.h[a];
+        for (int side = -1; side <= 1; side += 2) {
+          const int j = idx[a] + side;
+          if (j < 0 || j >= in.n[a]) {
+            const double G = 1.0 / (in.h[a] / (2.0 * kap[gi]) + 2.0 / cvsum);
+            d += G / in.h[a];
+          } else {
+            const long long gn = gi + side * strides[a];
+            const double kf = 2.0 * kap[gi] * kap[gn] / (kap[gi] + kap[gn]);
+            d += kf / hh;
+            if (side > 0) (a == 0 ? cx : (a == 1 ? cy : cz))[gi] = kf / hh;
+          }
+        }
+      }
+      diag[gi] = d;
+    }
+    const double theta = std::min(1.0, 1.5 / tmax);
+    c->h_theta.push_back(theta);
+    for (long long i = 0; i < nc; ++i) theta_m[in.cell_off + i] = theta * m[in.cell_off + i];
+    // Emitter groups: thermal per band, then each wall per band.
+    for (int bb = 0; bb < nb; ++bb) {
+      Group gr;
+      std::memset(&gr, 0, sizeof(gr));
+      gr.first_particle = total_particles;
+      gr.inst = k;
+      gr.band = bb;
+      gr.kind = 0;
+      gr.n_emitters = in.ncells;
+      gr.per_emitter = (int)nband[bb];
+      total_particles += (long long)gr.n_emitters * gr.per_emitter;
+      c->h_groups_all.push_back(gr);
+    }
+    for (int bb = 0; bb < nb; ++bb) {
+      for (int w = 0; w < 2 * dim; ++w) {
+        const int a = w >> 1;
+        Group gr;
+        std::memset(&gr, 0, sizeof(gr));
+        gr.first_particle = total_particles;
+        gr.inst = k;
+        gr.band = bb;
+        gr.kind = 1 + w;
+        gr.n_emitters = in.n[(a + 1) % 3] * in.n[(a + 2) % 3];
+        gr.per_emitter = (int)nwall[bb];
+        total_particles += (long long)gr.n_emitters * gr.per_emitter;
+        c->h_groups_all.push_back(gr);
+      }
+    }
+    c->h_nband.insert(c->h_nband.end(), nband.begin(), nband.end());
+  }
+  c->h_nwall = nwall;
+  c->total_particles = total_particles;
+  c->h_wallT = wallTv;
+
+  iugkp_status s;
+#define UP(ptr, vec)                                 \
+  if ((s = upload(c, &(ptr), (vec))) != IUGKP_OK) return bail(s);
+  UP(c->d_inst, c->h_inst);
+  UP(c->d_groups_all, c->h_groups_all);
+  UP(c->d_coef, coef);
+  UP(c->d_ratio64, r64);
+  UP(c->d_ratio32, r32);
+  UP(c->d_taumaj, taumaj);
+  UP(c->d_v, c->h_v);
+  UP(c->d_wcoef, wcoef);
+  UP(c->d_wallT, wallTv);
+  UP(c->d_m, m);
+  UP(c->d_Vm, Vm);
+  UP(c->d_invVm, invVm);
+  UP(c->d_VC, VC);
+  UP(c->d_theta, c->h_theta);
+  UP(c->d_theta_m, theta_m);
+  UP(c->d_diag, diag);
+  UP(c->d_cx, cx);
+  UP(c->d_cy, cy);
+  UP(c->d_cz, cz);
+#undef UP
+  if ((s = dalloc(c, &c->d_source, cell_off)) != IUGKP_OK) return bail(s);
+  if (cudaMemcpy(c->d_source, Qv.data(), Qv.size() * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess) {
+    fail(c, IUGKP_ECUDA, "source upload");
+    return bail(IUGKP_ECUDA);
+  }
+  if ((s = set_source(c, Qv, m)) != IUGKP_OK) return bail(s);
+  if ((s = rebuild_forward_groups(c)) != IUGKP_OK) return bail(s);
+  if ((s = dalloc(c, &c->d_pcg, 4 * (size_t)cell_off)) != IUGKP_OK) return bail(s);
+  if ((s = dalloc(c, &c->d_work, cell_off)) != IUGKP_OK) return bail(s);
+  if ((s = dalloc(c, &c->d_T2, cell_off)) != IUGKP_OK) return bail(s);
+  if ((s = dalloc(c, &c->d_R, (size_t)nb * cell_off)) != IUGKP_OK) return bail(s);
+  if ((s = dalloc(c, &c->d_W, (size_t)nb * cell_off)) != IUGKP_OK) return bail(s);
+  if ((s = dalloc(c, &c->d_F, face_off)) != IUGKP_OK) return bail(s);
+  if ((s = dalloc(c, &c->d_wall, c->total_walls)) != IUGKP_OK) return bail(s);
+  if ((s = dalloc(c, &c->d_red, 1024)) != IUGKP_OK) return bail(s);
+  if ((s = dalloc(c, &c->d_counters, CNT_N)) != IUGKP_OK) return bail(s);
+  if ((s = dalloc(c, &c->d_work_counter, 4)) != IUGKP_OK) return bail(s);
+  if ((s = dalloc(c, &c->d_err, 1)) != IUGKP_OK) return bail(s);
+  if ((s = dalloc(c, &c->d_pcg_iters, n)) != IUGKP_OK) return bail(s);
+  if ((s = dalloc(c, &c->d_scalar, 16)) != IUGKP_OK) return bail(s);
+  if (cudaMemset(c->d_err, 0, sizeof(int)) != cudaSuccess ||
+      cudaMallocHost((void**)&c->h_pinned, sizeof(double) * (16 + (size_t)n)) != cudaSuccess) {
+    cudaGetLastError();
+    fail(c, IUGKP_ECUDA, "set-up of error word / pinned buffer");
+    return bail(IUGKP_ECUDA);
+  }
+  *out = ctx;
+  return IUGKP_OK;
+}
+
+iugkp_status iugkp_create(const iugkp_grid* g, const double* tau, const iugkp_bands* b, const double* wall_T,
+                          const double* source, const iugkp_options* o, iugkp_ctx** out) {
+  const double* taus[1] = {tau};
+  const double* walls[1] = {wall_T};
+  const double* srcs[1] = {source};
+  return iugkp_create_batch(1, g, taus, b, walls, srcs, o, out);
+}
+
+void iugkp_destroy(iugkp_ctx* ctx) {
+  if (!ctx) return;
+  free_all(&ctx->c);
+  delete ctx;
+}
+
+iugkp_status iugkp_get_layout(const iugkp_ctx* ctx, iugkp_layout* lay, long long* cell_off, long long* face_off) {
+  if (!ctx) return IUGKP_EINVAL;
+  const Ctx* c = &ctx->c;
+  if (lay) {
+    lay->n_inst = c->n_inst;
+    lay->dim = c->dim;
+    lay->nb = c->nb;
+    lay->total_cells = c->total_cells;
+    lay->total_faces = c->total_faces;
+    lay->total_walls = c->total_walls;
+    lay->total_particles = c->total_particles;
+  }
+  for (int k = 0; k <= c->n_inst; ++k) {
+    if (cell_off) cell_off[k] = k < c->n_inst ? c->h_inst[k].cell_off : c->total_cells;
+    if (face_off) face_off[k] = k < c->n_inst ? c->h_inst[k].face_off : c->total_faces;
+  }
+  return IUGKP_OK;
+}
+
+}  // extern "C"
+
+namespace {
+
+SweepArgs base_args(Ctx* c) {
+  SweepArgs a;
+  std::memset(&a, 0, sizeof(a));
+  a.inst = c->d_inst;
+  a.nb = c->nb;
+  a.srcshift = c->d_srcshift;
+  a.coef = c->d_coef;
+  a.ratio64 = c->d_ratio64;
+  a.ratio32 = c->d_ratio32;
+  a.taumaj = c->d_taumaj;
+  a.v = c->d_v;
+  a.wcoef = c->d_wcoef;
+  a.wallT = c->d_wallT;
+  a.seed = c->opt.seed;
+  a.budget = c->opt.step_budget;
+  a.err = c->d_err;
+  a.work_counter = c->d_work_counter;
+  a.dim = c->dim;
+  a.invVm = c->d_invVm;
+  return a;
+}
+
+// Reads and clears the device error word (synchronises the stream).
+iugkp_status check_device(Ctx* c, cudaStream_t s) {
+  int* h = reinterpret_cast<int*>(c->h_pinned + 15);
+  CK(cudaMemcpyAsync(h, c->d_err, sizeof(int), cudaMemcpyDeviceToHost, s), "error readback");
+  CK(cudaStreamSynchronize(s), "stream synchronise");
+  int e = *h;
+  if (e) {
+    CK(cudaMemsetAsync(c->d_err, 0, sizeof(int), s), "error reset");
+    if (e & ERR_BUDGET) return fail(c, IUGKP_EBUDGET, "a particle exceeded the step budget and was dropped");
+    return fail(c, IUGKP_EDEVICE, "device-side check failed (code " + std::to_string(e) + ")");
+  }
+  return IUGKP_OK;
+}
+
+iugkp_status sweep_async(Ctx* c, const double* T, unsigned epoch, double* R, double* W, double* F, double* wall,
+                         unsigned long long* counters, cudaStream_t s) {
+  const size_t bc = (size_t)c->nb * c->total_cells;
+  CK(cudaMemsetAsync(R, 0, bc * sizeof(double), s), "clear R");
+  if (W) CK(cudaMemsetAsync(W, 0, bc * sizeof(double), s), "clear W");
+  if (F) CK(cudaMemsetAsync(F, 0, c->total_faces * sizeof(double), s), "clear F");
+  if (wall) CK(cudaMemsetAsync(wall, 0, c->total_walls * sizeof(double), s), "clear wall");
+  unsigned long long* cnt = counters ? counters : c->d_counters;
+  CK(cudaMemsetAsync(cnt, 0, CNT_N * sizeof(unsigned long long), s), "clear counters");
+  CK(cudaMemsetAsync(c->d_work_counter, 0, sizeof(unsigned long long), s), "clear work counter");
+  SweepArgs a = base_args(c);
+  a.groups = c->d_groups_fwd;
+  a.n_groups = (int)c->h_groups_fwd.size();
+  a.total_particles = c->fwd_particles;
+  a.T = T;
+  a.R = R;
+  a.W = W;
+  a.F = F;
+  a.wall = wall;
+  a.counters = cnt;
+  a.epoch = epoch;
+  CK(launch_sweep(c, a, s), "sweep launch");
+  return IUGKP_OK;
+}
+
+double dT_ref_of(const Ctx* c) {
+  double lo = INFINITY, hi = -INFINITY, amax = 0.0;
+  for (double t : c->h_wallT) {
+    lo = std::min(lo, t);
+    hi = std::max(hi, t);
+    amax = std::max(amax, std::fabs(t));
+  }
+  if (hi - lo > 0.0) return hi - lo;
+  return amax;
+}
+
+// Residual between two iterates (synchronises): ||T1 - T0|| / max(||T1||, ref sqrt(N)).
+iugkp_status residual(Ctx* c, const double* T0, const double* T1, double ref, cudaStream_t s, double* res) {
+  CK(launch_residual(c, T0, T1, ref, c->d_scalar, s), "residual");
+  CK(cudaMemcpyAsync(c->h_pinned, c->d_scalar, 2 * sizeof(double), cudaMemcpyDeviceToHost, s), "residual readback");
+  CK(cudaStreamSynchronize(s), "residual sync");
+  const double num = std::sqrt(c->h_pinned[0]);
+  const double den = std::max(std::sqrt(c->h_pinned[1]), ref * std::sqrt((double)c->total_cells));
+  *res = den > 0.0 ? num / den : (num > 0.0 ? INFINITY : 0.0);
+  return IUGKP_OK;
+}
+
+iugkp_status pcg_status(Ctx* c, cudaStream_t s, int* iters) {
+  int* h = reinterpret_cast<int*>(c->h_pinned + 16);
+  CK(cudaMemcpyAsync(h, c->d_pcg_iters, c->n_inst * sizeof(int), cudaMemcpyDeviceToHost, s), "pcg readback");
+  CK(cudaStreamSynchronize(s), "pcg sync");
+  int worst = 0;
+  bool fail_ = false;
+  for (int k = 0; k < c->n_inst; ++k) {
+    if (h[k] < 0) fail_ = true;
+    worst = std::max(worst, h[k] < 0 ? c->opt.cg_maxit : h[k]);
+  }
+  if (iters) *iters = worst;
+  if (fail_) return fail(c, IUGKP_ENOCONV, "PCG reached cg_maxit before cg_rtol");
+  return IUGKP_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+iugkp_status iugkp_set_field(iugkp_ctx* ctx, int which, const double* data, int on_device, void* cuda_stream) {
+  if (!ctx || !data) return IUGKP_EINVAL;
+  Ctx* c = &ctx->c;
+  cudaStream_t s = (cudaStream_t)cuda_stream;
+  size_t count = which == IUGKP_FIELD_SOURCE ? (size_t)c->total_cells
+                 : which == IUGKP_FIELD_WALL_T ? (size_t)c->total_walls : 0;
+  if (!count) return fail(c, IUGKP_EINVAL, "unknown field");
+  std::vector<double> h(count);
+  if (on_device) {
+    CK(cudaMemcpyAsync(h.data(), data, count * sizeof(double), cudaMemcpyDeviceToHost, s), "field readback");
+    CK(cudaStreamSynchronize(s), "field sync");
+  } else {
+    std::copy(data, data + count, h.begin());
+  }
+  for (double x : h)
+    if (!std::isfinite(x)) return fail(c, IUGKP_EINVAL, "field values must be finite");
+  CK(cudaStreamSynchronize(s), "field sync");
+  if (which == IUGKP_FIELD_SOURCE) {
+    CK(cudaMemcpy(c->d_source, h.data(), count * sizeof(double), cudaMemcpyHostToDevice), "source upload");
+    std::vector<double> m(count);
+    CK(cudaMemcpy(m.data(), c->d_m, count * sizeof(double), cudaMemcpyDeviceToHost), "m readback");
+    return set_source(c, h, m);
+  }
+  c->h_wallT = h;
+  CK(cudaMemcpy(c->d_wallT, h.data(), count * sizeof(double), cudaMemcpyHostToDevice), "wall upload");
+  return rebuild_forward_groups(c);
+}
+
+iugkp_status iugkp_sweep(iugkp_ctx* ctx, const double* T_in_dev, unsigned epoch, double* R_dev, double* W_dev,
+                         double* F_dev, double* wall_dev, unsigned long long* counters_dev, void* cuda_stream) {
+  if (!ctx) return IUGKP_EINVAL;
+  Ctx* c = &ctx->c;
+  if (!T_in_dev || !R_dev) return fail(c, IUGKP_EINVAL, "T_in_dev and R_dev are required");
+  cudaStream_t s = (cudaStream_t)cuda_stream;
+  iugkp_status st = sweep_async(c, T_in_dev, epoch, R_dev, W_dev, F_dev, wall_dev, counters_dev, s);
+  if (st != IUGKP_OK) return st;
+  return check_device(c, s);
+}
+
+iugkp_status iugkp_macro(iugkp_ctx* ctx, const double* R_dev, const double* W_dev, double* T_half_dev,
+                         double* T_E_dev, void* cuda_stream) {
+  if (!ctx) return IUGKP_EINVAL;
+  Ctx* c = &ctx->c;
+  if (!R_dev || !T_half_dev) return fail(c, IUGKP_EINVAL, "R_dev and T_half_dev are required");
+  CK(launch_macro(c, R_dev, W_dev, T_half_dev, T_E_dev, (cudaStream_t)cuda_stream), "macro");
+  return IUGKP_OK;
+}
+
+iugkp_status iugkp_newton_step(iugkp_ctx* ctx, const double* T_n_dev, double* T_half_inout_dev, const double* R_dev,
+                               void* cuda_stream, int* cg_iters_out) {
+  if (!ctx) return IUGKP_EINVAL;
+  Ctx* c = &ctx->c;
+  if (!T_n_dev || !T_half_inout_dev || !R_dev) return fail(c, IUGKP_EINVAL, "NULL device pointer");
+  cudaStream_t s = (cudaStream_t)cuda_stream;
+  CK(launch_newton(c, T_n_dev, T_half_inout_dev, R_dev, s), "newton");
+  return pcg_status(c, s, cg_iters_out);
+}
+
+iugkp_status iugkp_solve_steady(iugkp_ctx* ctx, double* T_inout_dev, double tol, int max_iter, int* iters_out,
+                                double* res_out, void* cuda_stream) {
+  if (!ctx) return IUGKP_EINVAL;
+  Ctx* c = &ctx->c;
+  if (!T_inout_dev || max_iter < 1 || !(tol >= 0.0)) return fail(c, IUGKP_EINVAL, "bad argument");
+  cudaStream_t s = (cudaStream_t)cuda_stream;
+  const double ref = dT_ref_of(c);
+  double* cur = T_inout_dev;
+  double* nxt = c->d_T2;
+  double res = INFINITY;
+  int it = 0;
+  iugkp_status st;
+  while (it < max_iter) {
+    const unsigned epoch = c->opt.draws == IUGKP_DRAWS_FROZEN ? c->opt.epoch0 : c->opt.epoch0 + (unsigned)it;
+    if ((st = sweep_async(c, cur, epoch, c->d_R, c->d_W, c->d_F, c->d_wall, c->d_counters, s)) != IUGKP_OK) return st;
+    CK(launch_macro(c, c->d_R, nullptr, nxt, nullptr, s), "macro");
+    if (c->opt.newton) {
+      CK(launch_newton(c, cur, nxt, c->d_R, s), "newton");
+      if ((st = pcg_status(c, s, nullptr)) != IUGKP_OK) return st;
+    }
+    if ((st = residual(c, cur, nxt, ref, s, &res)) != IUGKP_OK) return st;
+    std::swap(cur, nxt);
+    ++it;
+    if (res <= tol) break;
+  }
+  if (cur != T_inout_dev) CK(cudaMemcpyAsync(T_inout_dev, cur, c->total_cells * sizeof(double), cudaMemcpyDeviceToDevice, s), "copy result");
+  if ((st = check_device(c, s)) != IUGKP_OK) return st;
+  if (iters_out) *iters_out = it;
+  if (res_out) *res_out = res;
+  if (!(res <= tol)) return fail(c, IUGKP_ENOCONV, "max_iter reached before tol");
+  return IUGKP_OK;
+}
+
+iugkp_status iugkp_adjoint(iugkp_ctx* ctx, const double* T_star_dev, const double* g_dev, double tol, int max_iter,
+                           double* grad_source_dev, double* grad_wall_dev, double* lambda_dev, void* cuda_stream) {
+  (void)T_star_dev;
+  if (!ctx) return IUGKP_EINVAL;
+  Ctx* c = &ctx->c;
+  if (!g_dev || !grad_source_dev || !grad_wall_dev || max_iter < 1) return fail(c, IUGKP_EINVAL, "bad argument");
+  cudaStream_t s = (cudaStream_t)cuda_stream;
+  iugkp_status st;
+  if (!c->d_adj) {
+    if ((st = dalloc(c, &c->d_adj, 4 * (size_t)c->total_cells)) != IUGKP_OK) return st;
+  }
+  const size_t nc = (size_t)c->total_cells;
+  double* at = c->d_adj;
+  double* half = at + nc;
+  double* lam = lambda_dev ? lambda_dev : half + nc;
+  double* nxt = half + 2 * nc;
+  CK(cudaMemsetAsync(lam, 0, nc * sizeof(double), s), "clear lambda");
+  // |g| max as the residual floor.
+  std::vector<double> hg(nc);
+  CK(cudaMemcpyAsync(hg.data(), g_dev, nc * sizeof(double), cudaMemcpyDeviceToHost, s), "g readback");
+  CK(cudaStreamSynchronize(s), "g sync");
+  double gmax = 0.0;
+  for (double x : hg) gmax = std::max(gmax, std::fabs(x));
+  SweepArgs a = base_args(c);
+  a.groups = c->d_groups_all;
+  a.n_groups = (int)c->h_groups_all.size();
+  a.total_particles = c->total_particles;
+  a.epoch = c->opt.epoch0;
+  a.adj_out = at;
+  a.adj_wall = grad_wall_dev;
+  double res = INFINITY;
+  int it = 0;
+  while (it < max_iter) {
+    a.lambda = lam;
+    CK(cudaMemsetAsync(at, 0, nc * sizeof(double), s), "clear");
+    CK(cudaMemsetAsync(grad_wall_dev, 0, c->total_walls * sizeof(double), s), "clear");
+    CK(launch_adjoint(c, a, s), "adjoint sweep");
+    CK(launch_axpy_grad(c, at, g_dev, half, s), "adjoint axpy");
+    if (c->opt.newton) {
+      CK(launch_adjoint_correction(c, lam, half, nxt, s), "adjoint correction");
+      if ((st = pcg_status(c, s, nullptr)) != IUGKP_OK) return st;
+    } else {
+      CK(cudaMemcpyAsync(nxt, half, nc * sizeof(double), cudaMemcpyDeviceToDevice, s), "copy");
+    }
+    if ((st = residual(c, lam, nxt, gmax, s, &res)) != IUGKP_OK) return st;
+    CK(cudaMemcpyAsync(lam, nxt, nc * sizeof(double), cudaMemcpyDeviceToDevice, s), "copy lambda");
+    ++it;
+    if (res <= tol) break;
+  }
+  // Gradients at the converged lambda: dJ/dQ = (A^T lambda) / m, dJ/dT_w = B_w^T lambda.
+  a.lambda = lam;
+  CK(cudaMemsetAsync(at, 0, nc * sizeof(double), s), "clear");
+  CK(cudaMemsetAsync(grad_wall_dev, 0, c->total_walls * sizeof(double), s), "clear");
+  CK(launch_adjoint(c, a, s), "adjoint sweep");
+  CK(launch_grad_source(c, at, grad_source_dev, s), "grad source");
+  if ((st = check_device(c, s)) != IUGKP_OK) return st;
+  if (!(res <= tol)) return fail(c, IUGKP_ENOCONV, "adjoint: max_iter reached before tol");
+  return IUGKP_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,123 @@
+// Host-side context of the CUDA library and the launchers shared between its
+// translation units. Not part of the public ABI (include/iugkp.h is).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/iugkp.h"
+#include "layout.h"
+
+namespace iugkp {
+
+// Arguments of the forward and adjoint sweep kernels (all device pointers).
+struct SweepArgs {
+  const InstDesc* inst;
+  const Group* groups;
+  int n_groups;
+  int nb;
+  long long total_particles;
+  const double* T;         // [cells] temperature (forward)
+  const double* srcshift;  // [cells] Q / m, or null
+  const double* coef;      // [bc] C_b V / (tau N_b): weight per unit emission temperature
+  const double* ratio64;   // [bc] tau_maj / tau (acceptance probability of a candidate)
+  const float* ratio32;
+  const double* taumaj;    // [inst * nb] majorant tau per instance and band
+  const double* v;         // [nb] group speed
+  const double* wcoef;     // [inst * nb * 6] C_b v_b A / (4 N_w) per wall
+  const double* wallT;     // [walls]
+  double* R;
+  double* W;
+  double* F;
+  double* wall;
+  unsigned long long* counters;
+  const double* lambda;    // adjoint: [cells]
+  const double* invVm;     // adjoint: [cells] 1 / (V m)
+  double* adj_out;         // adjoint: [cells] (A^T lambda)
+  double* adj_wall;        // adjoint: [walls]
+  unsigned long long seed;
+  unsigned epoch;
+  long long budget;
+  int* err;
+  unsigned long long* work_counter;  // persistent schedule: next particle index
+  int staged_faces;                  // staged schedule: faces held in shared memory (0 = none)
+  int dim;
+};
+
+struct Ctx {
+  std::string err;
+  iugkp_options opt;
+  int n_inst = 0, dim = 0, nb = 0;
+  long long total_cells = 0, total_faces = 0, total_walls = 0, total_particles = 0;
+  int max_inst_faces = 0, max_inst_cells = 0;
+  std::vector<InstDesc> h_inst;
+  std::vector<Group> h_groups_all;  // every emitter (adjoint)
+  std::vector<Group> h_groups_fwd;  // walls at T_w = 0 left out (forward)
+  long long fwd_particles = 0;
+  std::vector<double> h_wallT;      // [walls]
+  std::vector<double> h_C, h_v;
+  std::vector<long long> h_nband, h_nwall;
+  std::vector<double> h_theta;      // per instance damping of the Newton correction
+  std::vector<double> h_Vcell;      // per instance cell volume
+
+  // device buffers
+  InstDesc* d_inst = nullptr;
+  Group* d_groups_all = nullptr;
+  Group* d_groups_fwd = nullptr;
+  double* d_coef = nullptr;
+  double* d_ratio64 = nullptr;
+  float* d_ratio32 = nullptr;
+  double* d_taumaj = nullptr;
+  double* d_v = nullptr;
+  double* d_wcoef = nullptr;
+  double* d_wallT = nullptr;
+  double* d_srcshift = nullptr;  // null when no source
+  double* d_source = nullptr;    // Q (kept for set_field)
+  double* d_m = nullptr;         // [cells] sum_b C_b / tau_b
+  double* d_Vm = nullptr;        // [cells] V m
+  double* d_invVm = nullptr;     // [cells] 1 / (V m)
+  double* d_VC = nullptr;        // [cells] V sum_b C_b
+  double* d_theta = nullptr;     // [n_inst] damping of the Newton correction
+  double* d_theta_m = nullptr;   // [cells] theta_k m_i (adjoint correction)
+  double* d_diag = nullptr;      // [cells] diffusion operator diagonal
+  double* d_cx = nullptr;        // [cells] coupling to the +x neighbour (0 at the row end)
+  double* d_cy = nullptr;
+  double* d_cz = nullptr;
+  double* d_pcg = nullptr;       // [4 * cells] x, r, p, q
+  double* d_work = nullptr;      // [cells] scratch
+  double* d_T2 = nullptr;        // [cells] scratch iterate
+  double* d_R = nullptr;         // [nb * cells]
+  double* d_W = nullptr;
+  double* d_F = nullptr;
+  double* d_wall = nullptr;
+  double* d_red = nullptr;       // reduction scratch
+  unsigned long long* d_counters = nullptr;
+  unsigned long long* d_work_counter = nullptr;
+  int* d_err = nullptr;
+  int* d_pcg_iters = nullptr;    // [n_inst]
+  double* d_scalar = nullptr;    // [8] small results
+  double* d_adj = nullptr;       // [4 * cells] adjoint iteration buffers (allocated on first use)
+  double* h_pinned = nullptr;    // [8 + n_inst] host readback
+  int sm_count = 0;
+  size_t smem_optin = 0;
+};
+
+// Status helpers
+iugkp_status fail(Ctx* c, iugkp_status s, const std::string& msg);
+iugkp_status cuda_fail(Ctx* c, cudaError_t e, const char* what);
+
+// Launchers (return the cudaError_t of the launch)
+cudaError_t launch_sweep(const Ctx* c, const SweepArgs& a, cudaStream_t s);
+cudaError_t launch_adjoint(const Ctx* c, const SweepArgs& a, cudaStream_t s);
+cudaError_t launch_macro(const Ctx* c, const double* R, const double* W, double* T_half, double* T_E, cudaStream_t s);
+cudaError_t launch_newton(const Ctx* c, const double* T_n, double* T_half, const double* R, cudaStream_t s);
+cudaError_t launch_adjoint_correction(const Ctx* c, const double* lam, const double* half, double* out,
+                                      cudaStream_t s);
+cudaError_t launch_residual(const Ctx* c, const double* T0, const double* T1, double dT_ref, double* out_dev,
+                            cudaStream_t s);
+cudaError_t launch_axpy_grad(const Ctx* c, const double* at, const double* g, double* lam_half, cudaStream_t s);
+cudaError_t launch_grad_source(const Ctx* c, const double* at, double* grad, cudaStream_t s);
+
+}  // namespace iugkp

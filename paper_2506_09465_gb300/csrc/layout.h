@@ -1,0 +1,42 @@
+// Plain-data descriptors shared by host and device code of the CUDA library.
+#pragma once
+
+#include <cstdint>
+
+namespace iugkp {
+
+// One instance (geometry and offsets into the concatenated arrays). Device-resident.
+struct InstDesc {
+  int dim;
+  int n[3];           // cells per axis (unused axes: 1)
+  int ncells;
+  int pad0;
+  double h[3];        // cell size per axis (unused axes: 1)
+  double V;           // cell volume (per unit area / depth in 1D / 2D)
+  long long cell_off; // offset into per-cell arrays
+  long long bc_off;   // offset into [band][cell] arrays (= nb * cell_off)
+  long long face_off; // offset into per-face arrays
+  long long fax_off[3];  // start of each axis's faces within the instance
+  long long nfaces;
+  int wall_off;       // offset into per-wall arrays (= 2 * dim * k)
+  uint32_t inst_id;   // Philox instance id
+};
+
+// A run of emitters sharing (instance, band, kind). kind 0 = the instance's cells;
+// kind 1 + w = the boundary faces of wall w. Particles of the run are numbered
+// emitter-major: local = e * per_emitter + q.
+struct Group {
+  long long first_particle;
+  int inst, band, kind;
+  int n_emitters;
+  int per_emitter;
+  int pad0;
+};
+
+// Counter slots (u64) written by a sweep.
+enum { CNT_FLIGHTS = 0, CNT_CANDIDATES, CNT_REAL, CNT_CROSSINGS, CNT_WALL_EXITS, CNT_DROPPED, CNT_N };
+
+// Device error bits.
+enum { ERR_BUDGET = 1, ERR_RANGE = 2, ERR_PCG = 4, ERR_WAIT = 8 };
+
+}  // namespace iugkp

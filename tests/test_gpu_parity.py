@@ -1,0 +1,212 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle on identical
+seeded inputs and identical Philox draws.
+
+Tolerances: FP64 tracking must match every tally to 1e-10 (normwise: max |gpu - oracle| /
+max |oracle|, per array); event counters are integers and must be equal. FP32 tracking
+draws the same uniforms but walks in single precision: its steady temperature must match
+the oracle's within 5e-4 of the wall-temperature span.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from oracle import oracle as O  # noqa: E402
+from paper_2506_09465_gb300 import workloads as WL  # noqa: E402
+from gpu_helpers import gpu_solver, normwise_close, oracle_problem  # noqa: E402
+
+RTOL64 = 1e-10
+
+
+def cuda_T(x):
+    return torch.as_tensor(np.asarray(x, dtype=np.float64), device="cuda")
+
+
+def cases():
+    rng = np.random.default_rng(2024)
+    out = []
+    out.append(("1d_gray", [WL.random_instance(rng, 1, (37,), 1)], [1.0], [1.0]))
+    out.append(("1d_nullcoll", [WL.Instance(1, (24,), (1.0,), np.where(np.arange(24) < 12, 10.0, 0.1)[None, :],
+                                             np.array([1.0, -1.0]))], [1.0], [1.0]))
+    out.append(("2d_gray_var", [WL.random_instance(rng, 2, (19, 13), 1, (0.02, 0.6))], [1.0], [1.0]))
+    out.append(("2d_3band_src", [WL.random_instance(rng, 2, (11, 9), 3, (0.05, 2.0), source=True)],
+                [0.5, 1.0, 1.5], [1.0, 0.7, 0.3]))
+    out.append(("3d_gray", [WL.random_instance(rng, 3, (6, 5, 7), 1, (0.05, 0.5), source=True)], [1.0], [1.0]))
+    return out
+
+
+@pytest.mark.parametrize("name,insts,C,v", cases(), ids=[c[0] for c in cases()])
+def test_sweep_fp64_matches_oracle(orc, name, insts, C, v):
+    inst = insts[0]
+    N, Nw = 60, 40
+    rng = np.random.default_rng(7)
+    T = rng.uniform(-0.5, 1.0, size=inst.ncells)
+    p = oracle_problem(inst, C, v, N, Nw, seed=11)
+    s = gpu_solver(inst, C, v, N, Nw, precision=0, tally=0, schedule=0, seed=11)
+    assert s.layout.total_particles == int(p.n_band.sum()) * inst.ncells + int(p.n_wall_band.sum()) * sum(
+        int(np.prod([inst.n[b] for b in range(inst.dim) if b != a])) * 2 for a in range(inst.dim))
+    for epoch in (0, 5):
+        r = orc.sweep(p, T, epoch)
+        g = s.sweep(cuda_T(T), epoch)
+        for key, ora in (("R", r.R), ("W", r.W), ("F", r.F), ("wall", r.wall)):
+            ok, err = normwise_close(g[key].cpu().numpy(), ora, RTOL64)
+            assert ok, (key, err)
+        assert g["counters"].cpu().numpy().tolist() == r.counters.astype(np.int64).tolist()
+
+
+@pytest.mark.parametrize("dim", [1, 2, 3])
+def test_sweep_fp32_tracks_same_particles(orc, dim):
+    rng = np.random.default_rng(30 + dim)
+    n = {1: (40,), 2: (16, 12), 3: (6, 6, 5)}[dim]
+    inst = WL.random_instance(rng, dim, n, 1, (0.05, 0.8))
+    N = 80
+    T = rng.uniform(0.0, 1.0, size=inst.ncells)
+    p = oracle_problem(inst, [1.0], [1.0], N, N, seed=3)
+    r = orc.sweep(p, T, 0)
+    s = gpu_solver(inst, [1.0], [1.0], N, N, precision=1, tally=0, schedule=0, seed=3)
+    g = s.sweep(cuda_T(T), 0)
+    # Same draws; single-precision walks change a particle's cell only when it stops
+    # within ~1e-7 of a face, so tallies agree to well below the statistical noise.
+    for key, ora in (("R", r.R), ("F", r.F), ("wall", r.wall)):
+        ok, err = normwise_close(g[key].cpu().numpy(), ora, 2e-3)
+        assert ok, (key, err)
+    c_g = g["counters"].cpu().numpy().astype(float)
+    c_o = r.counters.astype(float)
+    assert np.all(np.abs(c_g - c_o) <= 1e-3 * c_o + 2)
+
+
+def test_macro_matches_oracle(orc):
+    rng = np.random.default_rng(5)
+    inst = WL.random_instance(rng, 2, (9, 7), 2, (0.1, 1.0))
+    C, v = [0.7, 1.3], [1.0, 0.5]
+    p = oracle_problem(inst, C, v, 30, 30)
+    r = orc.sweep(p, rng.uniform(0, 1, inst.ncells), 0)
+    Th, TE = orc.macro(p, r.R, r.W)
+    s = gpu_solver(inst, C, v, 30, 30, precision=0)
+    gTh, gTE = s.macro(cuda_T(r.R.ravel()), cuda_T(r.W.ravel()))
+    assert np.allclose(gTh.cpu().numpy(), Th, rtol=1e-14, atol=0)
+    assert np.allclose(gTE.cpu().numpy(), TE, rtol=1e-14, atol=0)
+
+
+@pytest.mark.parametrize("dim", [1, 2, 3])
+def test_newton_step_matches_direct_solve(orc, dim):
+    rng = np.random.default_rng(40 + dim)
+    n = {1: (30,), 2: (14, 11), 3: (6, 5, 4)}[dim]
+    inst = WL.random_instance(rng, dim, n, 2, (0.01, 0.4))
+    C, v = [1.0, 0.5], [1.0, 1.5]
+    p = oracle_problem(inst, C, v, 40, 40)
+    T = rng.uniform(0, 1, inst.ncells)
+    r = orc.sweep(p, T, 0)
+    Th, _ = orc.macro(p, r.R, r.W)
+    T1, dT = orc.newton(p, T, Th, r.R)
+    s = gpu_solver(inst, C, v, 40, 40, precision=0, cg_rtol=1e-14, cg_maxit=20000)
+    gT = cuda_T(Th)
+    it = s.newton_step(cuda_T(T), gT, cuda_T(r.R.ravel()))
+    assert it > 0
+    ok, err = normwise_close(gT.cpu().numpy() - Th, T1 - Th, 1e-9)
+    assert ok, err
+
+
+@pytest.mark.parametrize("newton", [0, 1])
+def test_steady_fp64_matches_oracle(orc, newton):
+    inst = WL.slab(40, 0.1, 1.0, -1.0).instances[0]
+    N = 200
+    p = oracle_problem(inst, [1.0], [1.0], N, N, seed=1)
+    T_o, it_o, res_o, _ = orc.solve_steady(p, np.zeros(40), 1e-12, 3000, frozen=True, newton=bool(newton), dT_ref=2.0)
+    s = gpu_solver(inst, [1.0], [1.0], N, N, precision=0, tally=0, schedule=0, seed=1, newton=newton,
+                   cg_rtol=1e-14, cg_maxit=20000)
+    T_g, it_g, res_g = s.solve_steady(None, 1e-12, 3000)
+    assert res_o <= 1e-12 and res_g <= 1e-12
+    ok, err = normwise_close(T_g.cpu().numpy(), T_o, 1e-9)
+    assert ok, err
+    assert abs(it_g - it_o) <= 2
+
+
+def test_steady_fp32_within_5e4_of_span(orc):
+    # FP32 tracking, frozen draws: steady T within 5e-4 of dT (the accuracy target).
+    inst = WL.cavity(24, 0.1).instances[0]
+    N = 256
+    p = oracle_problem(inst, [1.0], [1.0], N, N, seed=2)
+    T_o, _, res_o, _ = orc.solve_steady(p, np.zeros(inst.ncells), 1e-9, 500, frozen=True, newton=True, dT_ref=1.0)
+    for tally in (0, 1):
+        s = gpu_solver(inst, [1.0], [1.0], N, N, precision=1, tally=tally, seed=2)
+        T_g, it, res = s.solve_steady(None, 1e-9, 500)
+        assert np.abs(T_g.cpu().numpy() - T_o).max() <= 5e-4, tally
+
+
+def test_batch_equals_standalone(orc):
+    rng = np.random.default_rng(77)
+    insts = [WL.random_instance(rng, 2, n, 1, (0.05, 0.5), source=(k % 2 == 0), L=(1.0, 1.0))
+             for k, n in enumerate([(8, 8), (13, 5), (20, 17)])]
+    N = 50
+    Ts = [rng.uniform(0, 1, i.ncells) for i in insts]
+    sb = gpu_solver(insts, [1.0], [1.0], N, N, precision=0, tally=0, instance_base=4, seed=9)
+    gb = sb.sweep(cuda_T(np.concatenate(Ts)), 3)
+    Rb = gb["R"].cpu().numpy()
+    for k, inst in enumerate(insts):
+        s1 = gpu_solver(inst, [1.0], [1.0], N, N, precision=0, tally=0, instance_base=4 + k, seed=9)
+        g1 = s1.sweep(cuda_T(Ts[k]), 3)
+        co = sb.cell_off
+        ok, err = normwise_close(Rb[co[k]:co[k + 1]], g1["R"].cpu().numpy(), 1e-12)
+        assert ok, (k, err)
+        # and the oracle agrees with the standalone instance
+        p = oracle_problem(inst, [1.0], [1.0], N, N, seed=9, instance=4 + k)
+        ok, err = normwise_close(g1["R"].cpu().numpy(), orc.sweep(p, Ts[k], 3).R, RTOL64)
+        assert ok, err
+
+
+def test_adjoint_matches_dense_transpose(orc):
+    rng = np.random.default_rng(8)
+    inst = WL.random_instance(rng, 2, (6, 5), 1, (0.1, 0.8), source=True)
+    N = 40
+    p = oracle_problem(inst, [1.0], [1.0], N, N, seed=4)
+    g = np.zeros(inst.ncells)
+    g[[7, 8, 13, 14]] = 0.25
+    gQ, gW, lam, A, Bw = orc.adjoint_dense(p, g)
+    s = gpu_solver(inst, [1.0], [1.0], N, N, precision=0, tally=0, seed=4, cg_rtol=1e-14, cg_maxit=20000)
+    gs, gw, gl = s.adjoint(cuda_T(g), tol=1e-13, max_iter=500)
+    for got, ref in ((gl, lam), (gs, gQ), (gw, gW)):
+        ok, err = normwise_close(got.cpu().numpy(), ref, 1e-9)
+        assert ok, err
+
+
+def test_full_size_cavity_sampled_emitters(orc):
+    # The 128 x 128 cavity at the bench's particle count and launch configuration, with only
+    # a few cells hot (so the oracle traces only their particles): FP64 tallies agree.
+    inst = WL.cavity(128, 1.0).instances[0]
+    inst.wall_T = np.zeros(4)
+    T = np.zeros(inst.ncells)
+    T[[0, 5000, 8256, 16383]] = [1.0, 0.5, -0.25, 2.0]
+    N = 1024
+    p = oracle_problem(inst, [1.0], [1.0], N, N, seed=0)
+    r = orc.sweep(p, T, 0)
+    s = gpu_solver(inst, [1.0], [1.0], N, N, precision=0, tally=0, schedule=0, seed=0)
+    g = s.sweep(cuda_T(T), 0)
+    for key, ora in (("R", r.R), ("W", r.W), ("F", r.F), ("wall", r.wall)):
+        ok, err = normwise_close(g[key].cpu().numpy(), ora, RTOL64)
+        assert ok, (key, err)
+
+
+def test_full_size_conservation_every_mode():
+    # Any size, any mode: the net inflow from the face tallies equals absorbed minus emitted
+    # power in every cell, and walls balance globally.
+    inst = WL.cavity(128, 0.1).instances[0]
+    rng = np.random.default_rng(3)
+    T = rng.uniform(0, 1, inst.ncells)
+    for prec, tally, sched in ((0, 0, 0), (1, 0, 0), (1, 1, 1)):
+        s = gpu_solver(inst, [1.0], [1.0], 1024, 1024, precision=prec, tally=tally, schedule=sched)
+        g = s.sweep(cuda_T(T), 0)
+        F = g["F"].cpu().numpy()
+        R = g["R"].cpu().numpy()
+        n = 128
+        Fx = F[: (n + 1) * n].reshape(n, n + 1)
+        Fy = F[(n + 1) * n:].reshape(n + 1, n)
+        inflow = (Fx[:, :-1] - Fx[:, 1:] + Fy[:-1, :] - Fy[1:, :]).ravel()
+        V = 1.0 / n ** 2
+        emitted = T * V / 0.1
+        scale = np.abs(emitted).max()
+        tol = 1e-9 if tally == 0 else 1e-4
+        assert np.abs(inflow - (R - emitted)).max() <= tol * scale * 50, (prec, tally)
+        wall_em = 1.0 / 4.0 * 1.0
+        assert abs((g["wall"].cpu().numpy().sum() - wall_em) - (emitted.sum() - R.sum())) <= 1e-6 * emitted.sum()
