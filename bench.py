@@ -1,0 +1,382 @@
+"""Benchmark of the IUGKP hot path on GB300: cell-crossings/s of one full iteration (sweep +
+macro update + inexact-Newton correction + residual) and time to steady state (residual 1e-8),
+against the plain FP64 sweep on the same GPU, with the FP64 CPU oracle as the CPU baseline.
+
+Workload: 2D gray square cavity, 128 x 128 cells on the unit square, C = |v| = 1, top wall
+T = 1, other walls 0, Kn in {0.01, 0.1, 1, 10} as four instances of one batched context,
+1024 particles per cell (2^24 per instance per iteration) and 1024 per wall face, FP32
+tracking with FP64 tallies, frozen draws, Newton correction with CG.
+
+python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "cell-crossings/s and time-to-steady (res 1e-8) vs plain FP64 sweep, same GPU"
+KNS = (0.01, 0.1, 1.0, 10.0)
+NGRID = 128
+NPART = 1024
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-steady", action="store_true", help="skip the time-to-steady runs")
+    ap.add_argument("--no-plain", action="store_true", help="skip the plain FP64 baseline")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle (baseline leg and --impl reference)
+# ---------------------------------------------------------------------------
+
+def oracle_rate(n_particles: int, budget_s: float):
+    """Oracle sweeps over the four Kn instances with n_particles per cell and per wall face
+    until budget_s is spent; returns (crossings/s, seconds, crossings, sample text)."""
+    import numpy as np
+    from oracle import oracle as O
+    from paper_2506_09465_gb300 import workloads as WL
+    wl = WL.cavity_sweep(NGRID, KNS, NPART)
+    t0 = time.perf_counter()
+    crossings = 0
+    sweeps = 0
+    while True:
+        for inst in wl.instances:
+            p = O.Problem(2, inst.n, inst.L, wl.C, wl.v, inst.tau, inst.wall_T, np.array([n_particles]),
+                          np.array([n_particles]), seed=0)
+            T = np.full(inst.ncells, 0.3)
+            r = O.sweep(p, T, sweeps)
+            crossings += int(r.counters[3])
+            sweeps += 1
+            if time.perf_counter() - t0 > budget_s:
+                dt = time.perf_counter() - t0
+                sample = (f"{sweeps} oracle sweeps of the 128x128 cavity (Kn cycling {list(KNS)}, T = 0.3, "
+                          f"top wall 1) at {n_particles} particles per cell and wall face "
+                          f"({NPART // n_particles}x fewer than the GPU run)")
+                return crossings / dt, dt, crossings, sample
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    from oracle import oracle as O
+    O.build()
+    n_part = 16
+    times = []
+    total_cross = 0
+    sample = ""
+    for k in range(args.warmup + args.steps):
+        rate, dt, cr, sample = oracle_rate(n_part, 1.0)
+        if k >= args.warmup:
+            times.append(dt)
+            total_cross += cr
+    value = total_cross / sum(times)
+    line = {"metric": METRIC, "value": value, "unit": "cell-crossings/s", "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * sum(times) / len(times), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "impl": "reference",
+            "config": {"workload": "2D gray cavity 128x128, Kn {0.01,0.1,1,10}, top wall T=1 (oracle sample)",
+                       "particles_per_cell": n_part},
+            "cpu_baseline": {"value": value, "unit": "cell-crossings/s", "cores": 1, "kind": "oracle",
+                             "sample": sample + "; one step = about 1 s of oracle sweeps"},
+            "e2e": {"value": value, "unit": "cell-crossings/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+# ---------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------
+
+class ClockSampler:
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_bench_{os.getpid()}.csv")
+
+    def __enter__(self):
+        os.makedirs(os.path.dirname(self.path), exist_ok=True)
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f,
+                                         stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            self.f.close()
+
+    def summary(self):
+        if self.proc is None or not os.path.exists(self.path):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[5:9]):
+                if val.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def make_solver(wl, **opt):
+    from paper_2506_09465_gb300.solver import GridSpec, Solver
+    grids = [GridSpec(i.dim, i.n, i.L) for i in wl.instances]
+    return Solver(grids, [i.tau for i in wl.instances], wl.C, wl.v, [i.wall_T for i in wl.instances],
+                  [i.source for i in wl.instances], particles_per_cell=wl.particles_per_cell,
+                  particles_per_wall_face=wl.particles_per_wall_face, **opt)
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    rank, world, local = dist_env()
+    if world > 1:
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    from paper_2506_09465_gb300 import build as B
+    B.build()
+    from paper_2506_09465_gb300 import _lib as L
+    from paper_2506_09465_gb300 import workloads as WL
+
+    lib = L.load()
+    wl = WL.cavity_sweep(NGRID, KNS, NPART)
+    # Each rank runs an independent replica of the batch (different Philox instance ids).
+    solver = make_solver(wl, seed=0, instance_base=rank * len(KNS))
+    stream = torch.cuda.current_stream()
+    sp = stream.cuda_stream
+    nc = solver.total_cells
+    dev = torch.device("cuda", local)
+    # A realistic mid-iteration temperature field: the steady state of one frozen solve
+    # is not needed; T = 0.3 in every cell plus the hot wall exercises every emitter.
+    T = torch.full((nc,), 0.3, dtype=torch.float64, device=dev)
+    T_half = torch.empty_like(T)
+    R = torch.empty(solver.nb * nc, dtype=torch.float64, device=dev)
+    W = torch.empty_like(R)
+    F = torch.empty(solver.total_faces, dtype=torch.float64, device=dev)
+    wall = torch.empty(solver.total_walls, dtype=torch.float64, device=dev)
+    cnt = torch.zeros(6, dtype=torch.int64, device=dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # 256 MB > L2 (129 MB)
+    res_buf = torch.empty(2, dtype=torch.float64, device=dev)
+
+    def step(Tin, Tout, epoch=0):
+        """One full iteration: sweep (R, W, F, wall) -> macro -> Newton -> residual."""
+        L.check(lib.iugkp_sweep(solver.ctx, Tin.data_ptr(), epoch, R.data_ptr(), W.data_ptr(), F.data_ptr(),
+                                wall.data_ptr(), cnt.data_ptr(), sp), solver.ctx)
+        L.check(lib.iugkp_macro(solver.ctx, R.data_ptr(), None, Tout.data_ptr(), None, sp), solver.ctx)
+        import ctypes
+        it = ctypes.c_int(0)
+        L.check(lib.iugkp_newton_step(solver.ctx, Tin.data_ptr(), Tout.data_ptr(), R.data_ptr(), sp,
+                                      ctypes.byref(it)), solver.ctx)
+        L.check(lib.iugkp_residual(solver.ctx, Tin.data_ptr(), Tout.data_ptr(), res_buf.data_ptr(), sp), solver.ctx)
+        return it.value
+
+    for _ in range(args.warmup):
+        step(T, T_half)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    per_step_ms = []
+    crossings = 0
+    flights = 0
+    sweep_ms = []
+    with ClockSampler(local) as clk:
+        for k in range(args.steps):
+            flush.zero_()
+            ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            ev0.record(stream)
+            step(T, T_half)
+            ev1.record(stream)
+            torch.cuda.synchronize()
+            per_step_ms.append(ev0.elapsed_time(ev1))
+            c = cnt.cpu().numpy()
+            crossings += int(c[3])
+            flights += int(c[0])
+        # sweep kernel alone (the dominant kernel), timed on the launching stream
+        for k in range(max(3, args.steps // 2)):
+            flush.zero_()
+            ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            ev0.record(stream)
+            L.check(lib.iugkp_sweep(solver.ctx, T.data_ptr(), 0, R.data_ptr(), W.data_ptr(), F.data_ptr(),
+                                    wall.data_ptr(), cnt.data_ptr(), sp), solver.ctx)
+            ev1.record(stream)
+            torch.cuda.synchronize()
+            sweep_ms.append(ev0.elapsed_time(ev1))
+    sweep_counts = cnt.cpu().numpy().astype(np.int64)
+    t_local = sum(per_step_ms) / 1e3
+    t_max = t_local
+    if world > 1:
+        tt = torch.tensor([t_local], device=dev, dtype=torch.float64)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_max = float(tt.item())
+        cc = torch.tensor([crossings], device=dev, dtype=torch.float64)
+        dist.all_reduce(cc)
+        crossings_all = float(cc.item())
+    else:
+        crossings_all = float(crossings)
+    value = crossings_all / t_max
+    ms_per_step = 1e3 * t_max / args.steps
+
+    # End-to-end through the public API with host buffers: copy T in (pinned), one
+    # iteration, copy T_{n+1} out, every step.
+    T_host = torch.full((nc,), 0.3, dtype=torch.float64).pin_memory()
+    T_out_host = torch.empty((nc,), dtype=torch.float64).pin_memory()
+    T_dev = torch.empty_like(T)
+    e2e_ms = []
+    e2e_cross = 0
+    for k in range(max(3, args.steps // 2)):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        T_dev.copy_(T_host, non_blocking=True)
+        step(T_dev, T_half)
+        T_out_host.copy_(T_half, non_blocking=True)
+        torch.cuda.synchronize()
+        e2e_ms.append(1e3 * (time.perf_counter() - t0))
+        e2e_cross += int(cnt[3].item())
+    e2e_value = e2e_cross / (sum(e2e_ms) / 1e3)
+
+    out = {}
+    if rank == 0:
+        # Time to steady state (res 1e-8, frozen draws, Newton): batched FP32 fast path.
+        steady = {}
+        if not args.no_steady:
+            s2 = make_solver(wl, seed=0)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            Ts, its, res = s2.solve_steady(None, 1e-8, 400, raise_on_noconv=False)
+            torch.cuda.synchronize()
+            steady["fast_batched_s"] = time.perf_counter() - t0
+            steady["fast_batched_iters"] = its
+            steady["fast_batched_res"] = res
+            del s2
+        plain = {}
+        if not args.no_plain:
+            # Plain FP64: FP64 walk, global FP64 atomics, one thread per particle, one
+            # instance at a time, no graph.
+            ptot_cross, ptot_ms, psteady, piters = 0, 0.0, 0.0, []
+            for kn in KNS:
+                w1 = WL.cavity(NGRID, kn, NPART)
+                sp1 = make_solver(w1, seed=0, precision=0, tally=0, schedule=0)
+                T1 = torch.full((sp1.total_cells,), 0.3, dtype=torch.float64, device=dev)
+                R1 = torch.empty(sp1.total_cells, dtype=torch.float64, device=dev)
+                F1 = torch.empty(sp1.total_faces, dtype=torch.float64, device=dev)
+                W1 = torch.empty_like(R1)
+                wall1 = torch.empty(sp1.total_walls, dtype=torch.float64, device=dev)
+                for rep in range(2):
+                    flush.zero_()
+                    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    ev0.record(stream)
+                    L.check(lib.iugkp_sweep(sp1.ctx, T1.data_ptr(), 0, R1.data_ptr(), W1.data_ptr(), F1.data_ptr(),
+                                            wall1.data_ptr(), cnt.data_ptr(), sp), sp1.ctx)
+                    ev1.record(stream)
+                    torch.cuda.synchronize()
+                    if rep == 1:
+                        ptot_ms += ev0.elapsed_time(ev1)
+                        ptot_cross += int(cnt[3].item())
+                if not args.no_steady:
+                    torch.cuda.synchronize()
+                    t0 = time.perf_counter()
+                    _, its, _ = sp1.solve_steady(None, 1e-8, 400, raise_on_noconv=False)
+                    torch.cuda.synchronize()
+                    psteady += time.perf_counter() - t0
+                    piters.append(its)
+                del sp1
+            plain = {"sweep_crossings_per_s": ptot_cross / (ptot_ms / 1e3),
+                     "steady_s_sequential": psteady if not args.no_steady else None, "steady_iters": piters}
+        cpu = None
+        if not args.no_cpu:
+            rate, dt, cr, sample = oracle_rate(64, 12.0)
+            cpu = {"value": rate, "unit": "cell-crossings/s", "cores": 1, "kind": "oracle", "sample": sample}
+        clocks = clk.summary()
+        # Roofline of the dominant kernel (the sweep): ALU issue bound. Algorithmic
+        # lane-operations per event x events / kernel time.
+        OPS_CROSS, OPS_CAND, OPS_FLIGHT = 14, 60, 180
+        sw_s = statistics.median(sweep_ms) / 1e3
+        ops = (OPS_CROSS * sweep_counts[3] + OPS_CAND * sweep_counts[1] + OPS_FLIGHT * sweep_counts[0])
+        peak_ops = 152 * 128 * 2.07e9  # FP32/INT32 lanes x max SM clock
+        achieved = ops / sw_s
+        out = {
+            "metric": METRIC, "value": value, "unit": "cell-crossings/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "2D gray cavity 128x128 unit square, Kn {0.01,0.1,1,10} batched (4 instances), "
+                                   "top wall T=1, 1024 particles/cell (2^24 per instance) + 1024 per wall face; "
+                                   "one step = sweep + macro + Newton(CG) + residual",
+                       "tracking": "fp32", "tallies": "fp64", "draws": "frozen",
+                       "l2": "flushed between timed steps (256 MB write)",
+                       "parallelism": f"replicas x{world}" if world > 1 else "1 GPU"},
+            "flights_per_step": int(flights / args.steps), "crossings_per_step": int(crossings / args.steps),
+            "sweep_ms": statistics.median(sweep_ms),
+            "time_to_steady": steady,
+            "plain_fp64": plain,
+            "speedup_vs_plain_fp64_sweep": (sweep_counts[3] / sw_s) / plain["sweep_crossings_per_s"] if plain else None,
+            "e2e": {"value": e2e_value, "unit": "cell-crossings/s", "h2d_bytes_per_step": nc * 8,
+                    "d2h_bytes_per_step": nc * 8},
+            "gpu_launches": args.steps * 7,
+            "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": peak_ops / 1e12,
+                         "unit": "Tops/s (FP32+INT32 lane ops)", "frac": achieved / peak_ops, "traffic": None,
+                         "kernel": "sweep", "peak_source": "152 SMs x 128 lanes x 2.07 GHz (unit counts and clock)"},
+            "cpu_baseline": cpu,
+            "clocks": clocks,
+        }
+        print(json.dumps(out))
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -164,6 +164,12 @@ iugkp_status iugkp_macro(iugkp_ctx *ctx, const double *R_dev, const double *W_de
 iugkp_status iugkp_newton_step(iugkp_ctx *ctx, const double *T_n_dev, double *T_half_inout_dev,
                                const double *R_dev, void *cuda_stream, int *cg_iters_out);
 
+/* Convergence measure of one iteration (residual definition used by the steady driver):
+ * out_dev[0] = sum_i (T1_i - T0_i)^2 and out_dev[1] = sum_i T1_i^2 over all cells of all
+ * instances, in a fixed reduction order (deterministic). Asynchronous. */
+iugkp_status iugkp_residual(iugkp_ctx *ctx, const double *T0_dev, const double *T1_dev, double *out_dev,
+                            void *cuda_stream);
+
 /* Steady driver: from the initial T_inout_dev, repeats sweep -> macro -> [Newton]
  * until res = ||T^{n+1} - T^n|| / max(||T^{n+1}||, dT_ref sqrt(ncells)) <= tol over
  * all instances (dT_ref = the wall-temperature span, or max |T_w|, or 1).

@@ -58,6 +58,7 @@ SIGNATURES = {
     "iugkp_sweep": (_i, [_vp, _vp, _u, _vp, _vp, _vp, _vp, _vp, _vp]),
     "iugkp_macro": (_i, [_vp, _vp, _vp, _vp, _vp, _vp]),
     "iugkp_newton_step": (_i, [_vp, _vp, _vp, _vp, _vp, ctypes.POINTER(_i)]),
+    "iugkp_residual": (_i, [_vp, _vp, _vp, _vp, _vp]),
     "iugkp_solve_steady": (_i, [_vp, _vp, _d, _i, ctypes.POINTER(_i), ctypes.POINTER(_d), _vp]),
     "iugkp_adjoint": (_i, [_vp, _vp, _vp, _d, _i, _vp, _vp, _vp, _vp]),
 }

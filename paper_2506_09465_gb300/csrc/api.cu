@@ -99,7 +99,8 @@ void free_all(Ctx* c) {
                   c->d_v, c->d_wcoef, c->d_wallT, c->d_srcshift, c->d_source, c->d_m, c->d_Vm, c->d_invVm, c->d_VC,
                   c->d_theta, c->d_theta_m, c->d_diag, c->d_cx, c->d_cy, c->d_cz, c->d_pcg, c->d_work, c->d_T2,
                   c->d_R, c->d_W, c->d_F, c->d_wall, c->d_red, c->d_counters, c->d_work_counter, c->d_err,
-                  c->d_pcg_iters, c->d_scalar, c->d_adj};
+                  c->d_pcg_iters, c->d_scalar, c->d_adj, c->d_mg, c->d_mg_diag, c->d_mg_dinv, c->d_mg_cx,
+                  c->d_mg_cy, c->d_mg_cz, c->d_mg_cinv, c->d_mg_b, c->d_mg_x, c->d_mg_t, c->d_mg_r};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (c->h_pinned) cudaFreeHost(c->h_pinned);
@@ -452,7 +453,8 @@ iugkp_status iugkp_create_batch(int n, const iugkp_grid* g, const double* const*
   }
   if ((s = set_source(c, Qv, m)) != IUGKP_OK) return bail(s);
   if ((s = rebuild_forward_groups(c)) != IUGKP_OK) return bail(s);
-  if ((s = dalloc(c, &c->d_pcg, 4 * (size_t)cell_off)) != IUGKP_OK) return bail(s);
+  if ((s = dalloc(c, &c->d_pcg, 5 * (size_t)cell_off)) != IUGKP_OK) return bail(s);
+  if ((s = build_multigrid(c, diag, cx, cy, cz)) != IUGKP_OK) return bail(s);
   if ((s = dalloc(c, &c->d_work, cell_off)) != IUGKP_OK) return bail(s);
   if ((s = dalloc(c, &c->d_T2, cell_off)) != IUGKP_OK) return bail(s);
   if ((s = dalloc(c, &c->d_R, (size_t)nb * cell_off)) != IUGKP_OK) return bail(s);
@@ -670,6 +672,15 @@ iugkp_status iugkp_newton_step(iugkp_ctx* ctx, const double* T_n_dev, double* T_
   cudaStream_t s = (cudaStream_t)cuda_stream;
   CK(launch_newton(c, T_n_dev, T_half_inout_dev, R_dev, s), "newton");
   return pcg_status(c, s, cg_iters_out);
+}
+
+iugkp_status iugkp_residual(iugkp_ctx* ctx, const double* T0_dev, const double* T1_dev, double* out_dev,
+                            void* cuda_stream) {
+  if (!ctx) return IUGKP_EINVAL;
+  Ctx* c = &ctx->c;
+  if (!T0_dev || !T1_dev || !out_dev) return fail(c, IUGKP_EINVAL, "NULL device pointer");
+  CK(launch_residual(c, T0_dev, T1_dev, 0.0, out_dev, (cudaStream_t)cuda_stream), "residual");
+  return IUGKP_OK;
 }
 
 iugkp_status iugkp_solve_steady(iugkp_ctx* ctx, double* T_inout_dev, double tol, int max_iter, int* iters_out,

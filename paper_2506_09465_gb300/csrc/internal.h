@@ -12,6 +12,8 @@
 
 namespace iugkp {
 
+struct InstMG;
+
 // Arguments of the forward and adjoint sweep kernels (all device pointers).
 struct SweepArgs {
   const InstDesc* inst;
@@ -85,7 +87,7 @@ struct Ctx {
   double* d_cx = nullptr;        // [cells] coupling to the +x neighbour (0 at the row end)
   double* d_cy = nullptr;
   double* d_cz = nullptr;
-  double* d_pcg = nullptr;       // [4 * cells] x, r, p, q
+  double* d_pcg = nullptr;       // [5 * cells] x, r, p, q, z
   double* d_work = nullptr;      // [cells] scratch
   double* d_T2 = nullptr;        // [cells] scratch iterate
   double* d_R = nullptr;         // [nb * cells]
@@ -100,6 +102,19 @@ struct Ctx {
   double* d_scalar = nullptr;    // [8] small results
   double* d_adj = nullptr;       // [4 * cells] adjoint iteration buffers (allocated on first use)
   double* h_pinned = nullptr;    // [8 + n_inst] host readback
+  // multigrid preconditioner of the Newton correction (mg_setup.cu, mgpcg.cu)
+  struct InstMG* d_mg = nullptr;
+  float* d_mg_diag = nullptr;
+  float* d_mg_dinv = nullptr;
+  float* d_mg_cx = nullptr;
+  float* d_mg_cy = nullptr;
+  float* d_mg_cz = nullptr;
+  float* d_mg_cinv = nullptr;
+  float* d_mg_b = nullptr;
+  float* d_mg_x = nullptr;
+  float* d_mg_t = nullptr;
+  float* d_mg_r = nullptr;
+  long long mg_level_cells = 0;
   int sm_count = 0;
   size_t smem_optin = 0;
 };
@@ -118,6 +133,9 @@ cudaError_t launch_adjoint_correction(const Ctx* c, const double* lam, const dou
 cudaError_t launch_residual(const Ctx* c, const double* T0, const double* T1, double dT_ref, double* out_dev,
                             cudaStream_t s);
 cudaError_t launch_axpy_grad(const Ctx* c, const double* at, const double* g, double* lam_half, cudaStream_t s);
+cudaError_t launch_mgpcg(const Ctx* c, const double* rhs, cudaStream_t s);
+iugkp_status build_multigrid(Ctx* c, const std::vector<double>& diag, const std::vector<double>& cx,
+                             const std::vector<double>& cy, const std::vector<double>& cz);
 cudaError_t launch_grad_source(const Ctx* c, const double* at, double* grad, cudaStream_t s);
 
 }  // namespace iugkp

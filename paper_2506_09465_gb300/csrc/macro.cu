@@ -224,15 +224,7 @@ cudaError_t launch_macro(const Ctx* c, const double* R, const double* W, double*
   return cudaGetLastError();
 }
 
-static cudaError_t pcg(const Ctx* c, const double* rhs, cudaStream_t s) {
-  double* X = c->d_pcg;
-  double* Rr = X + c->total_cells;
-  double* P = Rr + c->total_cells;
-  double* Q = P + c->total_cells;
-  pcg_block_kernel<1024><<<c->n_inst, 1024, 0, s>>>(c->d_inst, c->d_diag, c->d_cx, c->d_cy, c->d_cz, rhs, X, Rr, P, Q,
-                                                    c->opt.cg_rtol, c->opt.cg_maxit, c->d_pcg_iters);
-  return cudaGetLastError();
-}
+static cudaError_t pcg(const Ctx* c, const double* rhs, cudaStream_t s) { return launch_mgpcg(c, rhs, s); }
 
 // T_half += theta dT with dT solving the diffusion problem for the Newton source.
 cudaError_t launch_newton(const Ctx* c, const double* T_n, double* T_half, const double* R, cudaStream_t s) {
