@@ -37,7 +37,47 @@ def parse():
     ap.add_argument("--no-steady", action="store_true", help="skip the time-to-steady runs")
     ap.add_argument("--no-plain", action="store_true", help="skip the plain FP64 baseline")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--profile", default=None, choices=["sweep", "step"],
+                    help="run --warmup then --steps sweeps (or full steps) of the workload and exit; for ncu")
+    ap.add_argument("--kn", type=float, default=None, help="profile one Knudsen number only")
+    ap.add_argument("--mode", default="fast", choices=["fast", "plain64", "plain32"], help="profiled path")
+    ap.add_argument("--no-flux", action="store_true", help="profile the sweep without face tallies (F = NULL)")
+    ap.add_argument("--refill", type=int, default=0, help="staged sweep refill threshold (0 = auto)")
     return ap.parse_args()
+
+
+def run_profile(args):
+    """Kernel launches only (no timing, no side legs): the command that ncu captures."""
+    import torch
+    from paper_2506_09465_gb300 import build as B
+    B.build()
+    from paper_2506_09465_gb300 import _lib as L
+    from paper_2506_09465_gb300 import workloads as WL
+    torch.cuda.set_device(0)
+    kns = KNS if args.kn is None else (args.kn,)
+    wl = WL.cavity_sweep(NGRID, kns, NPART)
+    opt = {"fast": {"refill_lanes": args.refill}, "plain64": {"precision": 0, "tally": 0, "schedule": 0},
+           "plain32": {"precision": 1, "tally": 0, "schedule": 0}}[args.mode]
+    s = make_solver(wl, seed=0, **opt)
+    T = torch.full((s.total_cells,), 0.3, dtype=torch.float64, device="cuda")
+    R = torch.empty(s.nb * s.total_cells, dtype=torch.float64, device="cuda")
+    W = torch.empty_like(R)
+    F = torch.empty(s.total_faces, dtype=torch.float64, device="cuda")
+    wall = torch.empty(s.total_walls, dtype=torch.float64, device="cuda")
+    cnt = torch.zeros(6, dtype=torch.int64, device="cuda")
+    Th = torch.empty_like(T)
+    sp = torch.cuda.current_stream().cuda_stream
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    for k in range(args.warmup + args.steps):
+        if k == args.warmup:
+            ev0.record()
+        s.sweep_into(T, 0, R, W, None if args.no_flux else F, wall, cnt)
+        if args.profile == "step":
+            L.check(s.lib.iugkp_macro(s.ctx, R.data_ptr(), None, Th.data_ptr(), None, sp), s.ctx)
+            s.newton_step(T, Th, R)
+    ev1.record()
+    torch.cuda.synchronize()
+    print("profile run done", cnt.cpu().tolist(), "ms/sweep", ev0.elapsed_time(ev1) / max(1, args.steps))
 
 
 def dist_env():
@@ -372,7 +412,9 @@ def run_ours(args):
 
 def main():
     args = parse()
-    if args.impl == "reference":
+    if args.profile:
+        run_profile(args)
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_ours(args)

@@ -90,6 +90,9 @@ typedef struct {
   long long step_budget;              /* max crossings + candidates per particle */
   int block_threads;                  /* threads per block of the trace kernel (0 = auto) */
   int blocks_per_sm;                  /* persistent blocks per SM (0 = auto) */
+  int refill_lanes;                   /* staged sweep: a warp refills its idle lanes once at
+                                         least this many (1..32) are idle; 0 = chosen per
+                                         instance from the expected events per particle */
 } iugkp_options;
 
 /* Fills *o with defaults: FP32 tracking, staged tallies, frozen draws, Newton on,

@@ -95,12 +95,14 @@ iugkp_status upload(Ctx* c, T** p, const std::vector<T>& h) {
 }
 
 void free_all(Ctx* c) {
-  void* ptrs[] = {c->d_inst, c->d_groups_all, c->d_groups_fwd, c->d_coef, c->d_ratio64, c->d_ratio32, c->d_taumaj,
+  void* ptrs[] = {c->d_vtm32, c->d_inst, c->d_groups_all, c->d_groups_fwd, c->d_coef, c->d_ratio64, c->d_ratio32, c->d_taumaj,
                   c->d_v, c->d_wcoef, c->d_wallT, c->d_srcshift, c->d_source, c->d_m, c->d_Vm, c->d_invVm, c->d_VC,
                   c->d_theta, c->d_theta_m, c->d_diag, c->d_cx, c->d_cy, c->d_cz, c->d_pcg, c->d_work, c->d_T2,
                   c->d_R, c->d_W, c->d_F, c->d_wall, c->d_red, c->d_counters, c->d_work_counter, c->d_err,
                   c->d_pcg_iters, c->d_scalar, c->d_adj, c->d_mg, c->d_mg_diag, c->d_mg_dinv, c->d_mg_cx,
-                  c->d_mg_cy, c->d_mg_cz, c->d_mg_cinv, c->d_mg_b, c->d_mg_x, c->d_mg_t, c->d_mg_r};
+                  c->d_mg_cy, c->d_mg_cz, c->d_mg_cinv, c->d_mg_b, c->d_mg_x, c->d_mg_t, c->d_mg_r,
+                  c->d_inst_beg, c->d_inst_end, c->d_inst_next, c->d_cost_prefix, c->d_win_fits, c->d_wmax,
+                  c->d_group_rcp, c->d_rcp, c->d_wall_unit};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (c->h_pinned) cudaFreeHost(c->h_pinned);
@@ -160,7 +162,58 @@ iugkp_status rebuild_forward_groups(Ctx* c) {
   c->fwd_particles = off;
   if (c->d_groups_fwd) cudaFree(c->d_groups_fwd);
   c->d_groups_fwd = nullptr;
-  return upload(c, &c->d_groups_fwd, c->h_groups_fwd);
+  iugkp_status s = upload(c, &c->d_groups_fwd, c->h_groups_fwd);
+  if (s != IUGKP_OK) return s;
+  // Staged sweep: each instance's forward particles are contiguous (groups are ordered
+  // by instance); blocks start on instances in proportion to the estimated cost
+  // (particles x expected events per particle).
+  std::vector<long long> beg(c->n_inst, 0), end(c->n_inst, 0);
+  std::vector<double> cost(c->n_inst, 0.0);
+  std::vector<int> seen(c->n_inst, 0);
+  for (const Group& g : c->h_groups_fwd) {
+    const long long np = (long long)g.n_emitters * g.per_emitter;
+    if (!seen[g.inst]) {
+      beg[g.inst] = g.first_particle;
+      end[g.inst] = g.first_particle;
+      seen[g.inst] = 1;
+    }
+    end[g.inst] = g.first_particle + np;
+    const InstDesc& in = c->h_inst[g.inst];
+    double hmin = in.h[0];
+    for (int a = 1; a < in.dim; ++a) hmin = std::min(hmin, in.h[a]);
+    const double lam = c->h_v[g.band] * c->h_taumean[(size_t)g.inst * c->nb + g.band];
+    const double nmax = (double)std::max(in.n[0], std::max(in.n[1], in.n[2]));
+    cost[g.inst] += (double)np * (1.0 + std::min(lam / hmin, nmax));
+  }
+  for (int k = 0; k < c->n_inst; ++k)
+    if (!seen[k]) beg[k] = end[k] = 0;
+  std::vector<double> prefix(c->n_inst, 0.0);
+  double tot = 0.0;
+  for (int k = 0; k < c->n_inst; ++k) {
+    prefix[k] = tot;
+    tot += cost[k];
+  }
+  c->cost_total = tot;
+  std::vector<int> fits(c->n_inst, 0);
+  for (int k = 0; k < c->n_inst; ++k) {
+    const InstDesc& in = c->h_inst[k];
+    fits[k] = (long long)(in.n[0] + 1) * in.n[1] * in.n[2] <= c->staged_cap ? 1 : 0;
+  }
+  std::vector<float> grcp;
+  for (const Group& g : c->h_groups_fwd) grcp.push_back(1.0f / (float)std::max(1, g.per_emitter));
+  if (c->d_group_rcp) cudaFree(c->d_group_rcp);
+  c->d_group_rcp = nullptr;
+  if ((s = upload(c, &c->d_group_rcp, grcp)) != IUGKP_OK) return s;
+  void* olds[] = {c->d_inst_beg, c->d_inst_end, c->d_cost_prefix, c->d_win_fits};
+  for (void* p : olds)
+    if (p) cudaFree(p);
+  c->d_inst_beg = c->d_inst_end = nullptr;
+  c->d_cost_prefix = nullptr;
+  c->d_win_fits = nullptr;
+  if ((s = upload(c, &c->d_inst_beg, beg)) != IUGKP_OK) return s;
+  if ((s = upload(c, &c->d_inst_end, end)) != IUGKP_OK) return s;
+  if ((s = upload(c, &c->d_cost_prefix, prefix)) != IUGKP_OK) return s;
+  return upload(c, &c->d_win_fits, fits);
 }
 
 }  // namespace
@@ -185,6 +238,7 @@ void iugkp_default_options(iugkp_options* o) {
   o->step_budget = 1ll << 24;
   o->block_threads = 0;
   o->blocks_per_sm = 0;
+  o->refill_lanes = 0;
 }
 
 const char* iugkp_last_error(const iugkp_ctx* ctx) {
@@ -213,6 +267,7 @@ iugkp_status iugkp_create_batch(int n, const iugkp_grid* g, const double* const*
       o->particles_per_wall_face > (1ll << 31))
     return fail(nullptr, IUGKP_EINVAL, "particles per cell / wall face must be in [nb, 2^31]");
   if (!(o->cg_rtol > 0.0) || o->cg_maxit < 1 || o->step_budget < 1) return fail(nullptr, IUGKP_EINVAL, "cg / budget options");
+  if (o->refill_lanes < 0 || o->refill_lanes > 32) return fail(nullptr, IUGKP_EINVAL, "refill_lanes must be in 0..32");
 
   iugkp_ctx* ctx = new (std::nothrow) iugkp_ctx();
   if (!ctx) return fail(nullptr, IUGKP_ENOMEM, "host allocation failed");
@@ -254,6 +309,8 @@ iugkp_status iugkp_create_batch(int n, const iugkp_grid* g, const double* const*
     }
     in.ncells = in.n[0] * in.n[1] * in.n[2];
     in.V = in.h[0] * in.h[1] * in.h[2];
+    for (int a = 0; a < 3; ++a) in.hf[a] = (float)in.h[a];
+    in.refill = 8;
     in.cell_off = cell_off;
     in.bc_off = (long long)nb * cell_off;
     in.face_off = face_off;
@@ -315,6 +372,7 @@ iugkp_status iugkp_create_batch(int n, const iugkp_grid* g, const double* const*
       }
       taumaj[(size_t)k * nb + bb] = tmin;
       rb[bb] = c->h_C[bb] * (inv_sum / (double)nc);
+      c->h_taumean.push_back((double)nc / inv_sum);
     }
     std::vector<long long> nband;
     if (!split_counts(o->particles_per_cell, rb, nband)) {
@@ -418,8 +476,31 @@ iugkp_status iugkp_create_batch(int n, const iugkp_grid* g, const double* const*
       }
     }
     c->h_nband.insert(c->h_nband.end(), nband.begin(), nband.end());
+    {
+      // Refill threshold of the staged sweep: long flights keep lanes busy (refill early,
+      // few lanes at a time); short flights are dominated by emission (refill in bulk).
+      double ev = 0.0, wsum = 0.0;
+      for (int bb = 0; bb < nb; ++bb) {
+        const double lam = c->h_v[bb] * c->h_taumean[(size_t)k * nb + bb];
+        const double nmax = (double)std::max(in.n[0], std::max(in.n[1], in.n[2]));
+        ev += (double)nband[bb] * (1.0 + std::min(lam / hmin, nmax));
+        wsum += (double)nband[bb];
+      }
+      ev /= wsum;
+      c->h_inst[k].refill = ev > 24.0 ? 4 : (ev > 6.0 ? 8 : 16);
+    }
   }
   c->h_nwall = nwall;
+  {
+    // Power entering through one face of each wall per unit wall temperature: the sum
+    // over bands of the particles' weights (N_w particles of C_b v_b A / (4 N_w) each).
+    std::vector<double> wu((size_t)n * 6, 0.0);
+    for (int k = 0; k < n; ++k)
+      for (int w = 0; w < 2 * dim; ++w)
+        for (int bb = 0; bb < nb; ++bb) wu[(size_t)k * 6 + w] += wcoef[((size_t)k * nb + bb) * 6 + w] * (double)nwall[bb];
+    iugkp_status s2 = upload(c, &c->d_wall_unit, wu);
+    if (s2 != IUGKP_OK) return bail(s2);
+  }
   c->total_particles = total_particles;
   c->h_wallT = wallTv;
 
@@ -432,6 +513,12 @@ iugkp_status iugkp_create_batch(int n, const iugkp_grid* g, const double* const*
   UP(c->d_ratio64, r64);
   UP(c->d_ratio32, r32);
   UP(c->d_taumaj, taumaj);
+  {
+    std::vector<float> vtm((size_t)n * nb);
+    for (int k = 0; k < n; ++k)
+      for (int bb = 0; bb < nb; ++bb) vtm[(size_t)k * nb + bb] = (float)(c->h_v[bb] * taumaj[(size_t)k * nb + bb]);
+    UP(c->d_vtm32, vtm);
+  }
   UP(c->d_v, c->h_v);
   UP(c->d_wcoef, wcoef);
   UP(c->d_wallT, wallTv);
@@ -445,14 +532,37 @@ iugkp_status iugkp_create_batch(int n, const iugkp_grid* g, const double* const*
   UP(c->d_cx, cx);
   UP(c->d_cy, cy);
   UP(c->d_cz, cz);
-#undef UP
   if ((s = dalloc(c, &c->d_source, cell_off)) != IUGKP_OK) return bail(s);
   if (cudaMemcpy(c->d_source, Qv.data(), Qv.size() * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess) {
     fail(c, IUGKP_ECUDA, "source upload");
     return bail(IUGKP_ECUDA);
   }
   if ((s = set_source(c, Qv, m)) != IUGKP_OK) return bail(s);
+  {
+    long long maxX = 0;
+    for (const InstDesc& in : c->h_inst) maxX = std::max(maxX, (long long)(in.n[0] + 1) * in.n[1] * in.n[2]);
+    const long long budget = ((long long)c->smem_optin - 4096) / 8;
+    c->staged_cap = (int)std::max<long long>(1, std::min(maxX, budget));
+  }
   if ((s = rebuild_forward_groups(c)) != IUGKP_OK) return bail(s);
+  {
+    std::vector<float> rcp((size_t)5 * n);
+    for (int k = 0; k < n; ++k) {
+      const InstDesc& in = c->h_inst[k];
+      rcp[k] = 1.0f / (float)in.n[0];
+      rcp[n + k] = 1.0f / (float)in.n[1];
+      for (int a = 0; a < 3; ++a) rcp[2 * n + 3 * k + a] = 1.0f / (float)in.n[(a + 1) % 3];
+    }
+    UP(c->d_rcp, rcp);
+  }
+  if ((s = dalloc(c, &c->d_inst_next, n)) != IUGKP_OK) return bail(s);
+  if ((s = dalloc(c, &c->d_wmax, n)) != IUGKP_OK) return bail(s);
+#undef UP
+  if (configure_staged(c) != cudaSuccess) {
+    cudaGetLastError();
+    fail(c, IUGKP_ECUDA, "staged sweep configuration");
+    return bail(IUGKP_ECUDA);
+  }
   if ((s = dalloc(c, &c->d_pcg, 5 * (size_t)cell_off)) != IUGKP_OK) return bail(s);
   if ((s = build_multigrid(c, diag, cx, cy, cz)) != IUGKP_OK) return bail(s);
   if ((s = dalloc(c, &c->d_work, cell_off)) != IUGKP_OK) return bail(s);
@@ -524,6 +634,7 @@ SweepArgs base_args(Ctx* c) {
   a.ratio64 = c->d_ratio64;
   a.ratio32 = c->d_ratio32;
   a.taumaj = c->d_taumaj;
+  a.vtm32 = c->d_vtm32;
   a.v = c->d_v;
   a.wcoef = c->d_wcoef;
   a.wallT = c->d_wallT;
@@ -560,6 +671,12 @@ iugkp_status sweep_async(Ctx* c, const double* T, unsigned epoch, double* R, dou
   unsigned long long* cnt = counters ? counters : c->d_counters;
   CK(cudaMemsetAsync(cnt, 0, CNT_N * sizeof(unsigned long long), s), "clear counters");
   CK(cudaMemsetAsync(c->d_work_counter, 0, sizeof(unsigned long long), s), "clear work counter");
+  const bool staged = c->opt.tally == IUGKP_TALLY_STAGED && c->opt.precision == IUGKP_TRACK_FP32 &&
+                      c->fwd_particles < (1ll << 31);
+  if (staged && wall && !F) {  // the staged sweep derives wall tallies from the face tallies
+    F = c->d_F;
+    CK(cudaMemsetAsync(F, 0, c->total_faces * sizeof(double), s), "clear F");
+  }
   SweepArgs a = base_args(c);
   a.groups = c->d_groups_fwd;
   a.n_groups = (int)c->h_groups_fwd.size();
@@ -571,7 +688,10 @@ iugkp_status sweep_async(Ctx* c, const double* T, unsigned epoch, double* R, dou
   a.wall = wall;
   a.counters = cnt;
   a.epoch = epoch;
-  CK(launch_sweep(c, a, s), "sweep launch");
+  if (staged)
+    CK(launch_sweep_staged(c, a, s), "staged sweep launch");
+  else
+    CK(launch_sweep(c, a, s), "sweep launch");
   return IUGKP_OK;
 }
 

@@ -9,6 +9,7 @@
 
 #include "../../include/iugkp.h"
 #include "layout.h"
+#include "staged.h"
 
 namespace iugkp {
 
@@ -28,6 +29,7 @@ struct SweepArgs {
   const float* ratio32;
   const double* taumaj;    // [inst * nb] majorant tau per instance and band
   const double* v;         // [nb] group speed
+  const float* vtm32;      // [inst * nb] v_b tau_maj in FP32
   const double* wcoef;     // [inst * nb * 6] C_b v_b A / (4 N_w) per wall
   const double* wallT;     // [walls]
   double* R;
@@ -72,6 +74,7 @@ struct Ctx {
   double* d_ratio64 = nullptr;
   float* d_ratio32 = nullptr;
   double* d_taumaj = nullptr;
+  float* d_vtm32 = nullptr;
   double* d_v = nullptr;
   double* d_wcoef = nullptr;
   double* d_wallT = nullptr;
@@ -115,6 +118,20 @@ struct Ctx {
   float* d_mg_t = nullptr;
   float* d_mg_r = nullptr;
   long long mg_level_cells = 0;
+  // staged sweep
+  long long* d_inst_beg = nullptr;   // [n_inst] forward particle range per instance
+  long long* d_inst_end = nullptr;
+  unsigned long long* d_inst_next = nullptr;
+  double* d_cost_prefix = nullptr;
+  double cost_total = 0.0;
+  int* d_win_fits = nullptr;
+  unsigned long long* d_wmax = nullptr;  // [n_inst] bit patterns of the largest weight
+  float* d_group_rcp = nullptr;      // [forward groups]
+  double* d_wall_unit = nullptr;     // [n_inst * 6] power entering per face per unit wall T
+  float* d_rcp = nullptr;            // [n_inst * 5]: 1/n_x, 1/n_y, 1/n(o1) for walls normal to x, y, z
+  int staged_cap = 0;           // x-faces per shared-memory window
+  int staged_blocks_per_sm = 1;
+  std::vector<double> h_taumean;  // [inst * nb]
   int sm_count = 0;
   size_t smem_optin = 0;
 };
@@ -133,6 +150,8 @@ cudaError_t launch_adjoint_correction(const Ctx* c, const double* lam, const dou
 cudaError_t launch_residual(const Ctx* c, const double* T0, const double* T1, double dT_ref, double* out_dev,
                             cudaStream_t s);
 cudaError_t launch_axpy_grad(const Ctx* c, const double* at, const double* g, double* lam_half, cudaStream_t s);
+cudaError_t launch_sweep_staged(const Ctx* c, const SweepArgs& a, cudaStream_t s);
+cudaError_t configure_staged(Ctx* c);
 cudaError_t launch_mgpcg(const Ctx* c, const double* rhs, cudaStream_t s);
 iugkp_status build_multigrid(Ctx* c, const std::vector<double>& diag, const std::vector<double>& cx,
                              const std::vector<double>& cy, const std::vector<double>& cz);

@@ -20,6 +20,8 @@ struct InstDesc {
   long long nfaces;
   int wall_off;       // offset into per-wall arrays (= 2 * dim * k)
   uint32_t inst_id;   // Philox instance id
+  float hf[3];        // cell size per axis in FP32 (the FP32 walk)
+  int refill;         // staged sweep: refill a warp's lanes once this many are idle
 };
 
 // A run of emitters sharing (instance, band, kind). kind 0 = the instance's cells;

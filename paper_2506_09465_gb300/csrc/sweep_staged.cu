@@ -1,0 +1,630 @@
+// Fast forward sweep: FP32 walk, persistent blocks, face tallies staged in shared memory
+// in 64-bit fixed point. Same method and draws as the plain sweep
+// (arXiv 2506.09465 Sec. 3.1 steps (1)-(3), Sec. 3.2 null collisions); only the
+// arithmetic precision of the walk and the way tallies are accumulated differ.
+//
+// Face tallies:
+//  * faces normal to x are accumulated in a shared-memory copy of all of the instance's
+//    x-faces (when it fits), as integers in units of q = w_max 2^-36 (exact and
+//    independent of the order of the additions), and flushed to the FP64 array when the
+//    block leaves the instance; otherwise they are global FP64 atomics;
+//  * faces normal to the last axis (y in 2D, z in 3D) are not tallied, except on the low
+//    boundary: every particle conserves power, so in every cell the net inflow equals the
+//    absorbed minus emitted power, and the last-axis faces follow exactly by a prefix sum
+//    along each column (derive_last_axis_kernel);
+//  * in 3D the y-faces are tallied with global FP64 atomics;
+//  * nothing is tallied per particle for the walls: the power a wall emits enters through
+//    its faces deterministically (N particles of known weight per face), and the power it
+//    absorbs is its emission plus the outward net flux through its faces
+//    (boundary_emission_kernel, wall_absorbed_kernel).
+#include <cuda_runtime.h>
+
+#include "device.cuh"
+#include "internal.h"
+#include "staged.h"
+
+namespace iugkp {
+
+namespace {
+
+struct LCounts {
+  unsigned v[CNT_N];  // per thread and launch: far below 2^32
+};
+
+__device__ __forceinline__ void flush_lcounts(LCounts& c, unsigned long long* out) {
+#pragma unroll
+  for (int k = 0; k < CNT_N; ++k) {
+    unsigned long long x = c.v[k];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+    if ((threadIdx.x & 31) == 0 && x) atomicAdd(&out[k], x);
+  }
+}
+
+// Exact n / d for n < 2^31 and d >= 1 from an FP32 reciprocal and integer fix-ups.
+__device__ __forceinline__ unsigned udiv(unsigned n, unsigned d, float rcp) {
+  unsigned q = (unsigned)((float)n * rcp);
+  int r = (int)(n - q * d);
+  q += (int)((float)r * rcp);
+  r = (int)(n - q * d);
+  if (r < 0) q -= 1;
+  else if (r >= (int)d) q += 1;
+  return q;
+}
+
+// Register-resident walk state. t_a: path length at which the next face normal to axis a
+// is reached; d_a: path length per cell along a; s_a: +-1; xface: index of the x-face the
+// particle crosses next along x (kept incrementally).
+struct FW {
+  int i0, i1, i2, cell, xface;
+  float t0, t1, t2;
+  float d0, d1, d2;
+  int s0, s1, s2;
+  float D;
+};
+
+__device__ __forceinline__ void axis_init(float s, float xi, float h, float& t, float& d, int& st) {
+  const float as = fabsf(s);
+  st = s > 0.f ? 1 : -1;
+  d = __fdividef(h, as);  // +inf when s = 0
+  t = (s > 0.f ? 1.f - xi : xi) * d;
+}
+
+}  // namespace
+
+// One block per forward group: the largest |weight| of its emitters, max-reduced into
+// its instance's slot (non-negative doubles order like their bit patterns).
+__global__ void group_wmax_kernel(SweepArgs A, unsigned long long* wmax_bits) {
+  __shared__ double sh[32];
+  const Group G = A.groups[blockIdx.x];
+  const InstDesc& in = A.inst[G.inst];
+  double m = 0.0;
+  if (G.kind == 0) {
+    const double* coef = A.coef + in.bc_off + (long long)G.band * in.ncells;
+    for (int e = threadIdx.x; e < in.ncells; e += blockDim.x) {
+      double Te = A.T[in.cell_off + e];
+      if (A.srcshift) Te += A.srcshift[in.cell_off + e];
+      m = fmax(m, fabs(coef[e] * Te));
+    }
+  } else if (threadIdx.x == 0) {
+    const int wl = G.kind - 1;
+    m = fabs(A.wcoef[((long long)G.inst * A.nb + G.band) * 6 + wl] * A.wallT[in.wall_off + wl]);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_down_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = m;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double r = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) r = fmax(r, sh[w]);
+    atomicMax(&wmax_bits[G.inst], (unsigned long long)__double_as_longlong(r));
+  }
+}
+
+// Emits particle pid (global forward index) into lane state. Returns false for a
+// zero-weight particle (nothing to trace).
+// Per-lane cache of the group and emitter of the lane's previous particle: consecutive
+// particles share an emitter (N per cell), so most emissions load nothing from memory.
+struct EmitCache {
+  unsigned g_first, g_end;  // forward particle range of the cached group
+  int g_idx, g_per, g_kind, g_band;
+  float g_rcp;
+  int e;
+  double w;
+};
+
+// Emits forward particle pid into the lane state. Returns false for a zero-weight
+// particle (nothing to trace).
+template <int DIM>
+__device__ __forceinline__ bool staged_emit(const SweepArgs& A, const StagedArgs& S, unsigned pid, bool useF,
+                                            double& w, int& band, FW& f, Stream& st, uint32_t& ub, EmitCache& ec,
+                                            const InstDesc& in, int k) {
+  if (pid < ec.g_first || pid >= ec.g_end) {
+    const int gi = find_group(A.groups, A.n_groups, (long long)pid);
+    const Group G = A.groups[gi];
+    ec.g_idx = gi;
+    ec.g_first = (unsigned)G.first_particle;
+    ec.g_end = (unsigned)(G.first_particle + (long long)G.n_emitters * G.per_emitter);
+    ec.g_per = G.per_emitter;
+    ec.g_kind = G.kind;
+    ec.g_band = G.band;
+    ec.g_rcp = S.group_rcp[gi];
+    ec.e = -1;
+  }
+  band = ec.g_band;
+  const int b = ec.g_band;
+  const unsigned local = pid - ec.g_first;
+  const int e = (int)udiv(local, (unsigned)ec.g_per, ec.g_rcp);
+  const int q = (int)(local - (unsigned)e * (unsigned)ec.g_per);
+  const int n0 = in.n[0], n1 = in.n[1], n2 = in.n[2];
+  const int kind = ec.g_kind;
+  float xi0 = 0.5f, xi1 = 0.5f, xi2 = 0.5f, sx = 0.f, sy = 0.f, sz = 0.f;
+  if (kind == 0) {
+    if (e != ec.e) {
+      double Te = A.T[in.cell_off + e];
+      if (A.srcshift) Te += A.srcshift[in.cell_off + e];
+      ec.w = A.coef[in.bc_off + (long long)b * in.ncells + e] * Te;
+      ec.e = e;
+    }
+    w = ec.w;
+    if (w == 0.0) return false;
+    st.init(A.seed, in.inst_id, (uint32_t)b, A.epoch, (uint32_t)e, (uint32_t)q);
+    if (DIM == 1) {
+      f.i0 = e;
+      f.i1 = 0;
+      f.i2 = 0;
+    } else {
+      const int r = (int)udiv((unsigned)e, (unsigned)n0, S.rcp_n0[k]);
+      f.i0 = e - r * n0;
+      if (DIM == 2) {
+        f.i1 = r;
+        f.i2 = 0;
+      } else {
+        f.i2 = (int)udiv((unsigned)r, (unsigned)n1, S.rcp_n1[k]);
+        f.i1 = r - f.i2 * n1;
+      }
+    }
+    float u_mu, u_phi = 0.5f;
+    if (DIM == 1) {
+      xi0 = word_uniform<float>(st.buf.x);
+      u_mu = word_uniform<float>(st.buf.y);
+    } else if (DIM == 2) {
+      xi0 = word_uniform<float>(st.buf.x);
+      xi1 = word_uniform<float>(st.buf.y);
+      u_mu = word_uniform<float>(st.buf.z);
+      u_phi = word_uniform<float>(st.buf.w);
+    } else {
+      xi0 = word_uniform<float>(st.buf.x);
+      xi1 = word_uniform<float>(st.buf.y);
+      xi2 = word_uniform<float>(st.buf.z);
+      u_mu = word_uniform<float>(st.buf.w);
+      st.load_block(1);
+      u_phi = word_uniform<float>(st.buf.x);
+    }
+    const float mu = 2.f * u_mu - 1.f;
+    sx = mu;
+    if (DIM >= 2) {
+      const float sn = sqrtf(1.f - mu * mu);
+      float sp, cp;
+      sincospif(2.f * u_phi, &sp, &cp);
+      sy = sn * cp;
+      sz = sn * sp;
+    }
+    st.j = thermal_uniforms(DIM);
+  } else {
+    const int wl = kind - 1;
+    if (ec.e != -2) {
+      ec.w = A.wcoef[((long long)k * A.nb + b) * 6 + wl] * A.wallT[in.wall_off + wl];
+      ec.e = -2;  // one weight for the whole wall group
+    }
+    w = ec.w;
+    if (w == 0.0) return false;
+    const int a = wl >> 1, side = wl & 1;
+    // faces of wall a are enumerated over (o1, o2) = ((a+1)%3, (a+2)%3), o1 fastest
+    const int no1 = a == 0 ? n1 : (a == 1 ? n2 : n0);
+    const int j2 = (int)udiv((unsigned)e, (unsigned)no1, S.rcp_wall[k * 3 + a]);
+    const int j1 = e - j2 * no1;
+    long long face;
+    if (a == 0) {
+      f.i0 = side ? n0 - 1 : 0;
+      f.i1 = j1;
+      f.i2 = j2;
+      face = in.fax_off[0] + (side ? n0 : 0) + (long long)(n0 + 1) * (j1 + (long long)n1 * j2);
+    } else if (a == 1) {
+      f.i0 = j2;
+      f.i1 = side ? n1 - 1 : 0;
+      f.i2 = j1;
+      face = in.fax_off[1] + j2 + (long long)n0 * ((side ? n1 : 0) + (long long)(n1 + 1) * j1);
+    } else {
+      f.i0 = j1;
+      f.i1 = j2;
+      f.i2 = side ? n2 - 1 : 0;
+      face = in.fax_off[2] + j1 + (long long)n0 * (j2 + (long long)n1 * (side ? n2 : 0));
+    }
+    st.init(A.seed, in.inst_id, (uint32_t)b, A.epoch, (uint32_t)(in.ncells + face), (uint32_t)q);
+    float u_n, u_phi = 0.5f;
+    float t0 = 0.5f, t1 = 0.5f;  // tangential fractions, in axis order
+    if (DIM == 1) {
+      u_n = word_uniform<float>(st.buf.x);
+    } else if (DIM == 2) {
+      t0 = word_uniform<float>(st.buf.x);
+      u_n = word_uniform<float>(st.buf.y);
+      u_phi = word_uniform<float>(st.buf.z);
+    } else {
+      t0 = word_uniform<float>(st.buf.x);
+      t1 = word_uniform<float>(st.buf.y);
+      u_n = word_uniform<float>(st.buf.z);
+      u_phi = word_uniform<float>(st.buf.w);
+    }
+    const float mn = sqrtf(u_n);
+    const float sn = DIM >= 2 ? sqrtf(1.f - u_n) : 0.f;
+    float sp = 0.f, cp = 0.f;
+    if (DIM >= 2) sincospif(2.f * u_phi, &sp, &cp);
+    const float nrm = side ? -mn : mn, ta = sn * cp, tb = sn * sp;  // tangential (o1, o2)
+    if (a == 0) {
+      sx = nrm; sy = ta; sz = tb;
+      xi0 = side ? 1.f : 0.f; xi1 = t0; xi2 = t1;
+    } else if (a == 1) {
+      sy = nrm; sz = ta; sx = tb;
+      xi1 = side ? 1.f : 0.f; xi0 = t0; xi2 = t1;
+    } else {
+      sz = nrm; sx = ta; sy = tb;
+      xi2 = side ? 1.f : 0.f; xi0 = t0; xi1 = t1;
+    }
+    st.j = wall_uniforms(DIM);
+    (void)face;  // the power entering through wall faces is added by boundary_kernel
+  }
+  axis_init(sx, xi0, in.hf[0], f.t0, f.d0, f.s0);
+  if (DIM >= 2) axis_init(sy, xi1, in.hf[1], f.t1, f.d1, f.s1);
+  if (DIM >= 3) axis_init(sz, xi2, in.hf[2], f.t2, f.d2, f.s2);
+  f.cell = f.i0 + n0 * (f.i1 + n1 * f.i2);
+  f.xface = f.cell + (f.i1 + n1 * f.i2) + (f.s0 > 0 ? 1 : 0);
+  uint32_t ua;
+  st.next_pair(ua, ub);
+  f.D = -__logf(word_uniform<float>(ua)) * A.vtm32[(long long)k * A.nb + b];
+  return true;
+}
+
+// Persistent blocks. Each block works on one instance at a time (first the instance its
+// index falls on by estimated cost, then any instance with work left); its warps take
+// private ranges of the instance's particles and refill idle lanes together. Faces normal
+// to x go to a shared-memory copy of the instance's x-faces (when it fits), in units of
+// the instance's q; the block flushes it when it leaves the instance.
+template <int DIM>
+__global__ void __launch_bounds__(STAGED_NT, 1) sweep_staged_kernel(SweepArgs A, StagedArgs S) {
+  extern __shared__ unsigned long long win[];
+  __shared__ int s_inst;
+  LCounts cnt;
+#pragma unroll
+  for (int k = 0; k < CNT_N; ++k) cnt.v[k] = 0;
+  const int lane = threadIdx.x & 31;
+  const unsigned lt_mask = (1u << lane) - 1u;
+  const bool useF = A.F != nullptr;
+  const int n_inst = S.n_inst;
+  int start = 0;
+  {
+    const double pos = (blockIdx.x + 0.5) / gridDim.x * S.cost_total;
+    while (start + 1 < n_inst && S.cost_prefix[start + 1] <= pos) ++start;
+  }
+  for (int visit = 0; visit < n_inst; ++visit) {
+    const int k = (start + visit) % n_inst;
+    if (threadIdx.x == 0) s_inst = (*(volatile unsigned long long*)&S.inst_next[k] < (unsigned long long)S.inst_end[k]) ? k : -1;
+    __syncthreads();
+    if (s_inst < 0) {
+      __syncthreads();
+      continue;
+    }
+    const InstDesc& in = A.inst[k];
+    // descriptor fields used inside the walk, held in registers (the atomics below would
+    // otherwise force reloads)
+    const int n0 = in.n[0], n1 = in.n[1], n2 = in.n[2];
+    const long long face_off = in.face_off, fax1 = in.fax_off[1], fax2 = in.fax_off[2];
+    const long long bc_off = in.bc_off;
+    const int ncells = in.ncells, refill = S.refill > 0 ? S.refill : in.refill;
+    const int sy_cell = n0, sz_cell = n0 * n1;           // cell index steps along y, z
+    const int sy_xf = n0 + 1, sz_xf = (n0 + 1) * n1;     // x-face index steps along y, z
+    const bool staged = useF && S.win_fits[k];
+    const int X = staged ? (int)((n0 + 1) * (long long)n1 * n2) : 0;
+    for (int i = threadIdx.x; i < X; i += STAGED_NT) win[i] = 0ull;
+    __syncthreads();
+    const double wmax = S.wmax[k];
+    const double qinv = wmax > 0.0 ? 0x1p36 / wmax : 0.0;
+    const unsigned pend = (unsigned)S.inst_end[k];
+    unsigned rbeg = 0, rend = 0;  // this warp's private particle range
+    double w = 0.0, wt = 0.0;
+    unsigned long long qwx = 0;   // signed x-face contribution in units of q
+    int band = 0;
+    long long bcbase = 0;
+    float vtm = 0.f;
+    FW f;
+    Stream st;
+    uint32_t ub = 0;
+    bool alive = false, exhausted = false;
+    EmitCache ec;
+    ec.g_first = 1;
+    ec.g_end = 0;  // empty: forces a lookup on the first emission
+    ec.e = -1;
+    for (;;) {
+      // ---- refill idle lanes together ----
+      const unsigned dead = __ballot_sync(0xffffffffu, !alive);
+      if (!exhausted && __popc(dead) >= refill) {
+        if (rbeg == rend) {  // private range used up: take the next one of the instance
+          unsigned long long got = 0;
+          if (lane == 0) got = atomicAdd(&S.inst_next[k], (unsigned long long)S.warp_grab);
+          got = __shfl_sync(0xffffffffu, got, 0);
+          if (got < pend) {
+            rbeg = (unsigned)got;
+            rend = (unsigned)min(got + (unsigned long long)S.warp_grab, (unsigned long long)pend);
+          } else {
+            exhausted = true;
+          }
+        }
+        const unsigned rank = __popc(dead & lt_mask);
+        const unsigned take = min((unsigned)__popc(dead), rend - rbeg);
+        if (!alive && rank < take) {
+          alive = staged_emit<DIM>(A, S, rbeg + rank, useF, w, band, f, st, ub, ec, in, k);
+          if (alive) {
+            cnt.v[CNT_FLIGHTS] += 1;
+            const long long qw = __double2ll_rn(w * qinv);
+            qwx = (unsigned long long)(f.s0 > 0 ? qw : -qw);
+            wt = w * A.taumaj[(long long)k * A.nb + band];
+            vtm = A.vtm32[(long long)k * A.nb + band];
+            bcbase = bc_off + (long long)band * ncells;
+          }
+        }
+        rbeg += take;
+      }
+      if (!__any_sync(0xffffffffu, alive)) {
+        if (exhausted) break;
+        continue;
+      }
+      // ---- walk: up to WALK_K crossings per lane; lanes that stopped at a candidate
+      // collision are then handled together ----
+      if (alive) {
+        bool stop = false;
+        const int cy = f.s1 * sy_cell, cz = f.s2 * sz_cell, xy = f.s1 * sy_xf, xz = f.s2 * sz_xf;
+#pragma unroll 1
+        for (int it = 0; it < WALK_K; ++it) {
+          bool ax, ay = false;
+          float tmin;
+          if (DIM == 1) {
+            ax = true;
+            tmin = f.t0;
+          } else if (DIM == 2) {
+            ax = !(f.t1 < f.t0);  // equal distances cross x first
+            ay = !ax;
+            tmin = ax ? f.t0 : f.t1;
+          } else {
+            ax = !(f.t1 < f.t0) && !(f.t2 < f.t0);
+            ay = !ax && !(f.t2 < f.t1);
+            tmin = ax ? f.t0 : (ay ? f.t1 : f.t2);
+          }
+          if (f.D <= tmin) {
+            stop = true;
+            break;
+          }
+          const bool az = DIM == 3 && !ax && !ay;
+          if (useF) {
+            if (ax) {
+              if (staged) atomicAdd(&win[f.xface], qwx);
+              else atomicAdd(&A.F[face_off + f.xface], f.s0 > 0 ? w : -w);
+            } else if (ay && (DIM == 3 || (f.s1 < 0 && f.i1 == 0))) {
+              const int up = f.s1 > 0 ? 1 : 0;
+              atomicAdd(&A.F[face_off + fax1 + f.cell + (long long)n0 * f.i2 + (long long)n0 * up], up ? w : -w);
+            } else if (az && f.s2 < 0 && f.i2 == 0) {
+              atomicAdd(&A.F[face_off + fax2 + f.cell], -w);
+            }
+          }
+          bool out;
+          if (DIM == 1) {
+            f.i0 += f.s0;
+            f.t0 += f.d0;
+            f.cell += f.s0;
+            f.xface += f.s0;
+            out = (unsigned)f.i0 >= (unsigned)n0;
+          } else if (DIM == 2) {
+            f.i0 += ax ? f.s0 : 0;
+            f.i1 += ax ? 0 : f.s1;
+            f.t0 += ax ? f.d0 : 0.f;
+            f.t1 += ax ? 0.f : f.d1;
+            f.cell += ax ? f.s0 : cy;
+            f.xface += ax ? f.s0 : xy;
+            out = (unsigned)(ax ? f.i0 : f.i1) >= (unsigned)(ax ? n0 : n1);
+          } else {
+            f.i0 += ax ? f.s0 : 0;
+            f.i1 += ay ? f.s1 : 0;
+            f.i2 += az ? f.s2 : 0;
+            f.t0 += ax ? f.d0 : 0.f;
+            f.t1 += ay ? f.d1 : 0.f;
+            f.t2 += az ? f.d2 : 0.f;
+            f.cell += ax ? f.s0 : (ay ? cy : cz);
+            f.xface += ax ? f.s0 : (ay ? xy : xz);
+            out = (unsigned)(ax ? f.i0 : (ay ? f.i1 : f.i2)) >= (unsigned)(ax ? n0 : (ay ? n1 : n2));
+          }
+          if (out) {  // absorbed by a wall: its power reaches the wall tally through F
+            cnt.v[CNT_WALL_EXITS] += 1;
+            alive = false;
+            break;
+          }
+          cnt.v[CNT_CROSSINGS] += 1;
+        }
+        if (stop) {
+          // candidate collision in the current cell (Sec. 3.2): W tally, then accept with
+          // probability tau_maj / tau(x)
+          cnt.v[CNT_CANDIDATES] += 1;
+          const long long ci = bcbase + f.cell;
+          if (A.W) atomicAdd(&A.W[ci], wt);
+          if (word_uniform<float>(ub) < A.ratio32[ci]) {
+            cnt.v[CNT_REAL] += 1;
+            atomicAdd(&A.R[ci], w);
+            alive = false;
+          } else {
+            uint32_t ua;
+            st.next_pair(ua, ub);
+            f.D += -__logf(word_uniform<float>(ua)) * vtm;
+          }
+        }
+      }
+    }
+    __syncthreads();
+    if (staged) {
+      const double qs = wmax * 0x1p-36;
+      double* Fx = A.F + face_off;  // x-faces come first
+      for (int i = threadIdx.x; i < X; i += STAGED_NT) {
+        const long long v = (long long)win[i];
+        if (v) atomicAdd(&Fx[i], (double)v * qs);
+      }
+    }
+    __syncthreads();
+  }
+  flush_lcounts(cnt, A.counters);
+}
+
+// Faces normal to the last axis from per-cell conservation, one thread per column:
+// F[k+1] = F[k] + (net inflow through the other axes' faces of cell k) - (R_k - S_k),
+// S_k = V m T_emit (emitted thermal and source power), starting from the tallied low
+// boundary face.
+template <int DIM>
+__global__ void derive_last_axis_kernel(const InstDesc* inst, int n_inst, int nb, const double* T,
+                                        const double* srcshift, const double* Vm, const double* R, double* F) {
+  const int k = blockIdx.y;
+  if (k >= n_inst) return;
+  const InstDesc& in = inst[k];
+  const int n0 = in.n[0], n1 = in.n[1], n2 = in.n[2];
+  const int nlast = DIM == 2 ? n1 : n2;
+  const int ncol = in.ncells / nlast;
+  double* Fi = F + in.face_off;
+  for (int col = blockIdx.x * blockDim.x + threadIdx.x; col < ncol; col += gridDim.x * blockDim.x) {
+    double acc;
+    int ix = col % n0, iy = DIM == 3 ? col / n0 : 0;
+    const long long stride = DIM == 2 ? n0 : (long long)n0 * n1;
+    const long long base_cell = DIM == 2 ? ix : ix + (long long)n0 * iy;
+    // low boundary face of this column
+    const long long f0 = DIM == 2 ? in.fax_off[1] + ix : in.fax_off[2] + ix + (long long)n0 * iy;
+    acc = Fi[f0];
+    for (int kk = 0; kk < nlast; ++kk) {
+      const long long c = base_cell + kk * stride;
+      const long long g = in.cell_off + c;
+      double r = 0.0;
+      for (int b = 0; b < nb; ++b) r += R[in.bc_off + (long long)b * in.ncells + c];
+      double te = T[g];
+      if (srcshift) te += srcshift[g];
+      const long long row = c / n0;  // x-face index of the cell's low face = c + row
+      double inflow = Fi[in.fax_off[0] + c + row] - Fi[in.fax_off[0] + c + row + 1];
+      if (DIM == 3) {
+        const int cz = (int)(c / ((long long)n0 * n1));
+        const long long fy = in.fax_off[1] + c + (long long)n0 * cz;
+        inflow += Fi[fy] - Fi[fy + n0];
+      }
+      acc = acc + inflow - (r - Vm[g] * te);
+      const long long fn = DIM == 2 ? in.fax_off[1] + c + n0 : in.fax_off[2] + c + (long long)n0 * n1;
+      Fi[fn] = acc;
+    }
+  }
+}
+
+// Faces of wall w = 2a + side of an instance, enumerated as j1 + n(o1) j2 (o1 = (a+1)%3,
+// o2 = (a+2)%3); returns the face index within the instance.
+__device__ __forceinline__ long long wall_face(const InstDesc& in, int a, int side, int j) {
+  const int n0 = in.n[0], n1 = in.n[1], n2 = in.n[2];
+  if (a == 0) {
+    const int j1 = j % n1, j2 = j / n1;
+    return in.fax_off[0] + (side ? n0 : 0) + (long long)(n0 + 1) * (j1 + (long long)n1 * j2);
+  }
+  if (a == 1) {
+    const int j1 = j % n2, j2 = j / n2;
+    return in.fax_off[1] + j2 + (long long)n0 * ((side ? n1 : 0) + (long long)(n1 + 1) * j1);
+  }
+  const int j1 = j % n0, j2 = j / n0;
+  return in.fax_off[2] + j1 + (long long)n0 * (j2 + (long long)n1 * (side ? n2 : 0));
+}
+
+__device__ __forceinline__ int wall_faces(const InstDesc& in, int a) {
+  return in.n[(a + 1) % 3] * in.n[(a + 2) % 3];
+}
+
+// Power entering through every boundary face from its wall's emission (N_w particles of
+// weight C_b v_b A T_w / (4 N_w) per face and band), except on the high side of the
+// derived axis (that axis is rebuilt from conservation). Grid: (faces, walls, instances).
+__global__ void boundary_emission_kernel(const InstDesc* inst, int dim, const double* wall_unit, const double* wallT,
+                                         double* F) {
+  const int k = blockIdx.z, wl = blockIdx.y;
+  const int a = wl >> 1, side = wl & 1;
+  if (dim >= 2 && a == dim - 1 && side == 1) return;
+  const InstDesc& in = inst[k];
+  const double e = wall_unit[k * 6 + wl] * wallT[in.wall_off + wl];
+  if (e == 0.0) return;
+  const int nf = wall_faces(in, a);
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < nf; j += gridDim.x * blockDim.x)
+    F[in.face_off + wall_face(in, a, side, j)] += side ? -e : e;
+}
+
+// Absorbed power of each wall = its emission + the outward net flux through its faces.
+// One block per (wall, instance); fixed-order reduction.
+__global__ void __launch_bounds__(256) wall_absorbed_kernel(const InstDesc* inst, const double* wall_unit,
+                                                            const double* wallT, const double* F, double* wall) {
+  __shared__ double sh[8];
+  const int k = blockIdx.y, wl = blockIdx.x;
+  const int a = wl >> 1, side = wl & 1;
+  const InstDesc& in = inst[k];
+  const int nf = wall_faces(in, a);
+  double sum = 0.0;
+  for (int j = threadIdx.x; j < nf; j += 256) sum += F[in.face_off + wall_face(in, a, side, j)];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) sum += __shfl_down_sync(0xffffffffu, sum, o);
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = sum;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < 8; ++w) t += sh[w];
+    const double emitted = wall_unit[k * 6 + wl] * (double)nf * wallT[in.wall_off + wl];
+    wall[in.wall_off + wl] = emitted + (side ? t : -t);
+  }
+}
+
+cudaError_t launch_sweep_staged(const Ctx* c, const SweepArgs& a, cudaStream_t s) {
+  StagedArgs S;
+  S.n_inst = c->n_inst;
+  S.inst_next = c->d_inst_next;
+  S.inst_end = c->d_inst_end;
+  S.cost_prefix = c->d_cost_prefix;
+  S.cost_total = c->cost_total;
+  S.win_fits = c->d_win_fits;
+  S.wmax = reinterpret_cast<const double*>(c->d_wmax);
+  S.warp_grab = 256;
+  S.refill = c->opt.refill_lanes;
+  S.group_rcp = c->d_group_rcp;
+  S.rcp_n0 = c->d_rcp;
+  S.rcp_n1 = c->d_rcp + c->n_inst;
+  S.rcp_wall = c->d_rcp + 2 * c->n_inst;
+  cudaError_t e = cudaMemcpyAsync(c->d_inst_next, c->d_inst_beg, c->n_inst * sizeof(long long),
+                                  cudaMemcpyDeviceToDevice, s);
+  if (e != cudaSuccess) return e;
+  if ((e = cudaMemsetAsync(c->d_wmax, 0, c->n_inst * sizeof(double), s)) != cudaSuccess) return e;
+  group_wmax_kernel<<<a.n_groups, 256, 0, s>>>(a, c->d_wmax);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  const size_t smem = (size_t)c->staged_cap * sizeof(unsigned long long);
+  const int blocks = c->sm_count * c->staged_blocks_per_sm;
+  switch (c->dim) {
+    case 1: sweep_staged_kernel<1><<<blocks, STAGED_NT, smem, s>>>(a, S); break;
+    case 2: sweep_staged_kernel<2><<<blocks, STAGED_NT, smem, s>>>(a, S); break;
+    default: sweep_staged_kernel<3><<<blocks, STAGED_NT, smem, s>>>(a, S); break;
+  }
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  if (a.F) {
+    boundary_emission_kernel<<<dim3(8, 2 * c->dim, c->n_inst), 256, 0, s>>>(c->d_inst, c->dim, c->d_wall_unit,
+                                                                           c->d_wallT, a.F);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  }
+  if (a.F && c->dim >= 2) {
+    dim3 grid((unsigned)((c->max_inst_cells + 255) / 256), (unsigned)c->n_inst);
+    if (grid.x > 64) grid.x = 64;
+    if (c->dim == 2)
+      derive_last_axis_kernel<2><<<grid, 256, 0, s>>>(c->d_inst, c->n_inst, c->nb, a.T, a.srcshift, c->d_Vm, a.R, a.F);
+    else
+      derive_last_axis_kernel<3><<<grid, 256, 0, s>>>(c->d_inst, c->n_inst, c->nb, a.T, a.srcshift, c->d_Vm, a.R, a.F);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  if (a.F && a.wall) {
+    wall_absorbed_kernel<<<dim3(2 * c->dim, c->n_inst), 256, 0, s>>>(c->d_inst, c->d_wall_unit, c->d_wallT, a.F,
+                                                                    a.wall);
+    e = cudaGetLastError();
+  }
+  return e;
+}
+
+cudaError_t configure_staged(Ctx* c) {
+  cudaError_t e = cudaSuccess;
+  const size_t smem = (size_t)c->staged_cap * sizeof(unsigned long long);
+  if ((e = cudaFuncSetAttribute(sweep_staged_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess) return e;
+  if ((e = cudaFuncSetAttribute(sweep_staged_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess) return e;
+  if ((e = cudaFuncSetAttribute(sweep_staged_kernel<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess) return e;
+  int nb = 0;
+  void* fn = c->dim == 1 ? (void*)sweep_staged_kernel<1> : (c->dim == 2 ? (void*)sweep_staged_kernel<2> : (void*)sweep_staged_kernel<3>);
+  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, STAGED_NT, smem)) != cudaSuccess) return e;
+  c->staged_blocks_per_sm = nb > 0 ? nb : 1;
+  return cudaSuccess;
+}
+
+}  // namespace iugkp

@@ -55,8 +55,9 @@ def test_sweep_fp64_matches_oracle(orc, name, insts, C, v):
         assert g["counters"].cpu().numpy().tolist() == r.counters.astype(np.int64).tolist()
 
 
+@pytest.mark.parametrize("tally", [0, 1])
 @pytest.mark.parametrize("dim", [1, 2, 3])
-def test_sweep_fp32_tracks_same_particles(orc, dim):
+def test_sweep_fp32_tracks_same_particles(orc, dim, tally):
     rng = np.random.default_rng(30 + dim)
     n = {1: (40,), 2: (16, 12), 3: (6, 6, 5)}[dim]
     inst = WL.random_instance(rng, dim, n, 1, (0.05, 0.8))
@@ -64,11 +65,11 @@ def test_sweep_fp32_tracks_same_particles(orc, dim):
     T = rng.uniform(0.0, 1.0, size=inst.ncells)
     p = oracle_problem(inst, [1.0], [1.0], N, N, seed=3)
     r = orc.sweep(p, T, 0)
-    s = gpu_solver(inst, [1.0], [1.0], N, N, precision=1, tally=0, schedule=0, seed=3)
+    s = gpu_solver(inst, [1.0], [1.0], N, N, precision=1, tally=tally, schedule=tally, seed=3)
     g = s.sweep(cuda_T(T), 0)
     # Same draws; single-precision walks change a particle's cell only when it stops
     # within ~1e-7 of a face, so tallies agree to well below the statistical noise.
-    for key, ora in (("R", r.R), ("F", r.F), ("wall", r.wall)):
+    for key, ora in (("R", r.R), ("W", r.W), ("F", r.F), ("wall", r.wall)):
         ok, err = normwise_close(g[key].cpu().numpy(), ora, 2e-3)
         assert ok, (key, err)
     c_g = g["counters"].cpu().numpy().astype(float)
