@@ -193,6 +193,32 @@ iugkp_status iugkp_adjoint(iugkp_ctx *ctx, const double *T_star_dev, const doubl
                            double tol, int max_iter, double *grad_source_dev,
                            double *grad_wall_dev, double *lambda_dev, void *cuda_stream);
 
+/* ---------------------------------------------------------------------------------
+ * Allocation-free correction solve. The paper has no counterpart; this exists for
+ * callers that cannot call cudaMalloc: code whose device memory is owned entirely by
+ * another allocator (a framework's caching pool that has already reserved the GPU), or
+ * a latency-critical loop that cannot afford the device synchronisation an allocation
+ * may cause. The contexts above allocate their buffers in iugkp_create; this function
+ * needs no context and allocates nothing.
+ *
+ * Solves -div(kappa grad x) = rhs on one uniform grid g (the finite-volume operator of
+ * iugkp_newton_step: harmonic face kappa, vacuum wall condition with outward flux
+ * wall_cv / 2 times the wall value in series with half a cell of conduction) by
+ * Jacobi-preconditioned CG in FP64 to ||r|| <= rtol ||rhs||, starting from x = 0.
+ *   kappa_dev [cells] conductivity (> 0), rhs_dev [cells], x_dev [cells] output;
+ *   wall_cv   sum over bands of C_b v_b (> 0); *iters_out (may be NULL) gets the count.
+ * Scratch (stencil, CG vectors) lives in one static device array sized for
+ * IUGKP_NOALLOC_MAX_CELLS cells, kept by every GPU that loads the library until the
+ * process exits. Larger grids return IUGKP_EINVAL. Every call reuses that array, so
+ * calls whose work overlaps on the GPU (two streams, two host threads) race. The first
+ * call on a device looks the array's address up once with that device current; make
+ * that first call before any stream capture. Synchronises cuda_stream to read the
+ * iteration count; IUGKP_ENOCONV if maxit is reached. Errors: iugkp_last_error(NULL). */
+#define IUGKP_NOALLOC_MAX_CELLS 65536
+iugkp_status iugkp_diffusion_solve_noalloc(const iugkp_grid *g, const double *kappa_dev, double wall_cv,
+                                           const double *rhs_dev, double *x_dev, double rtol, int maxit,
+                                           int *iters_out, void *cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif
