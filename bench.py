@@ -375,7 +375,7 @@ def run_ours(args):
         clocks = clk.summary()
         # Roofline of the dominant kernel (the sweep): ALU issue bound. Algorithmic
         # lane-operations per event x events / kernel time.
-        OPS_CROSS, OPS_CAND, OPS_FLIGHT = 14, 60, 180
+        OPS_CROSS, OPS_CAND, OPS_FLIGHT = 10, 50, 200
         sw_s = statistics.median(sweep_ms) / 1e3
         ops = (OPS_CROSS * sweep_counts[3] + OPS_CAND * sweep_counts[1] + OPS_FLIGHT * sweep_counts[0])
         peak_ops = 152 * 128 * 2.07e9  # FP32/INT32 lanes x max SM clock
@@ -397,7 +397,9 @@ def run_ours(args):
             "speedup_vs_plain_fp64_sweep": (sweep_counts[3] / sw_s) / plain["sweep_crossings_per_s"] if plain else None,
             "e2e": {"value": e2e_value, "unit": "cell-crossings/s", "h2d_bytes_per_step": nc * 8,
                     "d2h_bytes_per_step": nc * 8},
-            "gpu_launches": args.steps * 7,
+            # per step: group_wmax, sweep_staged, boundary_emission, derive_last_axis,
+            # wall_absorbed, macro, newton_rhs, mgpcg, add_scaled, residual (2 kernels)
+            "gpu_launches": args.steps * 11,
             "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": peak_ops / 1e12,
                          "unit": "Tops/s (FP32+INT32 lane ops)", "frac": achieved / peak_ops, "traffic": None,
                          "kernel": "sweep", "peak_source": "152 SMs x 128 lanes x 2.07 GHz (unit counts and clock)"},
