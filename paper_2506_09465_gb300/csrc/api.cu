@@ -200,7 +200,7 @@ iugkp_status rebuild_forward_groups(Ctx* c) {
     fits[k] = (long long)(in.n[0] + 1) * in.n[1] * in.n[2] <= c->staged_cap ? 1 : 0;
   }
   std::vector<float> grcp;
-  for (const Group& g : c->h_groups_fwd) grcp.push_back(1.0f / (float)std::max(1, g.per_emitter));
+  for (const Group& g : c->h_groups_fwd) grcp.push_back(1.0f / (float)std::max(1, g.n_emitters));
   if (c->d_group_rcp) cudaFree(c->d_group_rcp);
   c->d_group_rcp = nullptr;
   if ((s = upload(c, &c->d_group_rcp, grcp)) != IUGKP_OK) return s;
@@ -233,7 +233,7 @@ void iugkp_default_options(iugkp_options* o) {
   o->seed = 0;
   o->epoch0 = 0;
   o->instance_base = 0;
-  o->cg_rtol = 1e-10;
+  o->cg_rtol = 1e-4;
   o->cg_maxit = 5000;
   o->step_budget = 1ll << 24;
   o->block_threads = 0;

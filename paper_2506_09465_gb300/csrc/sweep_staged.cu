@@ -103,12 +103,12 @@ __global__ void group_wmax_kernel(SweepArgs A, unsigned long long* wmax_bits) {
 
 // Emits particle pid (global forward index) into lane state. Returns false for a
 // zero-weight particle (nothing to trace).
-// Per-lane cache of the group and emitter of the lane's previous particle: consecutive
-// particles share an emitter (N per cell), so most emissions load nothing from memory.
+// Per-lane cache of the group of the lane's previous particle (and of the weight of a
+// wall group, which is the same for all its particles).
 struct EmitCache {
   unsigned g_first, g_end;  // forward particle range of the cached group
-  int g_idx, g_per, g_kind, g_band;
-  float g_rcp;
+  int g_idx, g_ne, g_kind, g_band;
+  float g_rcp;              // 1 / n_emitters
   int e;
   double w;
 };
@@ -125,7 +125,7 @@ __device__ __forceinline__ bool staged_emit(const SweepArgs& A, const StagedArgs
     ec.g_idx = gi;
     ec.g_first = (unsigned)G.first_particle;
     ec.g_end = (unsigned)(G.first_particle + (long long)G.n_emitters * G.per_emitter);
-    ec.g_per = G.per_emitter;
+    ec.g_ne = G.n_emitters;
     ec.g_kind = G.kind;
     ec.g_band = G.band;
     ec.g_rcp = S.group_rcp[gi];
@@ -133,20 +133,20 @@ __device__ __forceinline__ bool staged_emit(const SweepArgs& A, const StagedArgs
   }
   band = ec.g_band;
   const int b = ec.g_band;
+  // The staged sweep visits a group's particles q-major (particle q of every emitter,
+  // then q + 1), so the lanes of a warp start in different cells: their face and deposit
+  // tallies rarely hit the same address at the same time. Draws are keyed by (emitter,
+  // particle), so the order changes nothing else.
   const unsigned local = pid - ec.g_first;
-  const int e = (int)udiv(local, (unsigned)ec.g_per, ec.g_rcp);
-  const int q = (int)(local - (unsigned)e * (unsigned)ec.g_per);
+  const int q = (int)udiv(local, (unsigned)ec.g_ne, ec.g_rcp);
+  const int e = (int)(local - (unsigned)q * (unsigned)ec.g_ne);
   const int n0 = in.n[0], n1 = in.n[1], n2 = in.n[2];
   const int kind = ec.g_kind;
   float xi0 = 0.5f, xi1 = 0.5f, xi2 = 0.5f, sx = 0.f, sy = 0.f, sz = 0.f;
   if (kind == 0) {
-    if (e != ec.e) {
-      double Te = A.T[in.cell_off + e];
-      if (A.srcshift) Te += A.srcshift[in.cell_off + e];
-      ec.w = A.coef[in.bc_off + (long long)b * in.ncells + e] * Te;
-      ec.e = e;
-    }
-    w = ec.w;
+    double Te = A.T[in.cell_off + e];
+    if (A.srcshift) Te += A.srcshift[in.cell_off + e];
+    w = A.coef[in.bc_off + (long long)b * in.ncells + e] * Te;
     if (w == 0.0) return false;
     st.init(A.seed, in.inst_id, (uint32_t)b, A.epoch, (uint32_t)e, (uint32_t)q);
     if (DIM == 1) {
