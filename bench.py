@@ -337,11 +337,11 @@ def run_ours(args):
         plain = {}
         if not args.no_plain:
             # Plain FP64: FP64 walk, global FP64 atomics, one thread per particle, one
-            # instance at a time, no graph.
+            # instance at a time, no CUDA graph (same iteration, Newton and CG tolerance).
             ptot_cross, ptot_ms, psteady, piters = 0, 0.0, 0.0, []
             for kn in KNS:
                 w1 = WL.cavity(NGRID, kn, NPART)
-                sp1 = make_solver(w1, seed=0, precision=0, tally=0, schedule=0)
+                sp1 = make_solver(w1, seed=0, precision=0, tally=0, schedule=0, use_graphs=0)
                 T1 = torch.full((sp1.total_cells,), 0.3, dtype=torch.float64, device=dev)
                 R1 = torch.empty(sp1.total_cells, dtype=torch.float64, device=dev)
                 F1 = torch.empty(sp1.total_faces, dtype=torch.float64, device=dev)

@@ -93,6 +93,9 @@ typedef struct {
   int refill_lanes;                   /* staged sweep: a warp refills its idle lanes once at
                                          least this many (1..32) are idle; 0 = chosen per
                                          instance from the expected events per particle */
+  int use_graphs;                     /* 1: iugkp_solve_steady with frozen draws replays a
+                                         CUDA graph of two iterations (one host readback per
+                                         two iterations); 0: plain launches */
 } iugkp_options;
 
 /* Fills *o with defaults: FP32 tracking, staged tallies, frozen draws, Newton on,

@@ -34,7 +34,8 @@ class Options(ctypes.Structure):
                 ("particles_per_cell", ctypes.c_longlong), ("particles_per_wall_face", ctypes.c_longlong),
                 ("seed", ctypes.c_ulonglong), ("epoch0", ctypes.c_uint), ("instance_base", ctypes.c_uint),
                 ("cg_rtol", ctypes.c_double), ("cg_maxit", ctypes.c_int), ("step_budget", ctypes.c_longlong),
-                ("block_threads", ctypes.c_int), ("blocks_per_sm", ctypes.c_int), ("refill_lanes", ctypes.c_int)]
+                ("block_threads", ctypes.c_int), ("blocks_per_sm", ctypes.c_int), ("refill_lanes", ctypes.c_int),
+                ("use_graphs", ctypes.c_int)]
 
 
 class Layout(ctypes.Structure):

@@ -132,6 +132,10 @@ struct Ctx {
   int staged_cap = 0;           // x-faces per shared-memory window
   int staged_blocks_per_sm = 1;
   std::vector<double> h_taumean;  // [inst * nb]
+  // graph-captured steady iterations
+  cudaStream_t graph_stream = nullptr;
+  cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+  double* d_res_block = nullptr;  // [2 * GRAPH_ITERS] residual sums of a replay
   int sm_count = 0;
   size_t smem_optin = 0;
 };
@@ -149,6 +153,7 @@ cudaError_t launch_adjoint_correction(const Ctx* c, const double* lam, const dou
                                       cudaStream_t s);
 cudaError_t launch_residual(const Ctx* c, const double* T0, const double* T1, double dT_ref, double* out_dev,
                             cudaStream_t s);
+cudaError_t launch_pcg_check(const Ctx* c, cudaStream_t s);
 cudaError_t launch_axpy_grad(const Ctx* c, const double* at, const double* g, double* lam_half, cudaStream_t s);
 cudaError_t launch_sweep_staged(const Ctx* c, const SweepArgs& a, cudaStream_t s);
 cudaError_t configure_staged(Ctx* c);

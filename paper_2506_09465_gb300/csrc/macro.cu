@@ -259,6 +259,18 @@ cudaError_t launch_residual(const Ctx* c, const double* T0, const double* T1, do
   return cudaGetLastError();
 }
 
+// Sets ERR_PCG in the device error word when any instance's CG hit its iteration cap
+// (lets an iteration run without a host round trip for the CG status).
+__global__ void pcg_check_kernel(const int* iters, int n_inst, int* err) {
+  for (int k = threadIdx.x; k < n_inst; k += blockDim.x)
+    if (iters[k] < 0) atomicOr(err, ERR_PCG);
+}
+
+cudaError_t launch_pcg_check(const Ctx* c, cudaStream_t s) {
+  pcg_check_kernel<<<1, 128, 0, s>>>(c->d_pcg_iters, c->n_inst, c->d_err);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_axpy_grad(const Ctx* c, const double* at, const double* g, double* lam_half, cudaStream_t s) {
   add_kernel<<<grid_for(c, c->total_cells), 256, 0, s>>>(c->total_cells, at, g, lam_half);
   return cudaGetLastError();

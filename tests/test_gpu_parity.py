@@ -211,3 +211,18 @@ def test_full_size_conservation_every_mode():
         assert np.abs(inflow - (R - emitted)).max() <= tol * scale * 50, (prec, tally)
         wall_em = 1.0 / 4.0 * 1.0
         assert abs((g["wall"].cpu().numpy().sum() - wall_em) - (emitted.sum() - R.sum())) <= 1e-6 * emitted.sum()
+
+
+def test_graph_replay_matches_plain_loop():
+    # Frozen draws: the CUDA-graph replay (two iterations per replay) and the plain loop
+    # run the same iteration; they differ only in atomic summation order.
+    inst = WL.cavity(40, 0.1).instances[0]
+    outs = []
+    for graphs in (1, 0):
+        s = gpu_solver(inst, [1.0], [1.0], 256, 256, use_graphs=graphs, seed=5)
+        T, it, res = s.solve_steady(None, 1e-9, 200)
+        assert res <= 1e-9
+        outs.append((T.cpu().numpy(), it))
+    ok, err = normwise_close(outs[0][0], outs[1][0], 1e-8)
+    assert ok, err
+    assert outs[0][1] >= outs[1][1] and outs[0][1] - outs[1][1] <= 1
