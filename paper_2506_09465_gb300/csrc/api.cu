@@ -102,7 +102,8 @@ void free_all(Ctx* c) {
                   c->d_pcg_iters, c->d_scalar, c->d_adj, c->d_mg, c->d_mg_diag, c->d_mg_dinv, c->d_mg_cx,
                   c->d_mg_cy, c->d_mg_cz, c->d_mg_cinv, c->d_mg_b, c->d_mg_x, c->d_mg_t, c->d_mg_r,
                   c->d_inst_beg, c->d_inst_end, c->d_inst_next, c->d_cost_prefix, c->d_win_fits, c->d_wmax,
-                  c->d_group_rcp, c->d_rcp, c->d_wall_unit};
+                  c->d_group_rcp, c->d_rcp, c->d_wall_unit, c->d_all_beg, c->d_all_end, c->d_all_cost_prefix,
+                  c->d_all_group_rcp};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (c->h_pinned) cudaFreeHost(c->h_pinned);
@@ -143,6 +144,40 @@ iugkp_status set_source(Ctx* c, const std::vector<double>& Q, const std::vector<
   return IUGKP_OK;
 }
 
+// Per-instance particle ranges of a group list (groups are ordered by instance), the
+// prefix sums of the estimated cost (particles x expected events per particle) and the
+// reciprocal of each group's emitter count.
+void staged_tables(const Ctx* c, const std::vector<Group>& groups, std::vector<long long>& beg,
+                   std::vector<long long>& end, std::vector<double>& prefix, double& total, std::vector<float>& grcp) {
+  beg.assign(c->n_inst, 0);
+  end.assign(c->n_inst, 0);
+  std::vector<double> cost(c->n_inst, 0.0);
+  std::vector<int> seen(c->n_inst, 0);
+  grcp.clear();
+  for (const Group& g : groups) {
+    grcp.push_back(1.0f / (float)std::max(1, g.n_emitters));
+    const long long np = (long long)g.n_emitters * g.per_emitter;
+    if (!seen[g.inst]) {
+      beg[g.inst] = g.first_particle;
+      end[g.inst] = g.first_particle;
+      seen[g.inst] = 1;
+    }
+    end[g.inst] = g.first_particle + np;
+    const InstDesc& in = c->h_inst[g.inst];
+    double hmin = in.h[0];
+    for (int a = 1; a < in.dim; ++a) hmin = std::min(hmin, in.h[a]);
+    const double lam = c->h_v[g.band] * c->h_taumean[(size_t)g.inst * c->nb + g.band];
+    const double nmax = (double)std::max(in.n[0], std::max(in.n[1], in.n[2]));
+    cost[g.inst] += (double)np * (1.0 + std::min(lam / hmin, nmax));
+  }
+  prefix.assign(c->n_inst, 0.0);
+  total = 0.0;
+  for (int k = 0; k < c->n_inst; ++k) {
+    prefix[k] = total;
+    total += cost[k];
+  }
+}
+
 // Forward groups leave out walls at zero temperature (their particles weigh zero).
 iugkp_status rebuild_forward_groups(Ctx* c) {
   c->h_groups_fwd.clear();
@@ -169,51 +204,26 @@ iugkp_status rebuild_forward_groups(Ctx* c) {
   iugkp_status s = upload(c, &c->d_groups_fwd, c->h_groups_fwd);
   if (s != IUGKP_OK) return s;
   // Staged sweep: each instance's forward particles are contiguous (groups are ordered
-  // by instance); blocks start on instances in proportion to the estimated cost
-  // (particles x expected events per particle).
-  std::vector<long long> beg(c->n_inst, 0), end(c->n_inst, 0);
-  std::vector<double> cost(c->n_inst, 0.0);
-  std::vector<int> seen(c->n_inst, 0);
-  for (const Group& g : c->h_groups_fwd) {
-    const long long np = (long long)g.n_emitters * g.per_emitter;
-    if (!seen[g.inst]) {
-      beg[g.inst] = g.first_particle;
-      end[g.inst] = g.first_particle;
-      seen[g.inst] = 1;
-    }
-    end[g.inst] = g.first_particle + np;
-    const InstDesc& in = c->h_inst[g.inst];
-    double hmin = in.h[0];
-    for (int a = 1; a < in.dim; ++a) hmin = std::min(hmin, in.h[a]);
-    const double lam = c->h_v[g.band] * c->h_taumean[(size_t)g.inst * c->nb + g.band];
-    const double nmax = (double)std::max(in.n[0], std::max(in.n[1], in.n[2]));
-    cost[g.inst] += (double)np * (1.0 + std::min(lam / hmin, nmax));
-  }
-  for (int k = 0; k < c->n_inst; ++k)
-    if (!seen[k]) beg[k] = end[k] = 0;
-  std::vector<double> prefix(c->n_inst, 0.0);
+  // by instance); blocks start on instances in proportion to the estimated cost.
+  std::vector<long long> beg, end;
+  std::vector<double> prefix;
+  std::vector<float> grcp;
   double tot = 0.0;
-  for (int k = 0; k < c->n_inst; ++k) {
-    prefix[k] = tot;
-    tot += cost[k];
-  }
+  staged_tables(c, c->h_groups_fwd, beg, end, prefix, tot, grcp);
   c->cost_total = tot;
   std::vector<int> fits(c->n_inst, 0);
   for (int k = 0; k < c->n_inst; ++k) {
     const InstDesc& in = c->h_inst[k];
     fits[k] = (long long)(in.n[0] + 1) * in.n[1] * in.n[2] <= c->staged_cap ? 1 : 0;
   }
-  std::vector<float> grcp;
-  for (const Group& g : c->h_groups_fwd) grcp.push_back(1.0f / (float)std::max(1, g.n_emitters));
-  if (c->d_group_rcp) cudaFree(c->d_group_rcp);
-  c->d_group_rcp = nullptr;
-  if ((s = upload(c, &c->d_group_rcp, grcp)) != IUGKP_OK) return s;
-  void* olds[] = {c->d_inst_beg, c->d_inst_end, c->d_cost_prefix, c->d_win_fits};
+  void* olds[] = {c->d_inst_beg, c->d_inst_end, c->d_cost_prefix, c->d_win_fits, c->d_group_rcp};
   for (void* p : olds)
     if (p) cudaFree(p);
   c->d_inst_beg = c->d_inst_end = nullptr;
   c->d_cost_prefix = nullptr;
   c->d_win_fits = nullptr;
+  c->d_group_rcp = nullptr;
+  if ((s = upload(c, &c->d_group_rcp, grcp)) != IUGKP_OK) return s;
   if ((s = upload(c, &c->d_inst_beg, beg)) != IUGKP_OK) return s;
   if ((s = upload(c, &c->d_inst_end, end)) != IUGKP_OK) return s;
   if ((s = upload(c, &c->d_cost_prefix, prefix)) != IUGKP_OK) return s;
@@ -550,6 +560,16 @@ iugkp_status iugkp_create_batch(int n, const iugkp_grid* g, const double* const*
     c->staged_cap = (int)std::max<long long>(1, std::min(maxX, budget));
   }
   if ((s = rebuild_forward_groups(c)) != IUGKP_OK) return bail(s);
+  {
+    std::vector<long long> beg, end;
+    std::vector<double> prefix;
+    std::vector<float> grcp;
+    staged_tables(c, c->h_groups_all, beg, end, prefix, c->all_cost_total, grcp);
+    UP(c->d_all_beg, beg);
+    UP(c->d_all_end, end);
+    UP(c->d_all_cost_prefix, prefix);
+    UP(c->d_all_group_rcp, grcp);
+  }
   {
     std::vector<float> rcp((size_t)5 * n);
     for (int k = 0; k < n; ++k) {
@@ -927,6 +947,22 @@ iugkp_status iugkp_solve_steady(iugkp_ctx* ctx, double* T_inout_dev, double tol,
   return IUGKP_OK;
 }
 
+}  // extern "C"
+
+namespace {
+
+// The adjoint re-trace: the staged kernel for the FP32 walk with staged tallies (the
+// fast path), else the plain one-thread-per-particle kernel.
+cudaError_t adjoint_sweep(Ctx* c, const SweepArgs& a, cudaStream_t s) {
+  if (c->opt.tally == IUGKP_TALLY_STAGED && c->opt.precision == IUGKP_TRACK_FP32 && c->total_particles < (1ll << 31))
+    return launch_adjoint_staged(c, a, s);
+  return launch_adjoint(c, a, s);
+}
+
+}  // namespace
+
+extern "C" {
+
 iugkp_status iugkp_adjoint(iugkp_ctx* ctx, const double* T_star_dev, const double* g_dev, double tol, int max_iter,
                            double* grad_source_dev, double* grad_wall_dev, double* lambda_dev, void* cuda_stream) {
   (void)T_star_dev;
@@ -957,13 +993,14 @@ iugkp_status iugkp_adjoint(iugkp_ctx* ctx, const double* T_star_dev, const doubl
   a.epoch = c->opt.epoch0;
   a.adj_out = at;
   a.adj_wall = grad_wall_dev;
+  a.counters = c->d_counters;  // event counts of the re-trace (diagnostic)
   double res = INFINITY;
   int it = 0;
   while (it < max_iter) {
     a.lambda = lam;
     CK(cudaMemsetAsync(at, 0, nc * sizeof(double), s), "clear");
     CK(cudaMemsetAsync(grad_wall_dev, 0, c->total_walls * sizeof(double), s), "clear");
-    CK(launch_adjoint(c, a, s), "adjoint sweep");
+    CK(adjoint_sweep(c, a, s), "adjoint sweep");
     CK(launch_axpy_grad(c, at, g_dev, half, s), "adjoint axpy");
     if (c->opt.newton) {
       CK(launch_adjoint_correction(c, lam, half, nxt, s), "adjoint correction");
@@ -980,7 +1017,7 @@ iugkp_status iugkp_adjoint(iugkp_ctx* ctx, const double* T_star_dev, const doubl
   a.lambda = lam;
   CK(cudaMemsetAsync(at, 0, nc * sizeof(double), s), "clear");
   CK(cudaMemsetAsync(grad_wall_dev, 0, c->total_walls * sizeof(double), s), "clear");
-  CK(launch_adjoint(c, a, s), "adjoint sweep");
+  CK(adjoint_sweep(c, a, s), "adjoint sweep");
   CK(launch_grad_source(c, at, grad_source_dev, s), "grad source");
   if ((st = check_device(c, s)) != IUGKP_OK) return st;
   if (!(res <= tol)) return fail(c, IUGKP_ENOCONV, "adjoint: max_iter reached before tol");

@@ -128,6 +128,13 @@ struct Ctx {
   unsigned long long* d_wmax = nullptr;  // [n_inst] bit patterns of the largest weight
   float* d_group_rcp = nullptr;      // [forward groups]
   double* d_wall_unit = nullptr;     // [n_inst * 6] power entering per face per unit wall T
+  // adjoint re-trace over all groups (staged kernel)
+  long long* d_all_beg = nullptr;
+  long long* d_all_end = nullptr;
+  double* d_all_cost_prefix = nullptr;
+  double all_cost_total = 0.0;
+  float* d_all_group_rcp = nullptr;
+  int adj_blocks_per_sm = 1;
   float* d_rcp = nullptr;            // [n_inst * 5]: 1/n_x, 1/n_y, 1/n(o1) for walls normal to x, y, z
   int staged_cap = 0;           // x-faces per shared-memory window
   int staged_blocks_per_sm = 1;
@@ -157,6 +164,7 @@ cudaError_t launch_pcg_check(const Ctx* c, cudaStream_t s);
 cudaError_t launch_axpy_grad(const Ctx* c, const double* at, const double* g, double* lam_half, cudaStream_t s);
 cudaError_t launch_sweep_staged(const Ctx* c, const SweepArgs& a, cudaStream_t s);
 cudaError_t configure_staged(Ctx* c);
+cudaError_t launch_adjoint_staged(const Ctx* c, const SweepArgs& a, cudaStream_t s);
 cudaError_t launch_mgpcg(const Ctx* c, const double* rhs, cudaStream_t s);
 iugkp_status build_multigrid(Ctx* c, const std::vector<double>& diag, const std::vector<double>& cx,
                              const std::vector<double>& cy, const std::vector<double>& cz);

@@ -32,6 +32,7 @@ struct LCounts {
 };
 
 __device__ __forceinline__ void flush_lcounts(LCounts& c, unsigned long long* out) {
+  if (!out) return;
 #pragma unroll
   for (int k = 0; k < CNT_N; ++k) {
     unsigned long long x = c.v[k];
@@ -115,10 +116,13 @@ struct EmitCache {
 
 // Emits forward particle pid into the lane state. Returns false for a zero-weight
 // particle (nothing to trace).
-template <int DIM>
+// ADJ: the adjoint re-trace; w is then the particle's weight per unit emission
+// temperature (every emitter is traced) and `emitter` receives the cell (>= 0) or the
+// wall slot (-1 - wall) the particle's gather belongs to.
+template <int DIM, bool ADJ>
 __device__ __forceinline__ bool staged_emit(const SweepArgs& A, const StagedArgs& S, unsigned pid, bool useF,
                                             double& w, int& band, FW& f, Stream& st, uint32_t& ub, EmitCache& ec,
-                                            const InstDesc& in, int k) {
+                                            const InstDesc& in, int k, int& emitter) {
   if (pid < ec.g_first || pid >= ec.g_end) {
     const int gi = find_group(A.groups, A.n_groups, (long long)pid);
     const Group G = A.groups[gi];
@@ -144,10 +148,15 @@ __device__ __forceinline__ bool staged_emit(const SweepArgs& A, const StagedArgs
   const int kind = ec.g_kind;
   float xi0 = 0.5f, xi1 = 0.5f, xi2 = 0.5f, sx = 0.f, sy = 0.f, sz = 0.f;
   if (kind == 0) {
-    double Te = A.T[in.cell_off + e];
-    if (A.srcshift) Te += A.srcshift[in.cell_off + e];
-    w = A.coef[in.bc_off + (long long)b * in.ncells + e] * Te;
-    if (w == 0.0) return false;
+    if (ADJ) {
+      w = A.coef[in.bc_off + (long long)b * in.ncells + e];
+    } else {
+      double Te = A.T[in.cell_off + e];
+      if (A.srcshift) Te += A.srcshift[in.cell_off + e];
+      w = A.coef[in.bc_off + (long long)b * in.ncells + e] * Te;
+      if (w == 0.0) return false;
+    }
+    emitter = e;
     st.init(A.seed, in.inst_id, (uint32_t)b, A.epoch, (uint32_t)e, (uint32_t)q);
     if (DIM == 1) {
       f.i0 = e;
@@ -194,11 +203,12 @@ __device__ __forceinline__ bool staged_emit(const SweepArgs& A, const StagedArgs
   } else {
     const int wl = kind - 1;
     if (ec.e != -2) {
-      ec.w = A.wcoef[((long long)k * A.nb + b) * 6 + wl] * A.wallT[in.wall_off + wl];
+      ec.w = A.wcoef[((long long)k * A.nb + b) * 6 + wl] * (ADJ ? 1.0 : A.wallT[in.wall_off + wl]);
       ec.e = -2;  // one weight for the whole wall group
     }
     w = ec.w;
     if (w == 0.0) return false;
+    emitter = -1 - wl;
     const int a = wl >> 1, side = wl & 1;
     // faces of wall a are enumerated over (o1, o2) = ((a+1)%3, (a+2)%3), o1 fastest
     const int no1 = a == 0 ? n1 : (a == 1 ? n2 : n0);
@@ -270,7 +280,10 @@ __device__ __forceinline__ bool staged_emit(const SweepArgs& A, const StagedArgs
 // private ranges of the instance's particles and refill idle lanes together. Faces normal
 // to x go to a shared-memory copy of the instance's x-faces (when it fits), in units of
 // the instance's q; the block flushes it when it leaves the instance.
-template <int DIM>
+// ADJ = true: the adjoint re-trace (see adjoint.cu for the map it transposes): no tallies;
+// a real collision gathers c_p lambda[stop] / (V m_stop) into the particle's emitter cell,
+// or into its wall, accumulated per lane while the lane stays on one wall group.
+template <int DIM, bool ADJ>
 __global__ void __launch_bounds__(STAGED_NT, 1) sweep_staged_kernel(SweepArgs A, StagedArgs S) {
   extern __shared__ unsigned long long win[];
   __shared__ int s_inst;
@@ -279,7 +292,7 @@ __global__ void __launch_bounds__(STAGED_NT, 1) sweep_staged_kernel(SweepArgs A,
   for (int k = 0; k < CNT_N; ++k) cnt.v[k] = 0;
   const int lane = threadIdx.x & 31;
   const unsigned lt_mask = (1u << lane) - 1u;
-  const bool useF = A.F != nullptr;
+  const bool useF = !ADJ && A.F != nullptr;
   const int n_inst = S.n_inst;
   int start = 0;
   {
@@ -324,6 +337,9 @@ __global__ void __launch_bounds__(STAGED_NT, 1) sweep_staged_kernel(SweepArgs A,
     ec.g_first = 1;
     ec.g_end = 0;  // empty: forces a lookup on the first emission
     ec.e = -1;
+    int emitter = 0;        // adjoint: gather target of the lane's particle
+    int acc_slot = 0;       // adjoint: wall slot of the pending per-lane wall sum
+    double acc = 0.0;
     for (;;) {
       // ---- refill idle lanes together ----
       const unsigned dead = __ballot_sync(0xffffffffu, !alive);
@@ -342,7 +358,12 @@ __global__ void __launch_bounds__(STAGED_NT, 1) sweep_staged_kernel(SweepArgs A,
         const unsigned rank = __popc(dead & lt_mask);
         const unsigned take = min((unsigned)__popc(dead), rend - rbeg);
         if (!alive && rank < take) {
-          alive = staged_emit<DIM>(A, S, rbeg + rank, useF, w, band, f, st, ub, ec, in, k);
+          alive = staged_emit<DIM, ADJ>(A, S, rbeg + rank, useF, w, band, f, st, ub, ec, in, k, emitter);
+          if (ADJ && alive && emitter < 0 && emitter != acc_slot) {
+            if (acc != 0.0) atomicAdd(&A.adj_wall[in.wall_off + (-1 - acc_slot)], acc);
+            acc = 0.0;
+            acc_slot = emitter;
+          }
           if (alive) {
             cnt.v[CNT_FLIGHTS] += 1;
             const long long qw = __double2ll_rn(w * qinv);
@@ -433,10 +454,17 @@ __global__ void __launch_bounds__(STAGED_NT, 1) sweep_staged_kernel(SweepArgs A,
           // probability tau_maj / tau(x)
           cnt.v[CNT_CANDIDATES] += 1;
           const long long ci = bcbase + f.cell;
-          if (A.W) atomicAdd(&A.W[ci], wt);
+          if (!ADJ && A.W) atomicAdd(&A.W[ci], wt);
           if (word_uniform<float>(ub) < A.ratio32[ci]) {
             cnt.v[CNT_REAL] += 1;
-            atomicAdd(&A.R[ci], w);
+            if (ADJ) {
+              const long long gc = in.cell_off + f.cell;
+              const double val = w * A.lambda[gc] * A.invVm[gc];
+              if (emitter >= 0) atomicAdd(&A.adj_out[in.cell_off + emitter], val);
+              else acc += val;
+            } else {
+              atomicAdd(&A.R[ci], w);
+            }
             alive = false;
           } else {
             uint32_t ua;
@@ -446,6 +474,7 @@ __global__ void __launch_bounds__(STAGED_NT, 1) sweep_staged_kernel(SweepArgs A,
         }
       }
     }
+    if (ADJ && acc != 0.0) atomicAdd(&A.adj_wall[in.wall_off + (-1 - acc_slot)], acc);
     __syncthreads();
     if (staged) {
       const double qs = wmax * 0x1p-36;
@@ -586,9 +615,9 @@ cudaError_t launch_sweep_staged(const Ctx* c, const SweepArgs& a, cudaStream_t s
   const size_t smem = (size_t)c->staged_cap * sizeof(unsigned long long);
   const int blocks = c->sm_count * c->staged_blocks_per_sm;
   switch (c->dim) {
-    case 1: sweep_staged_kernel<1><<<blocks, STAGED_NT, smem, s>>>(a, S); break;
-    case 2: sweep_staged_kernel<2><<<blocks, STAGED_NT, smem, s>>>(a, S); break;
-    default: sweep_staged_kernel<3><<<blocks, STAGED_NT, smem, s>>>(a, S); break;
+    case 1: sweep_staged_kernel<1, false><<<blocks, STAGED_NT, smem, s>>>(a, S); break;
+    case 2: sweep_staged_kernel<2, false><<<blocks, STAGED_NT, smem, s>>>(a, S); break;
+    default: sweep_staged_kernel<3, false><<<blocks, STAGED_NT, smem, s>>>(a, S); break;
   }
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   if (a.F) {
@@ -614,16 +643,49 @@ cudaError_t launch_sweep_staged(const Ctx* c, const SweepArgs& a, cudaStream_t s
   return e;
 }
 
+// Adjoint re-trace with the staged kernel over every emitter (all groups).
+cudaError_t launch_adjoint_staged(const Ctx* c, const SweepArgs& a, cudaStream_t s) {
+  StagedArgs S;
+  S.n_inst = c->n_inst;
+  S.inst_next = c->d_inst_next;
+  S.inst_end = c->d_all_end;
+  S.cost_prefix = c->d_all_cost_prefix;
+  S.cost_total = c->all_cost_total;
+  S.win_fits = c->d_win_fits;
+  S.wmax = reinterpret_cast<const double*>(c->d_wmax);
+  S.warp_grab = 256;
+  S.refill = c->opt.refill_lanes;
+  S.group_rcp = c->d_all_group_rcp;
+  S.rcp_n0 = c->d_rcp;
+  S.rcp_n1 = c->d_rcp + c->n_inst;
+  S.rcp_wall = c->d_rcp + 2 * c->n_inst;
+  cudaError_t e = cudaMemcpyAsync(c->d_inst_next, c->d_all_beg, c->n_inst * sizeof(long long),
+                                  cudaMemcpyDeviceToDevice, s);
+  if (e != cudaSuccess) return e;
+  const int blocks = c->sm_count * c->adj_blocks_per_sm;
+  switch (c->dim) {
+    case 1: sweep_staged_kernel<1, true><<<blocks, STAGED_NT, 0, s>>>(a, S); break;
+    case 2: sweep_staged_kernel<2, true><<<blocks, STAGED_NT, 0, s>>>(a, S); break;
+    default: sweep_staged_kernel<3, true><<<blocks, STAGED_NT, 0, s>>>(a, S); break;
+  }
+  return cudaGetLastError();
+}
+
 cudaError_t configure_staged(Ctx* c) {
   cudaError_t e = cudaSuccess;
   const size_t smem = (size_t)c->staged_cap * sizeof(unsigned long long);
-  if ((e = cudaFuncSetAttribute(sweep_staged_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess) return e;
-  if ((e = cudaFuncSetAttribute(sweep_staged_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess) return e;
-  if ((e = cudaFuncSetAttribute(sweep_staged_kernel<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess) return e;
+  if ((e = cudaFuncSetAttribute(sweep_staged_kernel<1, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess) return e;
+  if ((e = cudaFuncSetAttribute(sweep_staged_kernel<2, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess) return e;
+  if ((e = cudaFuncSetAttribute(sweep_staged_kernel<3, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess) return e;
   int nb = 0;
-  void* fn = c->dim == 1 ? (void*)sweep_staged_kernel<1> : (c->dim == 2 ? (void*)sweep_staged_kernel<2> : (void*)sweep_staged_kernel<3>);
+  void* fn = c->dim == 1 ? (void*)sweep_staged_kernel<1, false>
+                         : (c->dim == 2 ? (void*)sweep_staged_kernel<2, false> : (void*)sweep_staged_kernel<3, false>);
   if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, STAGED_NT, smem)) != cudaSuccess) return e;
   c->staged_blocks_per_sm = nb > 0 ? nb : 1;
+  void* fa = c->dim == 1 ? (void*)sweep_staged_kernel<1, true>
+                         : (c->dim == 2 ? (void*)sweep_staged_kernel<2, true> : (void*)sweep_staged_kernel<3, true>);
+  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fa, STAGED_NT, 0)) != cudaSuccess) return e;
+  c->adj_blocks_per_sm = nb > 0 ? nb : 1;
   return cudaSuccess;
 }
 

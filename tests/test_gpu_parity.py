@@ -226,3 +226,66 @@ def test_graph_replay_matches_plain_loop():
     ok, err = normwise_close(outs[0][0], outs[1][0], 1e-8)
     assert ok, err
     assert outs[0][1] >= outs[1][1] and outs[0][1] - outs[1][1] <= 1
+
+
+def test_fast_adjoint_matches_dense_transpose(orc):
+    # FP32 walk, staged kernel: same particles as the oracle up to rare single-precision
+    # classification differences.
+    rng = np.random.default_rng(18)
+    inst = WL.random_instance(rng, 2, (7, 6), 1, (0.1, 0.8), source=True)
+    N = 48
+    p = oracle_problem(inst, [1.0], [1.0], N, N, seed=6)
+    g = np.zeros(inst.ncells)
+    g[[8, 9, 15, 16]] = 0.25
+    gQ, gW, lam, A, Bw = orc.adjoint_dense(p, g)
+    s = gpu_solver(inst, [1.0], [1.0], N, N, seed=6, cg_rtol=1e-12)
+    gs, gw, gl = s.adjoint(cuda_T(g), tol=1e-12, max_iter=500)
+    for got, ref in ((gl, lam), (gs, gQ), (gw, gW)):
+        ok, err = normwise_close(got.cpu().numpy(), ref, 3e-3)
+        assert ok, err
+
+
+def test_adjoint_gradient_exact_for_frozen_map():
+    # With draws fixed the steady state is affine in theta = (Q, T_w) (T_ref = 0), so
+    # J = g . T* satisfies J = sum_k theta_k dJ/dtheta_k and central differences equal the
+    # adjoint gradient up to rounding and solver tolerances. Also through the autograd
+    # Function.
+    from paper_2506_09465_gb300.solver import IugkpSteady
+    rng = np.random.default_rng(21)
+    inst = WL.random_instance(rng, 2, (12, 10), 1, (0.05, 0.5), source=True)
+    N = 64
+    s = gpu_solver(inst, [1.0], [1.0], N, N, seed=2, cg_rtol=1e-12)
+    Q = torch.as_tensor(inst.source, device="cuda")
+    Tw = torch.as_tensor(inst.wall_T, device="cuda")
+    g = torch.zeros(inst.ncells, dtype=torch.float64, device="cuda")
+    g[[30, 31, 42, 43]] = 0.25
+
+    def J(Qv, Twv):
+        s.set_source(Qv)
+        s.set_wall_T(Twv)
+        T, it, res = s.solve_steady(None, 1e-13, 500)
+        return float((g * T).sum())
+
+    J0 = J(Q, Tw)
+    s.set_source(Q)
+    s.set_wall_T(Tw)
+    gs, gw, _ = s.adjoint(g, tol=1e-13, max_iter=500)
+    euler = float((Q * gs).sum() + (Tw * gw).sum())
+    assert abs(euler - J0) < 1e-9 * abs(J0)
+    h = 1e-3
+    for i in (31, 55):
+        e = torch.zeros_like(Q)
+        e[i] = h
+        fd = (J(Q + e, Tw) - J(Q - e, Tw)) / (2 * h)
+        assert abs(fd - float(gs[i])) < 1e-7 * max(1.0, abs(float(gs[i])))
+    e = torch.zeros_like(Tw)
+    e[3] = h
+    fd = (J(Q, Tw + e) - J(Q, Tw - e)) / (2 * h)
+    assert abs(fd - float(gw[3])) < 1e-7
+    # autograd
+    Qr = Q.clone().requires_grad_(True)
+    Twr = Tw.clone().requires_grad_(True)
+    T = IugkpSteady.apply(Qr, Twr, s, 1e-13, 500)
+    (g * T).sum().backward()
+    assert torch.allclose(Qr.grad, gs, rtol=1e-9, atol=1e-12)
+    assert torch.allclose(Twr.grad, gw, rtol=1e-9, atol=1e-12)
