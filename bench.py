@@ -201,6 +201,21 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+def aggregate_ranks(t_local: float, crossings_local: int, device=None):
+    """Whole-job numbers: the slowest rank's time (max) and all ranks' crossings (sum).
+    Each rank runs an independent replica, so there is no data exchange besides this."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return t_local, float(crossings_local)
+    dev = device if device is not None else torch.device("cpu")
+    tt = torch.tensor([t_local], device=dev, dtype=torch.float64)
+    dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+    cc = torch.tensor([float(crossings_local)], device=dev, dtype=torch.float64)
+    dist.all_reduce(cc)
+    return float(tt.item()), float(cc.item())
+
+
 def make_solver(wl, **opt):
     from paper_2506_09465_gb300.solver import GridSpec, Solver
     grids = [GridSpec(i.dim, i.n, i.L) for i in wl.instances]
@@ -287,17 +302,7 @@ def run_ours(args):
             torch.cuda.synchronize()
             sweep_ms.append(ev0.elapsed_time(ev1))
     sweep_counts = cnt.cpu().numpy().astype(np.int64)
-    t_local = sum(per_step_ms) / 1e3
-    t_max = t_local
-    if world > 1:
-        tt = torch.tensor([t_local], device=dev, dtype=torch.float64)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_max = float(tt.item())
-        cc = torch.tensor([crossings], device=dev, dtype=torch.float64)
-        dist.all_reduce(cc)
-        crossings_all = float(cc.item())
-    else:
-        crossings_all = float(crossings)
+    t_max, crossings_all = aggregate_ranks(sum(per_step_ms) / 1e3, crossings, dev)
     value = crossings_all / t_max
     ms_per_step = 1e3 * t_max / args.steps
 

@@ -282,6 +282,19 @@ iugkp_status iugkp_create_batch(int n, const iugkp_grid* g, const double* const*
       o->particles_per_wall_face > (1ll << 31))
     return fail(nullptr, IUGKP_EINVAL, "particles per cell / wall face must be in [nb, 2^31]");
   if (!(o->cg_rtol > 0.0) || o->cg_maxit < 1 || o->step_budget < 1) return fail(nullptr, IUGKP_EINVAL, "cg / budget options");
+  if (o->draws != IUGKP_DRAWS_FRESH && o->draws != IUGKP_DRAWS_FROZEN) return fail(nullptr, IUGKP_EINVAL, "options.draws");
+  // Field values, checked before any CUDA call.
+  for (int k = 0; k < n; ++k) {
+    long long nc = (long long)g[k].nx * (dim >= 2 ? g[k].ny : 1) * (dim >= 3 ? g[k].nz : 1);
+    for (long long i = 0; i < (long long)b->nb * nc; ++i)
+      if (!(tau[k][i] > 0.0) || !std::isfinite(tau[k][i]))
+        return fail(nullptr, IUGKP_EINVAL, "tau must be finite and > 0 (instance " + std::to_string(k) + ")");
+    for (int w = 0; w < 2 * dim; ++w)
+      if (!std::isfinite(wall_T[k][w])) return fail(nullptr, IUGKP_EINVAL, "wall temperature not finite");
+    if (source && source[k])
+      for (long long i = 0; i < nc; ++i)
+        if (!std::isfinite(source[k][i])) return fail(nullptr, IUGKP_EINVAL, "source not finite");
+  }
   if (o->refill_lanes < 0 || o->refill_lanes > 32) return fail(nullptr, IUGKP_EINVAL, "refill_lanes must be in 0..32");
 
   iugkp_ctx* ctx = new (std::nothrow) iugkp_ctx();
