@@ -97,39 +97,38 @@ def box_batch(n_inst: int = 16, seed: int = 7) -> Workload:
     return Workload(f"3D two-material boxes {sizes}", np.array([1.0]), np.array([1.0]), insts, 256, 256)
 
 
-def silicon_like_bands(n_bands: int = 40):
-    """Band-branch table for an isotropic, silicon-like dispersion (LA and TA, quadratic
-    omega(k) = v_s k - c k^2 on [0, k_max]), non-dimensionalised: group speeds relative to
-    the LA sound speed, specific heats from the linearised Bose-Einstein distribution at
-    300 K (x^2 e^x / (e^x - 1)^2 times the density of states k^2 / v_g), relaxation time
-    tau = 1 / (A omega^2) normalised so that the slowest-relaxing band centre has tau = 10
-    and the range spans three decades. Returns (C [2*n_bands], v, tau_band, omega)."""
-    branches = {"LA": (9.01, 2.0e-7), "TA": (5.23, 2.26e-7)}   # v_s [km/s], c [km/s * m] (fit shape only)
-    k_max = 1.0
+def silicon_like_bands(n_bands: int = 40, r: float = 0.1, tau_max: float = 10.0, decades: float = 3.0):
+    """Band-branch table for an isotropic, silicon-like dispersion, non-dimensionalised.
+
+    Two branches, LA (sound speed 1) and TA (5.23 / 9.01 of it, degeneracy 2), each with the
+    quadratic fit omega(k) = v_s (k - (1 - r) k^2 / 2) on k in [0, 1], so that the group speed
+    v_s (1 - (1 - r) k) falls to r v_s at the zone edge. Each branch is cut into n_bands equal
+    k-intervals; a band's specific heat is the linearised Bose-Einstein weight
+    x^2 e^x / (e^x - 1)^2 (x = omega / omega_T, omega_T = 0.5) times the density of states
+    k^2 dk times the degeneracy, normalised to sum 1. Relaxation times tau = 1 / (A omega^2)
+    with A set so that the longest is tau_max, clipped to span `decades` decades.
+    Returns (C, v, tau, omega), each of length 2 n_bands (LA bands first)."""
+    edges = np.linspace(0.0, 1.0, n_bands + 1)
+    kc = 0.5 * (edges[1:] + edges[:-1])
+    dk = np.diff(edges)
     C, v, om = [], [], []
-    for name, (vs, cc) in branches.items():
-        cn = cc * 1e7 / 2.0 * 0.9                             # curvature so that v_g(k_max) = 0.1 v_s
-        edges = np.linspace(0.0, k_max, n_bands + 1)
-        kc = 0.5 * (edges[1:] + edges[:-1])
-        dk = edges[1:] - edges[:-1]
-        omega = vs * kc - cn * vs * kc ** 2
-        vg = vs * (1.0 - 2.0 * cn * kc)
-        x = omega / omega.max() * 2.0                       # hbar omega / k_B T scale
-        cb = x ** 2 * np.exp(x) / np.expm1(x) ** 2 * kc ** 2 / vg * dk * (2.0 if name == "TA" else 1.0)
-        C.append(cb)
-        v.append(vg / 9.01)
+    for vs, deg in ((1.0, 1.0), (5.23 / 9.01, 2.0)):
+        omega = vs * (kc - 0.5 * (1.0 - r) * kc ** 2)
+        vg = vs * (1.0 - (1.0 - r) * kc)
+        x = omega / 0.5
+        C.append(deg * x ** 2 * np.exp(x) / np.expm1(x) ** 2 * kc ** 2 * dk)
+        v.append(vg)
         om.append(omega)
     C = np.concatenate(C)
+    C = C / C.sum()
     v = np.concatenate(v)
     om = np.concatenate(om)
-    C = C / C.sum()
-    tau = 1.0 / om ** 2
-    tau = tau / tau.max() * 10.0
-    tau = np.maximum(tau, tau.max() * 1e-3)
+    tau = tau_max * (om.min() / om) ** 2
+    tau = np.maximum(tau, tau_max * 10.0 ** (-decades))
     return C, v, tau, om
 
 
-def nongray_square(n=256, n_bands=40, particles=256, sigma=0.1, q0=1.0) -> Workload:
+def nongray_square(n=256, n_bands=40, particles=1024, sigma=0.1, q0=1.0) -> Workload:
     """2D non-gray square (unit side): silicon-like band table, tau uniform in space per
     band, Gaussian heat source of width sigma L at the centre, walls at T = 0."""
     C, v, tb, _ = silicon_like_bands(n_bands)
@@ -140,3 +139,32 @@ def nongray_square(n=256, n_bands=40, particles=256, sigma=0.1, q0=1.0) -> Workl
     tau = np.repeat(tb[:, None], nc, axis=1)
     inst = Instance(2, (n, n), (1.0, 1.0), tau, np.zeros(4), src.reshape(-1))
     return Workload(f"2D non-gray {n}x{n} {len(C)} band-branches", C, v, [inst], particles, particles)
+
+
+def nongray_batch(n_inst: int = 32, n_min: int = 64, n_max: int = 512, n_bands: int = 20, particles: int = 128,
+                  sigma: float = 0.1, q0: float = 1.0) -> Workload:
+    """Batch of non-gray squares of uneven sizes n_k = n_min (n_max / n_min)^(k / (n_inst - 1))
+    rounded to even numbers, each with the silicon-like table of n_bands per branch, a
+    Gaussian source of width sigma L at the centre and walls at T = 0."""
+    C, v, tb, _ = silicon_like_bands(n_bands)
+    insts = []
+    for k in range(n_inst):
+        nk = n_min * (n_max / n_min) ** (k / max(1, n_inst - 1))
+        nk = int(2 * round(nk / 2))
+        x = (np.arange(nk) + 0.5) / nk
+        X, Y = np.meshgrid(x, x, indexing="xy")
+        src = q0 * np.exp(-((X - 0.5) ** 2 + (Y - 0.5) ** 2) / (2 * sigma ** 2))
+        insts.append(Instance(2, (nk, nk), (1.0, 1.0), np.repeat(tb[:, None], nk * nk, axis=1), np.zeros(4),
+                              src.reshape(-1)))
+    return Workload(f"2D non-gray batch of {n_inst} squares {insts[0].n[0]}..{insts[-1].n[0]}", C, v, insts,
+                    particles, particles)
+
+
+def hotspot_objective(inst: Instance, frac: float = 0.1) -> np.ndarray:
+    """g with J = g . T the mean temperature over a centred square of `frac` of the area."""
+    n = inst.n[0]
+    side = max(1, int(round(n * np.sqrt(frac))))
+    lo = (n - side) // 2
+    g = np.zeros((inst.n[1], n))
+    g[lo:lo + side, lo:lo + side] = 1.0
+    return (g / g.sum()).reshape(-1)
