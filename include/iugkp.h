@@ -96,6 +96,10 @@ typedef struct {
   int use_graphs;                     /* 1: iugkp_solve_steady with frozen draws replays a
                                          CUDA graph of two iterations (one host readback per
                                          two iterations); 0: plain launches */
+  int warp_grab;                      /* staged sweep: particles a warp claims at a time
+                                         (0 = 256) */
+  int walk_k;                         /* staged sweep: crossings a lane walks between bulk
+                                         steps (0 = 16) */
 } iugkp_options;
 
 /* Fills *o with defaults: FP32 tracking, staged tallies, frozen draws, Newton on,
@@ -170,6 +174,20 @@ iugkp_status iugkp_macro(iugkp_ctx *ctx, const double *R_dev, const double *W_de
  * iteration count over instances. ENOCONV if cg_maxit is reached. */
 iugkp_status iugkp_newton_step(iugkp_ctx *ctx, const double *T_n_dev, double *T_half_inout_dev,
                                const double *R_dev, void *cuda_stream, int *cg_iters_out);
+
+/* Tuning of the staged sweep (no counterpart in the paper; the parameters change speed,
+ * not results). iugkp_autotune times full sweeps from T_dev (device FP64 [total_cells]) on
+ * the caller's stream with CUDA events, searches refill_lanes in {auto, 4, 8, 16, 24},
+ * warp_grab in {128, 256, 512} and walk_k in {8, 16, 32} one at a time, stores the fastest
+ * in the context's options and reports them in *out (may be NULL). Synchronises the stream.
+ * The context must use the staged FP32 path (EINVAL otherwise). */
+typedef struct {
+  int refill_lanes, warp_grab, walk_k;
+  double sweep_ms;      /* best sweep time found */
+  double baseline_ms;   /* sweep time with the options the context had on entry */
+} iugkp_tuning;
+iugkp_status iugkp_autotune(iugkp_ctx *ctx, const double *T_dev, unsigned epoch, iugkp_tuning *out,
+                            void *cuda_stream);
 
 /* Convergence measure of one iteration (residual definition used by the steady driver):
  * out_dev[0] = sum_i (T1_i - T0_i)^2 and out_dev[1] = sum_i T1_i^2 over all cells of all

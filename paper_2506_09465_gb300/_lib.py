@@ -35,7 +35,12 @@ class Options(ctypes.Structure):
                 ("seed", ctypes.c_ulonglong), ("epoch0", ctypes.c_uint), ("instance_base", ctypes.c_uint),
                 ("cg_rtol", ctypes.c_double), ("cg_maxit", ctypes.c_int), ("step_budget", ctypes.c_longlong),
                 ("block_threads", ctypes.c_int), ("blocks_per_sm", ctypes.c_int), ("refill_lanes", ctypes.c_int),
-                ("use_graphs", ctypes.c_int)]
+                ("use_graphs", ctypes.c_int), ("warp_grab", ctypes.c_int), ("walk_k", ctypes.c_int)]
+
+
+class Tuning(ctypes.Structure):
+    _fields_ = [("refill_lanes", ctypes.c_int), ("warp_grab", ctypes.c_int), ("walk_k", ctypes.c_int),
+                ("sweep_ms", ctypes.c_double), ("baseline_ms", ctypes.c_double)]
 
 
 class Layout(ctypes.Structure):
@@ -60,6 +65,7 @@ SIGNATURES = {
     "iugkp_macro": (_i, [_vp, _vp, _vp, _vp, _vp, _vp]),
     "iugkp_newton_step": (_i, [_vp, _vp, _vp, _vp, _vp, ctypes.POINTER(_i)]),
     "iugkp_residual": (_i, [_vp, _vp, _vp, _vp, _vp]),
+    "iugkp_autotune": (_i, [_vp, _vp, _u, ctypes.POINTER(Tuning), _vp]),
     "iugkp_solve_steady": (_i, [_vp, _vp, _d, _i, ctypes.POINTER(_i), ctypes.POINTER(_d), _vp]),
     "iugkp_adjoint": (_i, [_vp, _vp, _vp, _d, _i, _vp, _vp, _vp, _vp]),
     "iugkp_diffusion_solve_noalloc": (_i, [ctypes.POINTER(Grid), _vp, _d, _vp, _vp, _d, _i, ctypes.POINTER(_i), _vp]),

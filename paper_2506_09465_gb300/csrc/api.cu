@@ -254,6 +254,8 @@ void iugkp_default_options(iugkp_options* o) {
   o->blocks_per_sm = 0;
   o->refill_lanes = 0;
   o->use_graphs = 1;
+  o->warp_grab = 0;
+  o->walk_k = 0;
 }
 
 const char* iugkp_last_error(const iugkp_ctx* ctx) {
@@ -296,6 +298,8 @@ iugkp_status iugkp_create_batch(int n, const iugkp_grid* g, const double* const*
         if (!std::isfinite(source[k][i])) return fail(nullptr, IUGKP_EINVAL, "source not finite");
   }
   if (o->refill_lanes < 0 || o->refill_lanes > 32) return fail(nullptr, IUGKP_EINVAL, "refill_lanes must be in 0..32");
+  if (o->warp_grab < 0 || o->warp_grab > (1 << 20) || o->walk_k < 0 || o->walk_k > 4096)
+    return fail(nullptr, IUGKP_EINVAL, "warp_grab must be in 0..2^20 and walk_k in 0..4096");
 
   iugkp_ctx* ctx = new (std::nothrow) iugkp_ctx();
   if (!ctx) return fail(nullptr, IUGKP_ENOMEM, "host allocation failed");
@@ -831,6 +835,77 @@ iugkp_status iugkp_newton_step(iugkp_ctx* ctx, const double* T_n_dev, double* T_
   cudaStream_t s = (cudaStream_t)cuda_stream;
   CK(launch_newton(c, T_n_dev, T_half_inout_dev, R_dev, s), "newton");
   return pcg_status(c, s, cg_iters_out);
+}
+
+iugkp_status iugkp_autotune(iugkp_ctx* ctx, const double* T_dev, unsigned epoch, iugkp_tuning* out,
+                            void* cuda_stream) {
+  if (!ctx) return IUGKP_EINVAL;
+  Ctx* c = &ctx->c;
+  if (!T_dev) return fail(c, IUGKP_EINVAL, "T_dev is required");
+  if (!(c->opt.tally == IUGKP_TALLY_STAGED && c->opt.precision == IUGKP_TRACK_FP32))
+    return fail(c, IUGKP_EINVAL, "autotune applies to the staged FP32 sweep");
+  cudaStream_t s = (cudaStream_t)cuda_stream;
+  struct Events {  // destroyed on every return path
+    cudaEvent_t a = nullptr, b = nullptr;
+    ~Events() {
+      if (a) cudaEventDestroy(a);
+      if (b) cudaEventDestroy(b);
+    }
+  } ev;
+  CK(cudaEventCreate(&ev.a), "event");
+  CK(cudaEventCreate(&ev.b), "event");
+  // best of two sweeps (the first also warms the caches)
+  auto time_sweep = [&](double* ms) -> iugkp_status {
+    float best = 1e30f;
+    for (int rep = 0; rep < 2; ++rep) {
+      CK(cudaEventRecord(ev.a, s), "event record");
+      iugkp_status st = sweep_async(c, T_dev, epoch, c->d_R, c->d_W, c->d_F, c->d_wall, c->d_counters, s);
+      if (st != IUGKP_OK) return st;
+      CK(cudaEventRecord(ev.b, s), "event record");
+      CK(cudaEventSynchronize(ev.b), "event sync");
+      float t = 0.f;
+      CK(cudaEventElapsedTime(&t, ev.a, ev.b), "elapsed");
+      best = std::min(best, t);
+    }
+    *ms = best;
+    return IUGKP_OK;
+  };
+  iugkp_status st;
+  double base = 0.0;
+  if ((st = time_sweep(&base)) != IUGKP_OK) return st;
+  double best = base;
+  // coordinate descent, one tunable at a time, each keeping the best value found so far
+  const int refills[] = {0, 4, 8, 16, 24};
+  const int grabs[] = {128, 256, 512};
+  const int walks[] = {8, 16, 32};
+  int* knobs[3] = {&c->opt.refill_lanes, &c->opt.warp_grab, &c->opt.walk_k};
+  const int* values[3] = {refills, grabs, walks};
+  const int counts[3] = {5, 3, 3};
+  for (int kdx = 0; kdx < 3; ++kdx) {
+    int keep = *knobs[kdx];
+    for (int j = 0; j < counts[kdx]; ++j) {
+      *knobs[kdx] = values[kdx][j];
+      double t = 0.0;
+      if ((st = time_sweep(&t)) != IUGKP_OK) {
+        *knobs[kdx] = keep;
+        return st;
+      }
+      if (t < best) {
+        best = t;
+        keep = values[kdx][j];
+      }
+    }
+    *knobs[kdx] = keep;
+  }
+  if ((st = check_device(c, s)) != IUGKP_OK) return st;
+  if (out) {
+    out->refill_lanes = c->opt.refill_lanes;
+    out->warp_grab = c->opt.warp_grab > 0 ? c->opt.warp_grab : 256;
+    out->walk_k = c->opt.walk_k > 0 ? c->opt.walk_k : 16;
+    out->sweep_ms = best;
+    out->baseline_ms = base;
+  }
+  return IUGKP_OK;
 }
 
 iugkp_status iugkp_residual(iugkp_ctx* ctx, const double* T0_dev, const double* T1_dev, double* out_dev,

@@ -4,7 +4,6 @@
 namespace iugkp {
 
 constexpr int STAGED_NT = 1024;                 // threads per persistent block
-constexpr int WALK_K = 16;                      // crossings per lane between bulk steps
 
 struct StagedArgs {
   int n_inst;
@@ -16,6 +15,7 @@ struct StagedArgs {
   const double* wmax;             // [n_inst] largest |particle weight| of the sweep
   int warp_grab;                  // particles a warp claims at a time
   int refill;                     // idle lanes that trigger a refill (0: per-instance default)
+  int walk_k;                     // crossings per lane between bulk steps
   const float* group_rcp;         // [forward groups] 1 / particles per emitter
   const float* rcp_n0;            // [n_inst] 1 / n_x
   const float* rcp_n1;            // [n_inst] 1 / n_y

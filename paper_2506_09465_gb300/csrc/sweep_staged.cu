@@ -379,13 +379,13 @@ __global__ void __launch_bounds__(STAGED_NT, 1) sweep_staged_kernel(SweepArgs A,
         if (exhausted) break;
         continue;
       }
-      // ---- walk: up to WALK_K crossings per lane; lanes that stopped at a candidate
+      // ---- walk: up to walk_k crossings per lane; lanes that stopped at a candidate
       // collision are then handled together ----
       if (alive) {
         bool stop = false;
         const int cy = f.s1 * sy_cell, cz = f.s2 * sz_cell, xy = f.s1 * sy_xf, xz = f.s2 * sz_xf;
 #pragma unroll 1
-        for (int it = 0; it < WALK_K; ++it) {
+        for (int it = 0; it < S.walk_k; ++it) {
           bool ax, ay = false;
           float tmin;
           if (DIM == 1) {
@@ -600,7 +600,8 @@ cudaError_t launch_sweep_staged(const Ctx* c, const SweepArgs& a, cudaStream_t s
   S.cost_total = c->cost_total;
   S.win_fits = c->d_win_fits;
   S.wmax = reinterpret_cast<const double*>(c->d_wmax);
-  S.warp_grab = 256;
+  S.warp_grab = c->opt.warp_grab > 0 ? c->opt.warp_grab : 256;
+  S.walk_k = c->opt.walk_k > 0 ? c->opt.walk_k : 16;
   S.refill = c->opt.refill_lanes;
   S.group_rcp = c->d_group_rcp;
   S.rcp_n0 = c->d_rcp;
@@ -653,7 +654,8 @@ cudaError_t launch_adjoint_staged(const Ctx* c, const SweepArgs& a, cudaStream_t
   S.cost_total = c->all_cost_total;
   S.win_fits = c->d_win_fits;
   S.wmax = reinterpret_cast<const double*>(c->d_wmax);
-  S.warp_grab = 256;
+  S.warp_grab = c->opt.warp_grab > 0 ? c->opt.warp_grab : 256;
+  S.walk_k = c->opt.walk_k > 0 ? c->opt.walk_k : 16;
   S.refill = c->opt.refill_lanes;
   S.group_rcp = c->d_all_group_rcp;
   S.rcp_n0 = c->d_rcp;

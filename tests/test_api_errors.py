@@ -57,6 +57,8 @@ def _create(lib, dim=2, n=(4, 3), tau=None, wall=None, src=None, nb=1, **opt):
     ("too_few_particles", dict(nb=2, tau=np.full((2, 12), 0.5), particles_per_cell=1), "particles"),
     ("bad_precision", dict(precision=7), "precision"),
     ("bad_refill", dict(refill_lanes=40), "refill"),
+    ("bad_grab", dict(warp_grab=-1), "warp_grab"),
+    ("bad_walk", dict(walk_k=5000), "walk_k"),
     ("bad_cg", dict(cg_rtol=0.0), "cg"),
 ])
 def test_create_rejects_invalid_input(lib, case, kw, needle):
@@ -71,6 +73,7 @@ def test_null_arguments_rejected(lib):
     assert L.iugkp_sweep(None, None, 0, None, None, None, None, None, None) == 1
     assert L.iugkp_solve_steady(None, None, 1e-8, 10, None, None, None) == 1
     assert L.iugkp_adjoint(None, None, None, 1e-8, 10, None, None, None, None) == 1
+    assert L.iugkp_autotune(None, None, 0, None, None) == 1
     L.iugkp_destroy(None)  # no-op
 
 
@@ -86,5 +89,6 @@ def test_default_options(lib):
     o = lib.default_options()
     assert o.precision == lib.TRACK_FP32 and o.tally == lib.TALLY_STAGED and o.draws == lib.DRAWS_FROZEN
     assert o.newton == 1 and o.use_graphs == 1 and o.particles_per_cell == 1024
+    assert o.warp_grab == 0 and o.walk_k == 0 and o.refill_lanes == 0
     with pytest.raises(AttributeError):
         lib.default_options(no_such_option=1)

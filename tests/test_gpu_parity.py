@@ -213,6 +213,37 @@ def test_full_size_conservation_every_mode():
         assert abs((g["wall"].cpu().numpy().sum() - wall_em) - (emitted.sum() - R.sum())) <= 1e-6 * emitted.sum()
 
 
+def test_staged_tunables_change_speed_not_results():
+    # refill threshold, particles per warp claim and crossings per walk phase only reorder
+    # the work: the same particles take the same FP32 steps, so counters and the integer
+    # x-face window are exact and R, W, F differ by FP64 atomic order alone.
+    wl = WL.cavity_sweep(64, (0.05, 1.0))
+    rng = np.random.default_rng(8)
+    T = cuda_T(rng.uniform(0, 1, wl.total_cells))
+    ref = None
+    for kw in (dict(), dict(refill_lanes=4, warp_grab=128, walk_k=8), dict(refill_lanes=24, warp_grab=512, walk_k=32),
+               dict(refill_lanes=16, warp_grab=32, walk_k=1)):
+        s = gpu_solver(wl.instances, [1.0], [1.0], 512, 512, seed=4, **kw)
+        g = s.sweep(T, 3)
+        if ref is None:
+            ref = g
+            continue
+        assert g["counters"].cpu().tolist() == ref["counters"].cpu().tolist(), kw
+        for key in ("R", "W", "F", "wall"):
+            ok, err = normwise_close(g[key].cpu().numpy(), ref[key].cpu().numpy(), 1e-12)
+            assert ok, (kw, key, err)
+    s = gpu_solver(wl.instances, [1.0], [1.0], 512, 512, seed=4)
+    t = s.autotune(T, 3)
+    assert t["refill_lanes"] in (0, 4, 8, 16, 24) and t["warp_grab"] in (128, 256, 512)
+    assert t["walk_k"] in (8, 16, 32) and 0 < t["sweep_ms"] <= t["baseline_ms"]
+    g = s.sweep(T, 3)
+    assert g["counters"].cpu().tolist() == ref["counters"].cpu().tolist()
+    ok, err = normwise_close(g["R"].cpu().numpy(), ref["R"].cpu().numpy(), 1e-12)
+    assert ok, err
+    with pytest.raises(Exception):
+        gpu_solver(wl.instances, [1.0], [1.0], 512, 512, precision=0, tally=0, schedule=0).autotune(T)
+
+
 def test_graph_replay_matches_plain_loop():
     # Frozen draws: the CUDA-graph replay (two iterations per replay) and the plain loop
     # run the same iteration; they differ only in atomic summation order.
