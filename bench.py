@@ -37,6 +37,8 @@ def parse():
     ap.add_argument("--no-steady", action="store_true", help="skip the time-to-steady runs")
     ap.add_argument("--no-plain", action="store_true", help="skip the plain FP64 baseline")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint-gradient timing")
+    ap.add_argument("--no-tune", action="store_true", help="use the default staged-sweep parameters")
     ap.add_argument("--profile", default=None, choices=["sweep", "step"],
                     help="run --warmup then --steps sweeps (or full steps) of the workload and exit; for ncu")
     ap.add_argument("--kn", type=float, default=None, help="profile one Knudsen number only")
@@ -224,6 +226,59 @@ def make_solver(wl, **opt):
                   particles_per_wall_face=wl.particles_per_wall_face, **opt)
 
 
+def adjoint_gradient_time(WL, make_solver, tuned, with_plain):
+    """Gradient of J = mean T over a 10 %-area centred hotspot with respect to every cell's
+    source and the wall temperatures, for a batch of 32 non-gray squares (64^2 .. 512^2,
+    20 bands x 2 branches, 128 particles per cell, 2.06 M cells): forward steady solve
+    (residual 1e-8) and adjoint solve (1e-8) on the fast batched path; the same with the
+    plain FP64 path one instance at a time, and the largest relative difference of the two
+    source gradients (same particles: instance k draws with id k on both)."""
+    import numpy as np
+    import torch
+    wl = WL.nongray_batch(32, 64, 512, 20, 128)
+    g = torch.as_tensor(np.concatenate([WL.hotspot_objective(i, 0.1) for i in wl.instances]), device="cuda")
+    out = {"workload": "32 non-gray squares 64^2..512^2 (2059980 cells), 40 band-branches, 128 particles/cell",
+           "tol": 1e-8}
+    s = make_solver(wl, seed=0, **tuned)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    _, it_f, _ = s.solve_steady(None, 1e-8, 400, raise_on_noconv=False)
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
+    gs, gw, _ = s.adjoint(g, 1e-8, 400)
+    torch.cuda.synchronize()
+    t2 = time.perf_counter()
+    out.update({"fast_forward_s": t1 - t0, "fast_adjoint_s": t2 - t1, "fast_total_s": t2 - t0,
+                "forward_iters": it_f})
+    gs_fast = gs.cpu().numpy()
+    del s
+    if with_plain:
+        tf, ta, worst = 0.0, 0.0, 0.0
+        co = 0
+        for k, inst in enumerate(wl.instances):
+            w1 = WL.Workload("one", wl.C, wl.v, [inst], wl.particles_per_cell, wl.particles_per_wall_face)
+            sp = make_solver(w1, seed=0, instance_base=k, precision=0, tally=0, schedule=0, use_graphs=0)
+            gk = g[co:co + inst.ncells].contiguous()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            sp.solve_steady(None, 1e-8, 400, raise_on_noconv=False)
+            torch.cuda.synchronize()
+            t1 = time.perf_counter()
+            gsk, _, _ = sp.adjoint(gk, 1e-8, 400)
+            torch.cuda.synchronize()
+            t2 = time.perf_counter()
+            tf += t1 - t0
+            ta += t2 - t1
+            ref = gsk.cpu().numpy()
+            worst = max(worst, float(np.abs(gs_fast[co:co + inst.ncells] - ref).max() / np.abs(ref).max()))
+            co += inst.ncells
+            del sp
+        out.update({"plain_fp64_forward_s": tf, "plain_fp64_adjoint_s": ta, "plain_fp64_total_s": tf + ta,
+                    "speedup_vs_plain_fp64": (tf + ta) / out["fast_total_s"],
+                    "grad_source_max_rel_diff_vs_plain_fp64": worst})
+    return out
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -270,6 +325,12 @@ def run_ours(args):
         L.check(lib.iugkp_residual(solver.ctx, Tin.data_ptr(), Tout.data_ptr(), res_buf.data_ptr(), sp), solver.ctx)
         return it.value
 
+    # The autotuner picks refill threshold, particles per warp claim, walk length and the
+    # tally mode from timed sweeps (untimed here, like the warm-up).
+    tuning, tuned = None, {}
+    if not args.no_tune:
+        tuning = solver.autotune(T, 0, allow_k32=True)
+        tuned = {k: tuning[k] for k in ("refill_lanes", "warp_grab", "walk_k", "tally")}
     for _ in range(args.warmup):
         step(T, T_half)
     torch.cuda.synchronize()
@@ -330,7 +391,7 @@ def run_ours(args):
         # Time to steady state (res 1e-8, frozen draws, Newton): batched FP32 fast path.
         steady = {}
         if not args.no_steady:
-            s2 = make_solver(wl, seed=0)
+            s2 = make_solver(wl, seed=0, **tuned)
             torch.cuda.synchronize()
             t0 = time.perf_counter()
             Ts, its, res = s2.solve_steady(None, 1e-8, 400, raise_on_noconv=False)
@@ -373,6 +434,9 @@ def run_ours(args):
                 del sp1
             plain = {"sweep_crossings_per_s": ptot_cross / (ptot_ms / 1e3),
                      "steady_s_sequential": psteady if not args.no_steady else None, "steady_iters": piters}
+        adjoint = None
+        if not args.no_adjoint:
+            adjoint = adjoint_gradient_time(WL, make_solver, tuned, not args.no_plain)
         cpu = None
         if not args.no_cpu:
             rate, dt, cr, sample = oracle_rate(64, 12.0)
@@ -392,19 +456,23 @@ def run_ours(args):
             "config": {"workload": "2D gray cavity 128x128 unit square, Kn {0.01,0.1,1,10} batched (4 instances), "
                                    "top wall T=1, 1024 particles/cell (2^24 per instance) + 1024 per wall face; "
                                    "one step = sweep + macro + Newton(CG) + residual",
-                       "tracking": "fp32", "tallies": "fp64", "draws": "frozen",
+                       "tracking": "fp32",
+                       "tallies": "fp32 compensated (hi + exact-error word)" if tuned.get("tally") == 2 else "fp64",
+                       "draws": "frozen", "autotuned": tuning,
                        "l2": "flushed between timed steps (256 MB write)",
                        "parallelism": f"replicas x{world}" if world > 1 else "1 GPU"},
             "flights_per_step": int(flights / args.steps), "crossings_per_step": int(crossings / args.steps),
             "sweep_ms": statistics.median(sweep_ms),
             "time_to_steady": steady,
+            "adjoint_gradient": adjoint,
             "plain_fp64": plain,
             "speedup_vs_plain_fp64_sweep": (sweep_counts[3] / sw_s) / plain["sweep_crossings_per_s"] if plain else None,
             "e2e": {"value": e2e_value, "unit": "cell-crossings/s", "h2d_bytes_per_step": nc * 8,
                     "d2h_bytes_per_step": nc * 8},
             # per step: group_wmax, sweep_staged, boundary_emission, derive_last_axis,
-            # wall_absorbed, macro, newton_rhs, mgpcg, add_scaled, residual (2 kernels)
-            "gpu_launches": args.steps * 11,
+            # wall_absorbed, macro, newton_rhs, mgpcg, add_scaled, residual (2 kernels),
+            # plus three finalize passes (R, W, F) with compensated FP32 tallies
+            "gpu_launches": args.steps * (11 + (3 if tuned.get("tally") == 2 else 0)),
             "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": peak_ops / 1e12,
                          "unit": "Tops/s (FP32+INT32 lane ops)", "frac": achieved / peak_ops, "traffic": None,
                          "kernel": "sweep", "peak_source": "152 SMs x 128 lanes x 2.07 GHz (unit counts and clock)"},

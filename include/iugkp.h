@@ -65,7 +65,7 @@ typedef struct {
 } iugkp_bands;
 
 enum { IUGKP_TRACK_FP64 = 0, IUGKP_TRACK_FP32 = 1 };
-enum { IUGKP_TALLY_FP64 = 0, IUGKP_TALLY_STAGED = 1 };
+enum { IUGKP_TALLY_FP64 = 0, IUGKP_TALLY_STAGED = 1, IUGKP_TALLY_STAGED_K32 = 2 };
 enum { IUGKP_DRAWS_FRESH = 0, IUGKP_DRAWS_FROZEN = 1 };
 enum { IUGKP_SCHED_PLAIN = 0, IUGKP_SCHED_PERSISTENT = 1 };
 
@@ -73,8 +73,14 @@ typedef struct {
   int precision;      /* IUGKP_TRACK_FP64: positions, directions and paths in FP64;
                          IUGKP_TRACK_FP32: in FP32 (weights and tallies stay FP64). */
   int tally;          /* IUGKP_TALLY_FP64: every face / deposit tally is a global FP64
-                         atomic; IUGKP_TALLY_STAGED: face tallies are accumulated per
-                         block in shared memory (FP32) and flushed to FP64. */
+                         atomic; IUGKP_TALLY_STAGED (FP32 tracking only): x-face tallies
+                         are exact 64-bit fixed-point sums in a per-block shared-memory
+                         window flushed to FP64, last-axis faces and walls follow from
+                         per-cell conservation, deposits R, W are FP64 atomics;
+                         IUGKP_TALLY_STAGED_K32: as STAGED, but deposits and the face
+                         tallies that miss the window are compensated FP32 sums (a high
+                         word plus a word that collects each addition's exact rounding
+                         error), turned into FP64 after the sweep. Outputs stay FP64. */
   int draws;          /* IUGKP_DRAWS_FRESH: epoch = epoch0 + iteration;
                          IUGKP_DRAWS_FROZEN: epoch = epoch0 every iteration. */
   int newton;         /* 0: plain iteration; 1: inexact-Newton diffusion correction. */
@@ -175,19 +181,21 @@ iugkp_status iugkp_macro(iugkp_ctx *ctx, const double *R_dev, const double *W_de
 iugkp_status iugkp_newton_step(iugkp_ctx *ctx, const double *T_n_dev, double *T_half_inout_dev,
                                const double *R_dev, void *cuda_stream, int *cg_iters_out);
 
-/* Tuning of the staged sweep (no counterpart in the paper; the parameters change speed,
- * not results). iugkp_autotune times full sweeps from T_dev (device FP64 [total_cells]) on
- * the caller's stream with CUDA events, searches refill_lanes in {auto, 4, 8, 16, 24},
- * warp_grab in {128, 256, 512} and walk_k in {8, 16, 32} one at a time, stores the fastest
- * in the context's options and reports them in *out (may be NULL). Synchronises the stream.
- * The context must use the staged FP32 path (EINVAL otherwise). */
+/* Tuning of the staged sweep (no counterpart in the paper; refill, claim size and walk
+ * length change speed, not results; the tally mode changes results by rounding only).
+ * iugkp_autotune times full sweeps from T_dev (device FP64 [total_cells]) on the caller's
+ * stream with CUDA events, searches refill_lanes in {auto, 4, 8, 16, 24}, warp_grab in
+ * {128, 256, 512}, walk_k in {8, 16, 32} and, if allow_k32, tally in {STAGED, STAGED_K32}
+ * one at a time, stores the fastest in the context's options and reports them in *out
+ * (may be NULL). Synchronises the stream. The context must use FP32 tracking with a staged
+ * tally mode (EINVAL otherwise). */
 typedef struct {
-  int refill_lanes, warp_grab, walk_k;
+  int refill_lanes, warp_grab, walk_k, tally;
   double sweep_ms;      /* best sweep time found */
   double baseline_ms;   /* sweep time with the options the context had on entry */
 } iugkp_tuning;
-iugkp_status iugkp_autotune(iugkp_ctx *ctx, const double *T_dev, unsigned epoch, iugkp_tuning *out,
-                            void *cuda_stream);
+iugkp_status iugkp_autotune(iugkp_ctx *ctx, const double *T_dev, unsigned epoch, int allow_k32,
+                            iugkp_tuning *out, void *cuda_stream);
 
 /* Convergence measure of one iteration (residual definition used by the steady driver):
  * out_dev[0] = sum_i (T1_i - T0_i)^2 and out_dev[1] = sum_i T1_i^2 over all cells of all

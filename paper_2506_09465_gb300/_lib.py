@@ -13,7 +13,7 @@ STATUS = {0: "IUGKP_OK", 1: "IUGKP_EINVAL", 2: "IUGKP_ENOMEM", 3: "IUGKP_ECUDA",
           5: "IUGKP_EBUDGET", 6: "IUGKP_EDEVICE"}
 
 TRACK_FP64, TRACK_FP32 = 0, 1
-TALLY_FP64, TALLY_STAGED = 0, 1
+TALLY_FP64, TALLY_STAGED, TALLY_STAGED_K32 = 0, 1, 2
 DRAWS_FRESH, DRAWS_FROZEN = 0, 1
 SCHED_PLAIN, SCHED_PERSISTENT = 0, 1
 FIELD_SOURCE, FIELD_WALL_T = 0, 1
@@ -40,7 +40,7 @@ class Options(ctypes.Structure):
 
 class Tuning(ctypes.Structure):
     _fields_ = [("refill_lanes", ctypes.c_int), ("warp_grab", ctypes.c_int), ("walk_k", ctypes.c_int),
-                ("sweep_ms", ctypes.c_double), ("baseline_ms", ctypes.c_double)]
+                ("tally", ctypes.c_int), ("sweep_ms", ctypes.c_double), ("baseline_ms", ctypes.c_double)]
 
 
 class Layout(ctypes.Structure):
@@ -65,7 +65,7 @@ SIGNATURES = {
     "iugkp_macro": (_i, [_vp, _vp, _vp, _vp, _vp, _vp]),
     "iugkp_newton_step": (_i, [_vp, _vp, _vp, _vp, _vp, ctypes.POINTER(_i)]),
     "iugkp_residual": (_i, [_vp, _vp, _vp, _vp, _vp]),
-    "iugkp_autotune": (_i, [_vp, _vp, _u, ctypes.POINTER(Tuning), _vp]),
+    "iugkp_autotune": (_i, [_vp, _vp, _u, _i, ctypes.POINTER(Tuning), _vp]),
     "iugkp_solve_steady": (_i, [_vp, _vp, _d, _i, ctypes.POINTER(_i), ctypes.POINTER(_d), _vp]),
     "iugkp_adjoint": (_i, [_vp, _vp, _vp, _d, _i, _vp, _vp, _vp, _vp]),
     "iugkp_diffusion_solve_noalloc": (_i, [ctypes.POINTER(Grid), _vp, _d, _vp, _vp, _d, _i, ctypes.POINTER(_i), _vp]),

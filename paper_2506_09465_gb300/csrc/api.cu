@@ -43,6 +43,8 @@ iugkp_status cuda_fail(Ctx* c, cudaError_t e, const char* what) {
 
 namespace {
 
+iugkp_status ensure_k32(Ctx* c);
+
 // Largest-remainder split of N over weights r (r > 0, N >= nb): one particle per band
 // first, the remaining N - nb in proportion to r, leftovers to the largest fractional
 // parts (lower band first on ties).
@@ -103,7 +105,7 @@ void free_all(Ctx* c) {
                   c->d_mg_cy, c->d_mg_cz, c->d_mg_cinv, c->d_mg_b, c->d_mg_x, c->d_mg_t, c->d_mg_r,
                   c->d_inst_beg, c->d_inst_end, c->d_inst_next, c->d_cost_prefix, c->d_win_fits, c->d_wmax,
                   c->d_group_rcp, c->d_rcp, c->d_wall_unit, c->d_all_beg, c->d_all_end, c->d_all_cost_prefix,
-                  c->d_all_group_rcp};
+                  c->d_all_group_rcp, c->d_R32, c->d_W32, c->d_F32};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (c->h_pinned) cudaFreeHost(c->h_pinned);
@@ -279,7 +281,10 @@ iugkp_status iugkp_create_batch(int n, const iugkp_grid* g, const double* const*
       return fail(nullptr, IUGKP_EINVAL, "grid " + std::to_string(k) + " invalid (dim, sizes, lengths) or NULL field");
   if (o->precision != IUGKP_TRACK_FP32 && o->precision != IUGKP_TRACK_FP64)
     return fail(nullptr, IUGKP_EINVAL, "options.precision");
-  if (o->tally != IUGKP_TALLY_FP64 && o->tally != IUGKP_TALLY_STAGED) return fail(nullptr, IUGKP_EINVAL, "options.tally");
+  if (o->tally != IUGKP_TALLY_FP64 && o->tally != IUGKP_TALLY_STAGED && o->tally != IUGKP_TALLY_STAGED_K32)
+    return fail(nullptr, IUGKP_EINVAL, "options.tally");
+  if (o->tally == IUGKP_TALLY_STAGED_K32 && o->precision != IUGKP_TRACK_FP32)
+    return fail(nullptr, IUGKP_EINVAL, "options.tally: compensated FP32 tallies need FP32 tracking");
   if (o->particles_per_cell < b->nb || o->particles_per_wall_face < b->nb || o->particles_per_cell > (1ll << 31) ||
       o->particles_per_wall_face > (1ll << 31))
     return fail(nullptr, IUGKP_EINVAL, "particles per cell / wall face must be in [nb, 2^31]");
@@ -625,6 +630,10 @@ iugkp_status iugkp_create_batch(int n, const iugkp_grid* g, const double* const*
     fail(c, IUGKP_ECUDA, "set-up of error word / pinned buffer");
     return bail(IUGKP_ECUDA);
   }
+  if (c->opt.tally == IUGKP_TALLY_STAGED_K32) {
+    iugkp_status ks = ensure_k32(c);
+    if (ks != IUGKP_OK) return bail(ks);
+  }
   *out = ctx;
   return IUGKP_OK;
 }
@@ -704,18 +713,35 @@ iugkp_status check_device(Ctx* c, cudaStream_t s) {
   return IUGKP_OK;
 }
 
+bool staged_path(const Ctx* c) {
+  return c->opt.tally != IUGKP_TALLY_FP64 && c->opt.precision == IUGKP_TRACK_FP32 && c->fwd_particles < (1ll << 31);
+}
+
+// Buffers of the compensated FP32 tallies; allocated outside any stream capture.
+iugkp_status ensure_k32(Ctx* c) {
+  if (c->d_R32) return IUGKP_OK;
+  const size_t bc = (size_t)c->nb * c->total_cells;
+  iugkp_status st;
+  if ((st = dalloc(c, &c->d_R32, bc)) != IUGKP_OK) return st;
+  if ((st = dalloc(c, &c->d_W32, bc)) != IUGKP_OK) return st;
+  return dalloc(c, &c->d_F32, (size_t)c->total_faces);
+}
+
 iugkp_status sweep_async(Ctx* c, const double* T, unsigned epoch, double* R, double* W, double* F, double* wall,
                          unsigned long long* counters, cudaStream_t s) {
   const size_t bc = (size_t)c->nb * c->total_cells;
-  CK(cudaMemsetAsync(R, 0, bc * sizeof(double), s), "clear R");
-  if (W) CK(cudaMemsetAsync(W, 0, bc * sizeof(double), s), "clear W");
+  const bool staged = staged_path(c);
+  const bool k32 = staged && c->opt.tally == IUGKP_TALLY_STAGED_K32;
+  if (k32 && !c->d_R32) return fail(c, IUGKP_EINVAL, "compensated tally buffers missing");
+  if (!k32) {  // the compensated mode writes R and W whole after the sweep
+    CK(cudaMemsetAsync(R, 0, bc * sizeof(double), s), "clear R");
+    if (W) CK(cudaMemsetAsync(W, 0, bc * sizeof(double), s), "clear W");
+  }
   if (F) CK(cudaMemsetAsync(F, 0, c->total_faces * sizeof(double), s), "clear F");
   if (wall) CK(cudaMemsetAsync(wall, 0, c->total_walls * sizeof(double), s), "clear wall");
   unsigned long long* cnt = counters ? counters : c->d_counters;
   CK(cudaMemsetAsync(cnt, 0, CNT_N * sizeof(unsigned long long), s), "clear counters");
   CK(cudaMemsetAsync(c->d_work_counter, 0, sizeof(unsigned long long), s), "clear work counter");
-  const bool staged = c->opt.tally == IUGKP_TALLY_STAGED && c->opt.precision == IUGKP_TRACK_FP32 &&
-                      c->fwd_particles < (1ll << 31);
   if (staged && wall && !F) {  // the staged sweep derives wall tallies from the face tallies
     F = c->d_F;
     CK(cudaMemsetAsync(F, 0, c->total_faces * sizeof(double), s), "clear F");
@@ -837,13 +863,16 @@ iugkp_status iugkp_newton_step(iugkp_ctx* ctx, const double* T_n_dev, double* T_
   return pcg_status(c, s, cg_iters_out);
 }
 
-iugkp_status iugkp_autotune(iugkp_ctx* ctx, const double* T_dev, unsigned epoch, iugkp_tuning* out,
+iugkp_status iugkp_autotune(iugkp_ctx* ctx, const double* T_dev, unsigned epoch, int allow_k32, iugkp_tuning* out,
                             void* cuda_stream) {
   if (!ctx) return IUGKP_EINVAL;
   Ctx* c = &ctx->c;
   if (!T_dev) return fail(c, IUGKP_EINVAL, "T_dev is required");
-  if (!(c->opt.tally == IUGKP_TALLY_STAGED && c->opt.precision == IUGKP_TRACK_FP32))
-    return fail(c, IUGKP_EINVAL, "autotune applies to the staged FP32 sweep");
+  if (!staged_path(c)) return fail(c, IUGKP_EINVAL, "autotune applies to the staged FP32 sweep");
+  if (allow_k32) {
+    iugkp_status ks = ensure_k32(c);
+    if (ks != IUGKP_OK) return ks;
+  }
   cudaStream_t s = (cudaStream_t)cuda_stream;
   struct Events {  // destroyed on every return path
     cudaEvent_t a = nullptr, b = nullptr;
@@ -878,10 +907,11 @@ iugkp_status iugkp_autotune(iugkp_ctx* ctx, const double* T_dev, unsigned epoch,
   const int refills[] = {0, 4, 8, 16, 24};
   const int grabs[] = {128, 256, 512};
   const int walks[] = {8, 16, 32};
-  int* knobs[3] = {&c->opt.refill_lanes, &c->opt.warp_grab, &c->opt.walk_k};
-  const int* values[3] = {refills, grabs, walks};
-  const int counts[3] = {5, 3, 3};
-  for (int kdx = 0; kdx < 3; ++kdx) {
+  const int tallies[] = {IUGKP_TALLY_STAGED, IUGKP_TALLY_STAGED_K32};
+  int* knobs[4] = {&c->opt.refill_lanes, &c->opt.warp_grab, &c->opt.walk_k, &c->opt.tally};
+  const int* values[4] = {refills, grabs, walks, tallies};
+  const int counts[4] = {5, 3, 3, 2};
+  for (int kdx = 0; kdx < (allow_k32 ? 4 : 3); ++kdx) {
     int keep = *knobs[kdx];
     for (int j = 0; j < counts[kdx]; ++j) {
       *knobs[kdx] = values[kdx][j];
@@ -902,6 +932,7 @@ iugkp_status iugkp_autotune(iugkp_ctx* ctx, const double* T_dev, unsigned epoch,
     out->refill_lanes = c->opt.refill_lanes;
     out->warp_grab = c->opt.warp_grab > 0 ? c->opt.warp_grab : 256;
     out->walk_k = c->opt.walk_k > 0 ? c->opt.walk_k : 16;
+    out->tally = c->opt.tally;
     out->sweep_ms = best;
     out->baseline_ms = base;
   }
@@ -1042,7 +1073,7 @@ namespace {
 // The adjoint re-trace: the staged kernel for the FP32 walk with staged tallies (the
 // fast path), else the plain one-thread-per-particle kernel.
 cudaError_t adjoint_sweep(Ctx* c, const SweepArgs& a, cudaStream_t s) {
-  if (c->opt.tally == IUGKP_TALLY_STAGED && c->opt.precision == IUGKP_TRACK_FP32 && c->total_particles < (1ll << 31))
+  if (c->opt.tally != IUGKP_TALLY_FP64 && c->opt.precision == IUGKP_TRACK_FP32 && c->total_particles < (1ll << 31))
     return launch_adjoint_staged(c, a, s);
   return launch_adjoint(c, a, s);
 }

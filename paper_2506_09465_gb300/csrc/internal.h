@@ -97,6 +97,9 @@ struct Ctx {
   double* d_W = nullptr;
   double* d_F = nullptr;
   double* d_wall = nullptr;
+  float2* d_R32 = nullptr;       // compensated FP32 tallies {hi, err} (allocated on first use)
+  float2* d_W32 = nullptr;
+  float2* d_F32 = nullptr;
   double* d_red = nullptr;       // reduction scratch
   unsigned long long* d_counters = nullptr;
   unsigned long long* d_work_counter = nullptr;

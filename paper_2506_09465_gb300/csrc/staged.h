@@ -20,6 +20,10 @@ struct StagedArgs {
   const float* rcp_n0;            // [n_inst] 1 / n_x
   const float* rcp_n1;            // [n_inst] 1 / n_y
   const float* rcp_wall;          // [n_inst * 3] 1 / (cells along the first tangential axis of each wall)
+  // compensated FP32 tallies (IUGKP_TALLY_STAGED_K32): {high word, error word} per entry
+  float2* R32;                    // [nb * total_cells]
+  float2* W32;                    // [nb * total_cells] or null
+  float2* F32;                    // [total_faces] face tallies that miss the window, or null
 };
 
 }  // namespace iugkp

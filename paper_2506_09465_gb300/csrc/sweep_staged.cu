@@ -283,7 +283,32 @@ __device__ __forceinline__ bool staged_emit(const SweepArgs& A, const StagedArgs
 // ADJ = true: the adjoint re-trace (see adjoint.cu for the map it transposes): no tallies;
 // a real collision gathers c_p lambda[stop] / (V m_stop) into the particle's emitter cell,
 // or into its wall, accumulated per lane while the lane stays on one wall group.
-template <int DIM, bool ADJ>
+// Compensated FP32 tally. The atomic returns the value it added to, so the exact rounding
+// error of the stored sum is known locally (Knuth's TwoSum, six FP32 operations); that error
+// and the low part of the FP64 addend go to the companion word. After n additions the pair
+// holds the sum to about n 2^-48 relative. (atom.add.f32 flushes subnormal results to zero:
+// an absolute error below 2^-126 per addition, far under the tally scale.)
+__device__ __forceinline__ void tally_k32(float2* p, double x) {
+  const float xh = __double2float_rn(x);
+  const float xl = __double2float_rn(x - (double)xh);
+  const float old = atomicAdd(&p->x, xh);
+  const float sum = __fadd_rn(old, xh);
+  const float bv = __fsub_rn(sum, old);
+  const float err = __fadd_rn(__fsub_rn(old, __fsub_rn(sum, bv)), __fsub_rn(xh, bv));
+  const float lo = __fadd_rn(err, xl);
+  if (lo != 0.f) atomicAdd(&p->y, lo);
+}
+
+// FP64 value of compensated tallies: dst = hi + lo (add = 0) or dst += hi + lo (add = 1).
+__global__ void k32_finalize_kernel(const float2* src, double* dst, long long n, int add) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const float2 v = src[i];
+    const double x = (double)v.x + (double)v.y;
+    dst[i] = add ? dst[i] + x : x;
+  }
+}
+
+template <int DIM, bool ADJ, bool K32>
 __global__ void __launch_bounds__(STAGED_NT, 1) sweep_staged_kernel(SweepArgs A, StagedArgs S) {
   extern __shared__ unsigned long long win[];
   __shared__ int s_inst;
@@ -408,12 +433,16 @@ __global__ void __launch_bounds__(STAGED_NT, 1) sweep_staged_kernel(SweepArgs A,
           if (useF) {
             if (ax) {
               if (staged) atomicAdd(&win[f.xface], qwx);
+              else if (K32) tally_k32(&S.F32[face_off + f.xface], f.s0 > 0 ? w : -w);
               else atomicAdd(&A.F[face_off + f.xface], f.s0 > 0 ? w : -w);
             } else if (ay && (DIM == 3 || (f.s1 < 0 && f.i1 == 0))) {
               const int up = f.s1 > 0 ? 1 : 0;
-              atomicAdd(&A.F[face_off + fax1 + f.cell + (long long)n0 * f.i2 + (long long)n0 * up], up ? w : -w);
+              const long long fi = face_off + fax1 + f.cell + (long long)n0 * f.i2 + (long long)n0 * up;
+              if (K32) tally_k32(&S.F32[fi], up ? w : -w);
+              else atomicAdd(&A.F[fi], up ? w : -w);
             } else if (az && f.s2 < 0 && f.i2 == 0) {
-              atomicAdd(&A.F[face_off + fax2 + f.cell], -w);
+              if (K32) tally_k32(&S.F32[face_off + fax2 + f.cell], -w);
+              else atomicAdd(&A.F[face_off + fax2 + f.cell], -w);
             }
           }
           bool out;
@@ -454,7 +483,8 @@ __global__ void __launch_bounds__(STAGED_NT, 1) sweep_staged_kernel(SweepArgs A,
           // probability tau_maj / tau(x)
           cnt.v[CNT_CANDIDATES] += 1;
           const long long ci = bcbase + f.cell;
-          if (!ADJ && A.W) atomicAdd(&A.W[ci], wt);
+          if (!ADJ && K32 && S.W32) tally_k32(&S.W32[ci], wt);
+          else if (!ADJ && !K32 && A.W) atomicAdd(&A.W[ci], wt);
           if (word_uniform<float>(ub) < A.ratio32[ci]) {
             cnt.v[CNT_REAL] += 1;
             if (ADJ) {
@@ -462,6 +492,8 @@ __global__ void __launch_bounds__(STAGED_NT, 1) sweep_staged_kernel(SweepArgs A,
               const double val = w * A.lambda[gc] * A.invVm[gc];
               if (emitter >= 0) atomicAdd(&A.adj_out[in.cell_off + emitter], val);
               else acc += val;
+            } else if (K32) {
+              tally_k32(&S.R32[ci], w);
             } else {
               atomicAdd(&A.R[ci], w);
             }
@@ -615,10 +647,32 @@ cudaError_t launch_sweep_staged(const Ctx* c, const SweepArgs& a, cudaStream_t s
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   const size_t smem = (size_t)c->staged_cap * sizeof(unsigned long long);
   const int blocks = c->sm_count * c->staged_blocks_per_sm;
-  switch (c->dim) {
-    case 1: sweep_staged_kernel<1, false><<<blocks, STAGED_NT, smem, s>>>(a, S); break;
-    case 2: sweep_staged_kernel<2, false><<<blocks, STAGED_NT, smem, s>>>(a, S); break;
-    default: sweep_staged_kernel<3, false><<<blocks, STAGED_NT, smem, s>>>(a, S); break;
+  const bool k32 = c->opt.tally == IUGKP_TALLY_STAGED_K32;
+  S.R32 = k32 ? c->d_R32 : nullptr;
+  S.W32 = k32 && a.W ? c->d_W32 : nullptr;
+  S.F32 = k32 && a.F ? c->d_F32 : nullptr;
+  if (k32) {
+    const size_t bc = (size_t)c->nb * c->total_cells;
+    if ((e = cudaMemsetAsync(c->d_R32, 0, bc * sizeof(float2), s)) != cudaSuccess) return e;
+    if (a.W && (e = cudaMemsetAsync(c->d_W32, 0, bc * sizeof(float2), s)) != cudaSuccess) return e;
+    if (a.F && (e = cudaMemsetAsync(c->d_F32, 0, (size_t)c->total_faces * sizeof(float2), s)) != cudaSuccess)
+      return e;
+    switch (c->dim) {
+      case 1: sweep_staged_kernel<1, false, true><<<blocks, STAGED_NT, smem, s>>>(a, S); break;
+      case 2: sweep_staged_kernel<2, false, true><<<blocks, STAGED_NT, smem, s>>>(a, S); break;
+      default: sweep_staged_kernel<3, false, true><<<blocks, STAGED_NT, smem, s>>>(a, S); break;
+    }
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    const int fb = c->sm_count * 4;
+    k32_finalize_kernel<<<fb, 256, 0, s>>>(c->d_R32, a.R, (long long)bc, 0);
+    if (a.W) k32_finalize_kernel<<<fb, 256, 0, s>>>(c->d_W32, a.W, (long long)bc, 0);
+    if (a.F) k32_finalize_kernel<<<fb, 256, 0, s>>>(c->d_F32, a.F, c->total_faces, 1);
+  } else {
+    switch (c->dim) {
+      case 1: sweep_staged_kernel<1, false, false><<<blocks, STAGED_NT, smem, s>>>(a, S); break;
+      case 2: sweep_staged_kernel<2, false, false><<<blocks, STAGED_NT, smem, s>>>(a, S); break;
+      default: sweep_staged_kernel<3, false, false><<<blocks, STAGED_NT, smem, s>>>(a, S); break;
+    }
   }
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   if (a.F) {
@@ -664,11 +718,12 @@ cudaError_t launch_adjoint_staged(const Ctx* c, const SweepArgs& a, cudaStream_t
   cudaError_t e = cudaMemcpyAsync(c->d_inst_next, c->d_all_beg, c->n_inst * sizeof(long long),
                                   cudaMemcpyDeviceToDevice, s);
   if (e != cudaSuccess) return e;
+  S.R32 = S.W32 = S.F32 = nullptr;
   const int blocks = c->sm_count * c->adj_blocks_per_sm;
   switch (c->dim) {
-    case 1: sweep_staged_kernel<1, true><<<blocks, STAGED_NT, 0, s>>>(a, S); break;
-    case 2: sweep_staged_kernel<2, true><<<blocks, STAGED_NT, 0, s>>>(a, S); break;
-    default: sweep_staged_kernel<3, true><<<blocks, STAGED_NT, 0, s>>>(a, S); break;
+    case 1: sweep_staged_kernel<1, true, false><<<blocks, STAGED_NT, 0, s>>>(a, S); break;
+    case 2: sweep_staged_kernel<2, true, false><<<blocks, STAGED_NT, 0, s>>>(a, S); break;
+    default: sweep_staged_kernel<3, true, false><<<blocks, STAGED_NT, 0, s>>>(a, S); break;
   }
   return cudaGetLastError();
 }
@@ -676,16 +731,18 @@ cudaError_t launch_adjoint_staged(const Ctx* c, const SweepArgs& a, cudaStream_t
 cudaError_t configure_staged(Ctx* c) {
   cudaError_t e = cudaSuccess;
   const size_t smem = (size_t)c->staged_cap * sizeof(unsigned long long);
-  if ((e = cudaFuncSetAttribute(sweep_staged_kernel<1, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess) return e;
-  if ((e = cudaFuncSetAttribute(sweep_staged_kernel<2, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess) return e;
-  if ((e = cudaFuncSetAttribute(sweep_staged_kernel<3, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess) return e;
-  int nb = 0;
-  void* fn = c->dim == 1 ? (void*)sweep_staged_kernel<1, false>
-                         : (c->dim == 2 ? (void*)sweep_staged_kernel<2, false> : (void*)sweep_staged_kernel<3, false>);
-  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, STAGED_NT, smem)) != cudaSuccess) return e;
+  const void* fwd[6] = {(const void*)sweep_staged_kernel<1, false, false>, (const void*)sweep_staged_kernel<2, false, false>,
+                        (const void*)sweep_staged_kernel<3, false, false>, (const void*)sweep_staged_kernel<1, false, true>,
+                        (const void*)sweep_staged_kernel<2, false, true>, (const void*)sweep_staged_kernel<3, false, true>};
+  for (const void* f : fwd)
+    if ((e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess) return e;
+  int nb = 0, nk = 0;
+  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fwd[c->dim - 1], STAGED_NT, smem)) != cudaSuccess) return e;
+  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nk, fwd[c->dim + 2], STAGED_NT, smem)) != cudaSuccess) return e;
+  nb = std::min(nb, nk);  // one grid size for both tally modes
   c->staged_blocks_per_sm = nb > 0 ? nb : 1;
-  void* fa = c->dim == 1 ? (void*)sweep_staged_kernel<1, true>
-                         : (c->dim == 2 ? (void*)sweep_staged_kernel<2, true> : (void*)sweep_staged_kernel<3, true>);
+  void* fa = c->dim == 1 ? (void*)sweep_staged_kernel<1, true, false>
+                         : (c->dim == 2 ? (void*)sweep_staged_kernel<2, true, false> : (void*)sweep_staged_kernel<3, true, false>);
   if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fa, STAGED_NT, 0)) != cudaSuccess) return e;
   c->adj_blocks_per_sm = nb > 0 ? nb : 1;
   return cudaSuccess;

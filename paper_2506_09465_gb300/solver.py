@@ -163,11 +163,12 @@ class Solver:
                                        _stream_ptr(stream)), self.ctx)
         return gs, gw, lam
 
-    def autotune(self, T, epoch=0, stream=None):
+    def autotune(self, T, epoch=0, allow_k32=False, stream=None):
         """Times the staged sweep over its tunables and keeps the fastest (see iugkp_autotune)."""
         t = L.Tuning()
-        L.check(self.lib.iugkp_autotune(self.ctx, _dptr(T), epoch, ctypes.byref(t), _stream_ptr(stream)), self.ctx)
-        return {"refill_lanes": t.refill_lanes, "warp_grab": t.warp_grab, "walk_k": t.walk_k,
+        L.check(self.lib.iugkp_autotune(self.ctx, _dptr(T), epoch, int(allow_k32), ctypes.byref(t),
+                                        _stream_ptr(stream)), self.ctx)
+        return {"refill_lanes": t.refill_lanes, "warp_grab": t.warp_grab, "walk_k": t.walk_k, "tally": t.tally,
                 "sweep_ms": t.sweep_ms, "baseline_ms": t.baseline_ms}
 
     def set_source(self, Q, stream=None):

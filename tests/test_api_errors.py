@@ -56,6 +56,8 @@ def _create(lib, dim=2, n=(4, 3), tau=None, wall=None, src=None, nb=1, **opt):
     ("zero_cells", dict(n=(0, 3)), "grid"),
     ("too_few_particles", dict(nb=2, tau=np.full((2, 12), 0.5), particles_per_cell=1), "particles"),
     ("bad_precision", dict(precision=7), "precision"),
+    ("bad_tally", dict(tally=3), "tally"),
+    ("k32_needs_fp32", dict(tally=2, precision=0), "tally"),
     ("bad_refill", dict(refill_lanes=40), "refill"),
     ("bad_grab", dict(warp_grab=-1), "warp_grab"),
     ("bad_walk", dict(walk_k=5000), "walk_k"),
@@ -73,7 +75,7 @@ def test_null_arguments_rejected(lib):
     assert L.iugkp_sweep(None, None, 0, None, None, None, None, None, None) == 1
     assert L.iugkp_solve_steady(None, None, 1e-8, 10, None, None, None) == 1
     assert L.iugkp_adjoint(None, None, None, 1e-8, 10, None, None, None, None) == 1
-    assert L.iugkp_autotune(None, None, 0, None, None) == 1
+    assert L.iugkp_autotune(None, None, 0, 0, None, None) == 1
     L.iugkp_destroy(None)  # no-op
 
 

@@ -100,6 +100,31 @@ def test_box_batch_conserves_and_matches_standalone(orc):
     assert ok, err
 
 
+def test_box_batch_compensated_fp32_tallies_against_fp64():
+    # The 16-box batch with compensated FP32 tallies against FP64 tallies (same particles):
+    # equal counters, tallies within rounding, and the steady state of the smallest box
+    # within 5e-4 of its span of the FP64-tally solve.
+    wl = WL.box_batch(16)
+    T = torch.zeros(wl.total_cells, dtype=torch.float64, device="cuda")
+    g = []
+    for tally in (1, 2):
+        s = gpu_solver(wl.instances, wl.C, wl.v, 256, 256, seed=7, instance_base=100, tally=tally)
+        g.append(s.sweep(T, 0))
+    assert g[0]["counters"].cpu().tolist() == g[1]["counters"].cpu().tolist()
+    for key in ("R", "W", "F", "wall"):
+        ok, err = normwise_close(g[1][key].cpu().numpy(), g[0][key].cpu().numpy(), 1e-9)
+        assert ok, (key, err)
+    small = [wl.instances[0], wl.instances[3]]
+    Ts = []
+    for tally in (1, 2):
+        s = gpu_solver(small, wl.C, wl.v, 256, 256, seed=7, tally=tally)
+        Tt, it, res = s.solve_steady(None, 1e-8, 300)
+        assert res <= 1e-8
+        Ts.append(Tt.cpu().numpy())
+    span = Ts[0].max() - Ts[0].min()
+    assert np.abs(Ts[1] - Ts[0]).max() <= 5e-4 * span
+
+
 def test_nongray_adjoint_dense_transpose_8x8(orc):
     # 8 x 8, 40 band-branches: re-trace adjoint (FP64) = dense transpose of the oracle map.
     C, v, tb, _ = WL.silicon_like_bands(20)

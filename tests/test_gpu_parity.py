@@ -55,7 +55,7 @@ def test_sweep_fp64_matches_oracle(orc, name, insts, C, v):
         assert g["counters"].cpu().numpy().tolist() == r.counters.astype(np.int64).tolist()
 
 
-@pytest.mark.parametrize("tally", [0, 1])
+@pytest.mark.parametrize("tally", [0, 1, 2])
 @pytest.mark.parametrize("dim", [1, 2, 3])
 def test_sweep_fp32_tracks_same_particles(orc, dim, tally):
     rng = np.random.default_rng(30 + dim)
@@ -65,7 +65,7 @@ def test_sweep_fp32_tracks_same_particles(orc, dim, tally):
     T = rng.uniform(0.0, 1.0, size=inst.ncells)
     p = oracle_problem(inst, [1.0], [1.0], N, N, seed=3)
     r = orc.sweep(p, T, 0)
-    s = gpu_solver(inst, [1.0], [1.0], N, N, precision=1, tally=tally, schedule=tally, seed=3)
+    s = gpu_solver(inst, [1.0], [1.0], N, N, precision=1, tally=tally, schedule=min(tally, 1), seed=3)
     g = s.sweep(cuda_T(T), 0)
     # Same draws; single-precision walks change a particle's cell only when it stops
     # within ~1e-7 of a face, so tallies agree to well below the statistical noise.
@@ -130,7 +130,7 @@ def test_steady_fp32_within_5e4_of_span(orc):
     N = 256
     p = oracle_problem(inst, [1.0], [1.0], N, N, seed=2)
     T_o, _, res_o, _ = orc.solve_steady(p, np.zeros(inst.ncells), 1e-9, 500, frozen=True, newton=True, dT_ref=1.0)
-    for tally in (0, 1):
+    for tally in (0, 1, 2):
         s = gpu_solver(inst, [1.0], [1.0], N, N, precision=1, tally=tally, seed=2)
         T_g, it, res = s.solve_steady(None, 1e-9, 500)
         assert np.abs(T_g.cpu().numpy() - T_o).max() <= 5e-4, tally
@@ -213,6 +213,25 @@ def test_full_size_conservation_every_mode():
         assert abs((g["wall"].cpu().numpy().sum() - wall_em) - (emitted.sum() - R.sum())) <= 1e-6 * emitted.sum()
 
 
+def test_compensated_fp32_tallies_match_fp64_tallies():
+    # Same particles and FP32 walks, tallies either FP64 atomics or compensated FP32 pairs:
+    # the two differ by rounding only (about n 2^-48 relative after n additions), far below
+    # the FP32 walk's own effect; counters are identical. Includes a 200^2 instance whose
+    # x-faces miss the shared-memory window, so face tallies take the compensated path too.
+    wl = WL.cavity_sweep(64, (0.05, 1.0))
+    wl.instances.append(WL.cavity(200, 0.3).instances[0])
+    rng = np.random.default_rng(9)
+    T = cuda_T(rng.uniform(0, 1, wl.total_cells))
+    out = []
+    for tally in (1, 2):
+        s = gpu_solver(wl.instances, [1.0], [1.0], 256, 256, seed=6, tally=tally)
+        out.append(s.sweep(T, 1))
+    assert out[0]["counters"].cpu().tolist() == out[1]["counters"].cpu().tolist()
+    for key in ("R", "W", "F", "wall"):
+        ok, err = normwise_close(out[1][key].cpu().numpy(), out[0][key].cpu().numpy(), 1e-9)
+        assert ok, (key, err)
+
+
 def test_staged_tunables_change_speed_not_results():
     # refill threshold, particles per warp claim and crossings per walk phase only reorder
     # the work: the same particles take the same FP32 steps, so counters and the integer
@@ -233,12 +252,12 @@ def test_staged_tunables_change_speed_not_results():
             ok, err = normwise_close(g[key].cpu().numpy(), ref[key].cpu().numpy(), 1e-12)
             assert ok, (kw, key, err)
     s = gpu_solver(wl.instances, [1.0], [1.0], 512, 512, seed=4)
-    t = s.autotune(T, 3)
+    t = s.autotune(T, 3, allow_k32=True)
     assert t["refill_lanes"] in (0, 4, 8, 16, 24) and t["warp_grab"] in (128, 256, 512)
-    assert t["walk_k"] in (8, 16, 32) and 0 < t["sweep_ms"] <= t["baseline_ms"]
+    assert t["walk_k"] in (8, 16, 32) and t["tally"] in (1, 2) and 0 < t["sweep_ms"] <= t["baseline_ms"]
     g = s.sweep(T, 3)
     assert g["counters"].cpu().tolist() == ref["counters"].cpu().tolist()
-    ok, err = normwise_close(g["R"].cpu().numpy(), ref["R"].cpu().numpy(), 1e-12)
+    ok, err = normwise_close(g["R"].cpu().numpy(), ref["R"].cpu().numpy(), 1e-9 if t["tally"] == 2 else 1e-12)
     assert ok, err
     with pytest.raises(Exception):
         gpu_solver(wl.instances, [1.0], [1.0], 512, 512, precision=0, tally=0, schedule=0).autotune(T)
