@@ -103,7 +103,7 @@ void free_all(Ctx* c) {
                   c->d_R, c->d_W, c->d_F, c->d_wall, c->d_red, c->d_counters, c->d_work_counter, c->d_err,
                   c->d_pcg_iters, c->d_scalar, c->d_adj, c->d_mg, c->d_mg_diag, c->d_mg_dinv, c->d_mg_cx,
                   c->d_mg_cy, c->d_mg_cz, c->d_mg_cinv, c->d_mg_b, c->d_mg_x, c->d_mg_t, c->d_mg_r,
-                  c->d_inst_beg, c->d_inst_end, c->d_inst_next, c->d_cost_prefix, c->d_win_fits, c->d_wmax,
+                  c->d_inst_beg, c->d_inst_end, c->d_inst_next, c->d_cost_prefix, c->d_window, c->d_wmax,
                   c->d_group_rcp, c->d_rcp, c->d_wall_unit, c->d_all_beg, c->d_all_end, c->d_all_cost_prefix,
                   c->d_all_group_rcp, c->d_R32, c->d_W32, c->d_F32};
   for (void* p : ptrs)
@@ -213,23 +213,27 @@ iugkp_status rebuild_forward_groups(Ctx* c) {
   double tot = 0.0;
   staged_tables(c, c->h_groups_fwd, beg, end, prefix, tot, grcp);
   c->cost_total = tot;
-  std::vector<int> fits(c->n_inst, 0);
+  // x-face window: all x-faces when they fit, else a centred run of them (the rest take
+  // global atomics)
+  std::vector<int2> window(c->n_inst);
   for (int k = 0; k < c->n_inst; ++k) {
     const InstDesc& in = c->h_inst[k];
-    fits[k] = (long long)(in.n[0] + 1) * in.n[1] * in.n[2] <= c->staged_cap ? 1 : 0;
+    const long long X = (long long)(in.n[0] + 1) * in.n[1] * in.n[2];
+    const long long len = std::min<long long>(X, c->staged_cap);
+    window[k] = make_int2((int)((X - len) / 2), (int)len);
   }
-  void* olds[] = {c->d_inst_beg, c->d_inst_end, c->d_cost_prefix, c->d_win_fits, c->d_group_rcp};
+  void* olds[] = {c->d_inst_beg, c->d_inst_end, c->d_cost_prefix, c->d_window, c->d_group_rcp};
   for (void* p : olds)
     if (p) cudaFree(p);
   c->d_inst_beg = c->d_inst_end = nullptr;
   c->d_cost_prefix = nullptr;
-  c->d_win_fits = nullptr;
+  c->d_window = nullptr;
   c->d_group_rcp = nullptr;
   if ((s = upload(c, &c->d_group_rcp, grcp)) != IUGKP_OK) return s;
   if ((s = upload(c, &c->d_inst_beg, beg)) != IUGKP_OK) return s;
   if ((s = upload(c, &c->d_inst_end, end)) != IUGKP_OK) return s;
   if ((s = upload(c, &c->d_cost_prefix, prefix)) != IUGKP_OK) return s;
-  return upload(c, &c->d_win_fits, fits);
+  return upload(c, &c->d_window, window);
 }
 
 }  // namespace
@@ -578,7 +582,7 @@ iugkp_status iugkp_create_batch(int n, const iugkp_grid* g, const double* const*
   {
     long long maxX = 0;
     for (const InstDesc& in : c->h_inst) maxX = std::max(maxX, (long long)(in.n[0] + 1) * in.n[1] * in.n[2]);
-    const long long budget = ((long long)c->smem_optin - 4096) / 8;
+    const long long budget = ((long long)c->smem_optin - 4096) / (long long)sizeof(unsigned);
     c->staged_cap = (int)std::max<long long>(1, std::min(maxX, budget));
   }
   if ((s = rebuild_forward_groups(c)) != IUGKP_OK) return bail(s);

@@ -127,7 +127,7 @@ struct Ctx {
   unsigned long long* d_inst_next = nullptr;
   double* d_cost_prefix = nullptr;
   double cost_total = 0.0;
-  int* d_win_fits = nullptr;
+  int2* d_window = nullptr;      // [n_inst] {first x-face, count} of the shared-memory window
   unsigned long long* d_wmax = nullptr;  // [n_inst] bit patterns of the largest weight
   float* d_group_rcp = nullptr;      // [forward groups]
   double* d_wall_unit = nullptr;     // [n_inst * 6] power entering per face per unit wall T

@@ -5,13 +5,20 @@ namespace iugkp {
 
 constexpr int STAGED_NT = 1024;                 // threads per persistent block
 
+// Shared-memory x-face window: one 32-bit word per face holding the low word of a 64-bit
+// fixed-point sum in units of w_max 2^-26 (a contribution is below 2^26 units); words start
+// at 2^31, and a wrap of the word adds +-2^32 units (= 64 w_max) to the FP64 face at once.
+constexpr double WIN_SCALE = 0x1p26;
+constexpr double WIN_CARRY = 0x1p6;             // 2^32 units in multiples of w_max
+constexpr unsigned WIN_BIAS = 0x80000000u;
+
 struct StagedArgs {
   int n_inst;
   unsigned long long* inst_next;  // [n_inst] next unclaimed forward particle of each instance
   const long long* inst_end;      // [n_inst] end of each instance's forward particle range
   const double* cost_prefix;      // [n_inst] prefix sums of the estimated cost
   double cost_total;
-  const int* win_fits;            // [n_inst] 1 if all x-faces fit the shared-memory window
+  const int2* window;             // [n_inst] {first x-face, count} tallied in shared memory
   const double* wmax;             // [n_inst] largest |particle weight| of the sweep
   int warp_grab;                  // particles a warp claims at a time
   int refill;                     // idle lanes that trigger a refill (0: per-instance default)

@@ -1,13 +1,15 @@
 // Fast forward sweep: FP32 walk, persistent blocks, face tallies staged in shared memory
-// in 64-bit fixed point. Same method and draws as the plain sweep
+// in fixed point. Same method and draws as the plain sweep
 // (arXiv 2506.09465 Sec. 3.1 steps (1)-(3), Sec. 3.2 null collisions); only the
 // arithmetic precision of the walk and the way tallies are accumulated differ.
 //
 // Face tallies:
-//  * faces normal to x are accumulated in a shared-memory copy of all of the instance's
-//    x-faces (when it fits), as integers in units of q = w_max 2^-36 (exact and
-//    independent of the order of the additions), and flushed to the FP64 array when the
-//    block leaves the instance; otherwise they are global FP64 atomics;
+//  * faces normal to x are accumulated in a shared-memory copy of the instance's x-faces
+//    (all of them when they fit, else a centred run), as integers in units of
+//    q = w_max 2^-26 (exact and independent of the order of the additions): 32-bit words
+//    (native shared-memory atomics, about five times the rate of 64-bit ones) whose rare
+//    wrap-arounds add +-2^32 q to the FP64 face at once, flushed to the FP64 array when the
+//    block leaves the instance; x-faces outside the window take global atomics;
 //  * faces normal to the last axis (y in 2D, z in 3D) are not tallied, except on the low
 //    boundary: every particle conserves power, so in every cell the net inflow equals the
 //    absorbed minus emitted power, and the last-axis faces follow exactly by a prefix sum
@@ -53,15 +55,18 @@ __device__ __forceinline__ unsigned udiv(unsigned n, unsigned d, float rcp) {
   return q;
 }
 
-// Register-resident walk state. t_a: path length at which the next face normal to axis a
-// is reached; d_a: path length per cell along a; s_a: +-1; xface: index of the x-face the
-// particle crosses next along x (kept incrementally).
-struct FW {
-  int i0, i1, i2, cell, xface;
+// Register-resident path state. The direction does not change at null collisions, so the
+// path from emission to the end (real collision or wall) is one straight segment: i_a is
+// the emission cell, t_a the path length at which the first face normal to axis a is
+// reached, d_a the path length per cell along a (+inf when s_a = 0), so the k-th face along
+// a is reached at t_a + k d_a. D: path length of the current candidate collision;
+// tex: path length at which the segment leaves the domain.
+struct PW {
+  int i0, i1, i2;
+  int s0, s1, s2;
   float t0, t1, t2;
   float d0, d1, d2;
-  int s0, s1, s2;
-  float D;
+  float D, tex;
 };
 
 __device__ __forceinline__ void axis_init(float s, float xi, float h, float& t, float& d, int& st) {
@@ -70,6 +75,20 @@ __device__ __forceinline__ void axis_init(float s, float xi, float h, float& t, 
   d = __fdividef(h, as);  // +inf when s = 0
   t = (s > 0.f ? 1.f - xi : xi) * d;
 }
+
+// Faces normal to one axis reached before path length L: #{k >= 0 : t + k d < L}.
+__device__ __forceinline__ int faces_before(float L, float t, float d) {
+  return L > t ? (int)ceilf(__fdividef(L - t, d)) : 0;
+}
+
+// Faces up to and including the wall along one axis, and the path length of the wall face.
+__device__ __forceinline__ int faces_to_wall(int i, int s, int n) { return s > 0 ? n - i : i + 1; }
+__device__ __forceinline__ float axis_exit(int i, int s, int n, float t, float d) {
+  const int m = faces_to_wall(i, s, n);
+  return m > 1 ? fmaf((float)(m - 1), d, t) : t;
+}
+
+__device__ __forceinline__ int clampi(int v, int n) { return min(max(v, 0), n - 1); }
 
 }  // namespace
 
@@ -121,7 +140,7 @@ struct EmitCache {
 // wall slot (-1 - wall) the particle's gather belongs to.
 template <int DIM, bool ADJ>
 __device__ __forceinline__ bool staged_emit(const SweepArgs& A, const StagedArgs& S, unsigned pid, bool useF,
-                                            double& w, int& band, FW& f, Stream& st, uint32_t& ub, EmitCache& ec,
+                                            double& w, int& band, PW& f, Stream& st, uint32_t& ub, EmitCache& ec,
                                             const InstDesc& in, int k, int& emitter) {
   if (pid < ec.g_first || pid >= ec.g_end) {
     const int gi = find_group(A.groups, A.n_groups, (long long)pid);
@@ -265,10 +284,15 @@ __device__ __forceinline__ bool staged_emit(const SweepArgs& A, const StagedArgs
     (void)face;  // the power entering through wall faces is added by boundary_kernel
   }
   axis_init(sx, xi0, in.hf[0], f.t0, f.d0, f.s0);
-  if (DIM >= 2) axis_init(sy, xi1, in.hf[1], f.t1, f.d1, f.s1);
-  if (DIM >= 3) axis_init(sz, xi2, in.hf[2], f.t2, f.d2, f.s2);
-  f.cell = f.i0 + n0 * (f.i1 + n1 * f.i2);
-  f.xface = f.cell + (f.i1 + n1 * f.i2) + (f.s0 > 0 ? 1 : 0);
+  f.tex = axis_exit(f.i0, f.s0, n0, f.t0, f.d0);
+  if (DIM >= 2) {
+    axis_init(sy, xi1, in.hf[1], f.t1, f.d1, f.s1);
+    f.tex = fminf(f.tex, axis_exit(f.i1, f.s1, n1, f.t1, f.d1));
+  }
+  if (DIM >= 3) {
+    axis_init(sz, xi2, in.hf[2], f.t2, f.d2, f.s2);
+    f.tex = fminf(f.tex, axis_exit(f.i2, f.s2, n2, f.t2, f.d2));
+  }
   uint32_t ua;
   st.next_pair(ua, ub);
   f.D = -__logf(word_uniform<float>(ua)) * A.vtm32[(long long)k * A.nb + b];
@@ -310,7 +334,7 @@ __global__ void k32_finalize_kernel(const float2* src, double* dst, long long n,
 
 template <int DIM, bool ADJ, bool K32>
 __global__ void __launch_bounds__(STAGED_NT, 1) sweep_staged_kernel(SweepArgs A, StagedArgs S) {
-  extern __shared__ unsigned long long win[];
+  extern __shared__ unsigned win[];
   __shared__ int s_inst;
   LCounts cnt;
 #pragma unroll
@@ -341,23 +365,27 @@ __global__ void __launch_bounds__(STAGED_NT, 1) sweep_staged_kernel(SweepArgs A,
     const int ncells = in.ncells, refill = S.refill > 0 ? S.refill : in.refill;
     const int sy_cell = n0, sz_cell = n0 * n1;           // cell index steps along y, z
     const int sy_xf = n0 + 1, sz_xf = (n0 + 1) * n1;     // x-face index steps along y, z
-    const bool staged = useF && S.win_fits[k];
-    const int X = staged ? (int)((n0 + 1) * (long long)n1 * n2) : 0;
-    for (int i = threadIdx.x; i < X; i += STAGED_NT) win[i] = 0ull;
+    // x-faces [wbase, wbase + wlen) of this instance are tallied in the shared window
+    const int2 wd = useF ? S.window[k] : make_int2(0, 0);
+    const int wbase = wd.x;
+    const unsigned wlen = (unsigned)wd.y;
+    for (unsigned i = threadIdx.x; i < wlen; i += STAGED_NT) win[i] = WIN_BIAS;
     __syncthreads();
     const double wmax = S.wmax[k];
-    const double qinv = wmax > 0.0 ? 0x1p36 / wmax : 0.0;
+    const double qinv = wmax > 0.0 ? WIN_SCALE / wmax : 0.0;
     const unsigned pend = (unsigned)S.inst_end[k];
     unsigned rbeg = 0, rend = 0;  // this warp's private particle range
     double w = 0.0, wt = 0.0;
-    unsigned long long qwx = 0;   // signed x-face contribution in units of q
+    unsigned qwx = 0;             // signed x-face contribution in units of q (two's complement)
     int band = 0;
     long long bcbase = 0;
     float vtm = 0.f;
-    FW f;
+    PW f;
     Stream st;
     uint32_t ub = 0;
     bool alive = false, exhausted = false;
+    bool tally = false;     // the lane's particle has ended and tallies its faces
+    int kcur = 0, kend = 0; // face items of the tally phase (x-faces, then y-faces in 3D)
     EmitCache ec;
     ec.g_first = 1;
     ec.g_end = 0;  // empty: forces a lookup on the first emission
@@ -391,8 +419,8 @@ __global__ void __launch_bounds__(STAGED_NT, 1) sweep_staged_kernel(SweepArgs A,
           }
           if (alive) {
             cnt.v[CNT_FLIGHTS] += 1;
-            const long long qw = __double2ll_rn(w * qinv);
-            qwx = (unsigned long long)(f.s0 > 0 ? qw : -qw);
+            const int qw = __double2int_rn(w * qinv);
+            qwx = (unsigned)(f.s0 > 0 ? qw : -qw);
             wt = w * A.taumaj[(long long)k * A.nb + band];
             vtm = A.vtm32[(long long)k * A.nb + band];
             bcbase = bc_off + (long long)band * ncells;
@@ -404,91 +432,30 @@ __global__ void __launch_bounds__(STAGED_NT, 1) sweep_staged_kernel(SweepArgs A,
         if (exhausted) break;
         continue;
       }
-      // ---- walk: up to walk_k crossings per lane; lanes that stopped at a candidate
-      // collision are then handled together ----
-      if (alive) {
-        bool stop = false;
-        const int cy = f.s1 * sy_cell, cz = f.s2 * sz_cell, xy = f.s1 * sy_xf, xz = f.s2 * sz_xf;
+      // ---- candidates (Sec. 3.2): up to walk_k per lane. The candidate lies at path length D
+      // of the straight segment; its cell follows from the faces before D on each axis.
+      // W tally, then acceptance with probability tau_maj / tau(x); a rejected candidate
+      // draws the next flight length and the particle goes on in the same direction ----
+      if (alive && !tally) {
+        bool ended = false, wall_exit = false;
 #pragma unroll 1
         for (int it = 0; it < S.walk_k; ++it) {
-          bool ax, ay = false;
-          float tmin;
-          if (DIM == 1) {
-            ax = true;
-            tmin = f.t0;
-          } else if (DIM == 2) {
-            ax = !(f.t1 < f.t0);  // equal distances cross x first
-            ay = !ax;
-            tmin = ax ? f.t0 : f.t1;
-          } else {
-            ax = !(f.t1 < f.t0) && !(f.t2 < f.t0);
-            ay = !ax && !(f.t2 < f.t1);
-            tmin = ax ? f.t0 : (ay ? f.t1 : f.t2);
-          }
-          if (f.D <= tmin) {
-            stop = true;
-            break;
-          }
-          const bool az = DIM == 3 && !ax && !ay;
-          if (useF) {
-            if (ax) {
-              if (staged) atomicAdd(&win[f.xface], qwx);
-              else if (K32) tally_k32(&S.F32[face_off + f.xface], f.s0 > 0 ? w : -w);
-              else atomicAdd(&A.F[face_off + f.xface], f.s0 > 0 ? w : -w);
-            } else if (ay && (DIM == 3 || (f.s1 < 0 && f.i1 == 0))) {
-              const int up = f.s1 > 0 ? 1 : 0;
-              const long long fi = face_off + fax1 + f.cell + (long long)n0 * f.i2 + (long long)n0 * up;
-              if (K32) tally_k32(&S.F32[fi], up ? w : -w);
-              else atomicAdd(&A.F[fi], up ? w : -w);
-            } else if (az && f.s2 < 0 && f.i2 == 0) {
-              if (K32) tally_k32(&S.F32[face_off + fax2 + f.cell], -w);
-              else atomicAdd(&A.F[face_off + fax2 + f.cell], -w);
-            }
-          }
-          bool out;
-          if (DIM == 1) {
-            f.i0 += f.s0;
-            f.t0 += f.d0;
-            f.cell += f.s0;
-            f.xface += f.s0;
-            out = (unsigned)f.i0 >= (unsigned)n0;
-          } else if (DIM == 2) {
-            f.i0 += ax ? f.s0 : 0;
-            f.i1 += ax ? 0 : f.s1;
-            f.t0 += ax ? f.d0 : 0.f;
-            f.t1 += ax ? 0.f : f.d1;
-            f.cell += ax ? f.s0 : cy;
-            f.xface += ax ? f.s0 : xy;
-            out = (unsigned)(ax ? f.i0 : f.i1) >= (unsigned)(ax ? n0 : n1);
-          } else {
-            f.i0 += ax ? f.s0 : 0;
-            f.i1 += ay ? f.s1 : 0;
-            f.i2 += az ? f.s2 : 0;
-            f.t0 += ax ? f.d0 : 0.f;
-            f.t1 += ay ? f.d1 : 0.f;
-            f.t2 += az ? f.d2 : 0.f;
-            f.cell += ax ? f.s0 : (ay ? cy : cz);
-            f.xface += ax ? f.s0 : (ay ? xy : xz);
-            out = (unsigned)(ax ? f.i0 : (ay ? f.i1 : f.i2)) >= (unsigned)(ax ? n0 : (ay ? n1 : n2));
-          }
-          if (out) {  // absorbed by a wall: its power reaches the wall tally through F
+          if (f.tex < f.D) {  // the segment reaches a wall first: absorbed there
             cnt.v[CNT_WALL_EXITS] += 1;
-            alive = false;
+            ended = wall_exit = true;
             break;
           }
-          cnt.v[CNT_CROSSINGS] += 1;
-        }
-        if (stop) {
-          // candidate collision in the current cell (Sec. 3.2): W tally, then accept with
-          // probability tau_maj / tau(x)
           cnt.v[CNT_CANDIDATES] += 1;
-          const long long ci = bcbase + f.cell;
+          int cell = clampi(f.i0 + f.s0 * faces_before(f.D, f.t0, f.d0), n0);
+          if (DIM >= 2) cell += sy_cell * clampi(f.i1 + f.s1 * faces_before(f.D, f.t1, f.d1), n1);
+          if (DIM == 3) cell += sz_cell * clampi(f.i2 + f.s2 * faces_before(f.D, f.t2, f.d2), n2);
+          const long long ci = bcbase + cell;
           if (!ADJ && K32 && S.W32) tally_k32(&S.W32[ci], wt);
           else if (!ADJ && !K32 && A.W) atomicAdd(&A.W[ci], wt);
           if (word_uniform<float>(ub) < A.ratio32[ci]) {
             cnt.v[CNT_REAL] += 1;
             if (ADJ) {
-              const long long gc = in.cell_off + f.cell;
+              const long long gc = in.cell_off + cell;
               const double val = w * A.lambda[gc] * A.invVm[gc];
               if (emitter >= 0) atomicAdd(&A.adj_out[in.cell_off + emitter], val);
               else acc += val;
@@ -497,22 +464,121 @@ __global__ void __launch_bounds__(STAGED_NT, 1) sweep_staged_kernel(SweepArgs A,
             } else {
               atomicAdd(&A.R[ci], w);
             }
-            alive = false;
-          } else {
-            uint32_t ua;
-            st.next_pair(ua, ub);
-            f.D += -__logf(word_uniform<float>(ua)) * vtm;
+            ended = true;
+            break;
           }
+          uint32_t ua;
+          st.next_pair(ua, ub);
+          f.D += -__logf(word_uniform<float>(ua)) * vtm;
+        }
+        if (ended) {
+          // interior faces crossed before the end, per axis; on the exit axis the wall face
+          // lies exactly at tex, so its count is known without rounding
+          const float L = wall_exit ? f.tex : f.D;
+          int ex = -1;
+          if (wall_exit) {
+            const float e0 = axis_exit(f.i0, f.s0, n0, f.t0, f.d0);
+            const float e1 = DIM >= 2 ? axis_exit(f.i1, f.s1, n1, f.t1, f.d1) : INFINITY;
+            const float e2 = DIM == 3 ? axis_exit(f.i2, f.s2, n2, f.t2, f.d2) : INFINITY;
+            ex = (e0 <= e1 && e0 <= e2) ? 0 : (e1 <= e2 ? 1 : 2);
+          }
+          const int m0 = faces_to_wall(f.i0, f.s0, n0);
+          const int c0 = ex == 0 ? m0 - 1 : min(faces_before(L, f.t0, f.d0), m0 - 1);
+          int c1 = 0, c2 = 0, m1 = 1;
+          if (DIM >= 2) {
+            m1 = faces_to_wall(f.i1, f.s1, n1);
+            c1 = ex == 1 ? m1 - 1 : min(faces_before(L, f.t1, f.d1), m1 - 1);
+          }
+          if (DIM == 3) {
+            const int m2 = faces_to_wall(f.i2, f.s2, n2);
+            c2 = ex == 2 ? m2 - 1 : min(faces_before(L, f.t2, f.d2), m2 - 1);
+          }
+          cnt.v[CNT_CROSSINGS] += c0 + c1 + c2;
+          if (useF) {
+            // faces normal to the last axis: only the low boundary is tallied (the rest
+            // follow from conservation)
+            if (DIM == 2 && ex == 1 && f.s1 < 0) {
+              const long long fi = face_off + fax1 + (f.i0 + f.s0 * c0);
+              if (K32) tally_k32(&S.F32[fi], -w);
+              else atomicAdd(&A.F[fi], -w);
+            } else if (DIM == 3 && ex == 2 && f.s2 < 0) {
+              const long long fi = face_off + fax2 + (f.i0 + f.s0 * c0) + (long long)n0 * (f.i1 + f.s1 * c1);
+              if (K32) tally_k32(&S.F32[fi], -w);
+              else atomicAdd(&A.F[fi], -w);
+            }
+            // x-faces crossed (the wall face too when the particle leaves through x),
+            // then in 3D the y-faces
+            kcur = 0;
+            kend = c0 + (ex == 0 ? 1 : 0);
+            if (DIM == 3) {
+              f.tex = __int_as_float(kend);  // first y-face item
+              kend += c1 + (ex == 1 ? 1 : 0);
+            } else if (DIM == 2) {
+              // rows of the x-face crossings, incrementally: faces normal to y before the
+              // k-th x-face = ceil(u0 + k r), u0 = (t0 - t1) / d1, r = d0 / d1
+              const bool flat = !(f.d1 < INFINITY);
+              f.D = flat ? -1.f : __fdividef(f.t0 - f.t1, f.d1);
+              f.tex = flat ? 0.f : __fdividef(f.d0, f.d1);
+            }
+            tally = kend > 0;
+            alive = tally;
+          } else {
+            alive = false;
+          }
+        }
+      }
+      // ---- face tallies of ended particles: up to walk_k per lane ----
+      if (tally) {
+#pragma unroll 1
+        for (int it = 0; it < S.walk_k && kcur < kend; ++it, ++kcur) {
+          if (DIM == 3 && kcur >= __float_as_int(f.tex)) {
+            // y-face item: the (kcur - kx)-th face normal to y along the segment
+            const int mm = kcur - __float_as_int(f.tex);
+            const float tm = fmaf((float)mm, f.d1, f.t1);
+            const int col = clampi(f.i0 + f.s0 * faces_before(tm, f.t0, f.d0), n0);
+            const int lay = clampi(f.i2 + f.s2 * faces_before(tm, f.t2, f.d2), n2);
+            const int jf = f.s1 > 0 ? f.i1 + 1 + mm : f.i1 - mm;
+            const long long fi = face_off + fax1 + col + (long long)n0 * (jf + (long long)(n1 + 1) * lay);
+            if (K32) tally_k32(&S.F32[fi], f.s1 > 0 ? w : -w);
+            else atomicAdd(&A.F[fi], f.s1 > 0 ? w : -w);
+            continue;
+          }
+          int xface = f.s0 > 0 ? f.i0 + 1 + kcur : f.i0 - kcur;
+          if (DIM == 2) {
+            const float u = fmaf((float)kcur, f.tex, f.D);
+            xface += sy_xf * clampi(f.i1 + f.s1 * (u > 0.f ? (int)ceilf(u) : 0), n1);
+          } else if (DIM == 3) {
+            const float tk = fmaf((float)kcur, f.d0, f.t0);
+            xface += sy_xf * clampi(f.i1 + f.s1 * faces_before(tk, f.t1, f.d1), n1) +
+                     sz_xf * clampi(f.i2 + f.s2 * faces_before(tk, f.t2, f.d2), n2);
+          }
+          const unsigned rel = (unsigned)(xface - wbase);
+          if (rel < wlen) {
+            // 64-bit sum kept as a 32-bit low word here plus carries added to the FP64
+            // face: the old word tells whether this addition wrapped (rare: the word
+            // starts at 2^31 and one contribution is at most 2^26)
+            const unsigned old = atomicAdd(&win[rel], qwx);
+            const int carry = ((int)qwx >> 31) + (old + qwx < old ? 1 : 0);
+            if (carry) atomicAdd(&A.F[face_off + xface], (double)carry * S.wmax[k] * WIN_CARRY);
+          } else if (K32) {
+            tally_k32(&S.F32[face_off + xface], f.s0 > 0 ? w : -w);
+          } else {
+            atomicAdd(&A.F[face_off + xface], f.s0 > 0 ? w : -w);
+          }
+        }
+        if (kcur >= kend) {
+          tally = false;
+          alive = false;
         }
       }
     }
     if (ADJ && acc != 0.0) atomicAdd(&A.adj_wall[in.wall_off + (-1 - acc_slot)], acc);
     __syncthreads();
-    if (staged) {
-      const double qs = wmax * 0x1p-36;
-      double* Fx = A.F + face_off;  // x-faces come first
-      for (int i = threadIdx.x; i < X; i += STAGED_NT) {
-        const long long v = (long long)win[i];
+    if (wlen) {
+      const double qs = wmax / WIN_SCALE;
+      double* Fx = A.F + face_off + wbase;  // x-faces come first
+      for (unsigned i = threadIdx.x; i < wlen; i += STAGED_NT) {
+        const int v = (int)(win[i] - WIN_BIAS);
         if (v) atomicAdd(&Fx[i], (double)v * qs);
       }
     }
@@ -630,7 +696,7 @@ cudaError_t launch_sweep_staged(const Ctx* c, const SweepArgs& a, cudaStream_t s
   S.inst_end = c->d_inst_end;
   S.cost_prefix = c->d_cost_prefix;
   S.cost_total = c->cost_total;
-  S.win_fits = c->d_win_fits;
+  S.window = c->d_window;
   S.wmax = reinterpret_cast<const double*>(c->d_wmax);
   S.warp_grab = c->opt.warp_grab > 0 ? c->opt.warp_grab : 256;
   S.walk_k = c->opt.walk_k > 0 ? c->opt.walk_k : 16;
@@ -645,7 +711,7 @@ cudaError_t launch_sweep_staged(const Ctx* c, const SweepArgs& a, cudaStream_t s
   if ((e = cudaMemsetAsync(c->d_wmax, 0, c->n_inst * sizeof(double), s)) != cudaSuccess) return e;
   group_wmax_kernel<<<a.n_groups, 256, 0, s>>>(a, c->d_wmax);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  const size_t smem = (size_t)c->staged_cap * sizeof(unsigned long long);
+  const size_t smem = (size_t)c->staged_cap * sizeof(unsigned);
   const int blocks = c->sm_count * c->staged_blocks_per_sm;
   const bool k32 = c->opt.tally == IUGKP_TALLY_STAGED_K32;
   S.R32 = k32 ? c->d_R32 : nullptr;
@@ -706,7 +772,7 @@ cudaError_t launch_adjoint_staged(const Ctx* c, const SweepArgs& a, cudaStream_t
   S.inst_end = c->d_all_end;
   S.cost_prefix = c->d_all_cost_prefix;
   S.cost_total = c->all_cost_total;
-  S.win_fits = c->d_win_fits;
+  S.window = c->d_window;
   S.wmax = reinterpret_cast<const double*>(c->d_wmax);
   S.warp_grab = c->opt.warp_grab > 0 ? c->opt.warp_grab : 256;
   S.walk_k = c->opt.walk_k > 0 ? c->opt.walk_k : 16;
@@ -730,7 +796,7 @@ cudaError_t launch_adjoint_staged(const Ctx* c, const SweepArgs& a, cudaStream_t
 
 cudaError_t configure_staged(Ctx* c) {
   cudaError_t e = cudaSuccess;
-  const size_t smem = (size_t)c->staged_cap * sizeof(unsigned long long);
+  const size_t smem = (size_t)c->staged_cap * sizeof(unsigned);
   const void* fwd[6] = {(const void*)sweep_staged_kernel<1, false, false>, (const void*)sweep_staged_kernel<2, false, false>,
                         (const void*)sweep_staged_kernel<3, false, false>, (const void*)sweep_staged_kernel<1, false, true>,
                         (const void*)sweep_staged_kernel<2, false, true>, (const void*)sweep_staged_kernel<3, false, true>};

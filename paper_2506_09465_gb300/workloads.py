@@ -49,6 +49,29 @@ def slab(n=50, Kn=1.0, T_left=1.0, T_right=-1.0, particles=1000) -> Workload:
     return Workload(f"1D gray slab {n} cells Kn={Kn}", np.array([1.0]), np.array([1.0]), [inst], particles, particles)
 
 
+def jump_slab(case: str = "A", n: int = 100, particles: int = 8000) -> Workload:
+    """1D gray film with a tau jump at x = L/2 (Sec. 4.2 shape): L = 1, C = |v| = 1,
+    tau = 10 for x < L/2 and 0.1 (case A) or 1 (case B) for x > L/2, black walls at
+    T = +1 (x = 0) and -1 (x = L)."""
+    right = {"A": 0.1, "B": 1.0}[case]
+    x = (np.arange(n) + 0.5) / n
+    tau = np.where(x < 0.5, 10.0, right).reshape(1, n)
+    inst = Instance(1, (n,), (1.0,), tau, np.array([1.0, -1.0]))
+    return Workload(f"1D gray slab {n} cells tau 10 | {right}", np.array([1.0]), np.array([1.0]), [inst], particles,
+                    particles)
+
+
+def multiscale_slab(n: int = 100, particles: int = 8000, A1: float = 2.0, A2: float = 1.0) -> Workload:
+    """1D gray film with a continuously varying relaxation time (Sec. 4.3 shape),
+    tau(x) = 10^(|A1 sin(2 pi x / L)| - A2) at the cell centres; A1 = 2, A2 = 1 spans
+    [0.1, 10]. L = 1, C = |v| = 1, black walls at T = +1 and -1."""
+    x = (np.arange(n) + 0.5) / n
+    tau = (10.0 ** (np.abs(A1 * np.sin(2.0 * np.pi * x)) - A2)).reshape(1, n)
+    inst = Instance(1, (n,), (1.0,), tau, np.array([1.0, -1.0]))
+    return Workload(f"1D gray multiscale slab {n} cells", np.array([1.0]), np.array([1.0]), [inst], particles,
+                    particles)
+
+
 def cavity(n=128, Kn=1.0, particles=1024) -> Workload:
     """2D gray square cavity (Sec. 4.4 shape): unit square, top wall T = 1, others 0."""
     inst = Instance(2, (n, n), (1.0, 1.0), np.full((1, n * n), Kn), np.array([0.0, 0.0, 0.0, 1.0]))

@@ -49,3 +49,47 @@ def test_oracle_frozen_fixed_points_average_to_golden(orc):
     sols = np.array(sols)
     z = (sols.mean(0) - T_gold) / (sols.std(0, ddof=1) / np.sqrt(M))
     assert np.abs(z).max() < 4.5
+
+
+def load_variable_tau(name):
+    path = os.path.join(GOLDEN, name)
+    rows = np.array([[float(v) for v in l.split()] for l in open(path) if l[0] != "#"])
+    q = float([l for l in open(path) if "heat flux" in l][0].split(":")[1])
+    return rows[:, 0], rows[:, 1], rows[:, 2], q
+
+
+@pytest.mark.parametrize("name", ["slab_jump_caseA_100cells.txt", "slab_jump_caseB_100cells.txt",
+                                  "slab_multiscale_100cells.txt"])
+def test_variable_tau_golden_profiles(name):
+    # Stored steady states of the variable-tau films (Sec. 4.2, 4.3) equal the expected-
+    # operator fixed point, and at that state the net flux is the same through every face
+    # (zero divergence: what a steady state means).
+    x, tau, T, q = load_variable_tau(name)
+    xc = (np.arange(100) + 0.5) / 100
+    if "multiscale" in name:
+        tau_def = 10.0 ** (np.abs(2.0 * np.sin(2.0 * np.pi * xc)) - 1.0)
+    else:
+        tau_def = np.where(xc < 0.5, 10.0, 0.1 if "caseA" in name else 1.0)
+    assert np.allclose(tau, tau_def, rtol=1e-14)
+    T2, _, _ = X.slab_fixed_point(1.0, [1.0], [1.0], tau_def.reshape(1, -1), [1.0, -1.0])
+    assert np.allclose(T, T2, rtol=1e-13, atol=1e-14)
+    _, _, F, wall = X.slab_expected_sweep(1.0, [1.0], [1.0], tau.reshape(1, -1), T, [1.0, -1.0])
+    assert np.abs(F - q).max() <= 1e-10 * abs(q)
+    assert abs(wall.sum()) <= 1e-10 * abs(q)   # what one wall emits net, the other absorbs
+    assert np.all(np.diff(T) < 0) and 0 < q < 0.5   # below the ballistic limit C v dT / 4
+
+
+def test_multiscale_profile_is_antisymmetric():
+    # tau(x) = 10^(|2 sin 2 pi x| - 1) is symmetric about x = 1/2 and the walls are +-1.
+    _, tau, T, _ = load_variable_tau("slab_multiscale_100cells.txt")
+    assert np.allclose(tau, tau[::-1], rtol=1e-12)
+    assert np.abs(T + T[::-1]).max() < 1e-11
+
+
+def test_case_A_thick_half_follows_fourier():
+    # In the tau = 0.1 half (Kn 0.1), 1.5 mean free paths from the interface and the wall,
+    # the profile is linear with the slope of Fourier's law, k = C v^2 tau / 3.
+    x, tau, T, q = load_variable_tau("slab_jump_caseA_100cells.txt")
+    sel = (x > 0.65) & (x < 0.85)
+    slope = np.polyfit(x[sel], T[sel], 1)[0]
+    assert abs(slope / (-q / (0.1 / 3.0)) - 1.0) < 0.01
