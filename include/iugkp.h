@@ -181,6 +181,23 @@ iugkp_status iugkp_macro(iugkp_ctx *ctx, const double *R_dev, const double *W_de
 iugkp_status iugkp_newton_step(iugkp_ctx *ctx, const double *T_n_dev, double *T_half_inout_dev,
                                const double *R_dev, void *cuda_stream, int *cg_iters_out);
 
+/* Statistical averaging after convergence (Sec. 4.4-4.5: the paper adds 100-1500 steps whose
+ * results are averaged to reduce the statistical noise). Runs n_steps (>= 1) further
+ * iterations from T_inout_dev, each with fresh draws (epoch = epoch_first + step) and the
+ * update of iugkp_solve_steady (sweep, macro update, Newton correction when
+ * options.newton), and accumulates on the device in FP64 the running mean and, by
+ * Welford's update, the sample variance (n - 1 in the denominator; 0 for one step) of the
+ * iterates, and the mean net power through every face.
+ *   T_inout_dev  device FP64 [total_cells]: start on entry, last iterate on return
+ *   T_mean_dev   device FP64 [total_cells] (required)
+ *   T_var_dev    device FP64 [total_cells] or NULL
+ *   F_mean_dev   device FP64 [total_faces] or NULL (face layout of iugkp_sweep)
+ * Successive iterates are correlated: the variance is of the iterates, not of their mean.
+ * Enqueued on cuda_stream; synchronises once at the end for the device error check
+ * (IUGKP_ENOCONV if a correction solve hit cg_maxit). EINVAL for NULL T or mean, n_steps < 1. */
+iugkp_status iugkp_average(iugkp_ctx *ctx, double *T_inout_dev, int n_steps, unsigned epoch_first,
+                           double *T_mean_dev, double *T_var_dev, double *F_mean_dev, void *cuda_stream);
+
 /* Tuning of the staged sweep (no counterpart in the paper; refill, claim size and walk
  * length change speed, not results; the tally mode changes results by rounding only).
  * iugkp_autotune times full sweeps from T_dev (device FP64 [total_cells]) on the caller's

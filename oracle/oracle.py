@@ -268,6 +268,26 @@ def solve_steady(p: Problem, T0: np.ndarray, tol: float, max_iter: int, frozen: 
     return T, it.value, res.value, hist[: it.value]
 
 
+def average(p: Problem, T0: np.ndarray, n_steps: int, epoch_first: int, newton_on: bool = True):
+    """Statistical averaging after convergence (Sec. 4.4-4.5: extra steps whose results are
+    averaged to reduce the statistical noise): n_steps further iterations, each with fresh
+    draws (epoch = epoch_first + step) and the same update as the solve (sweep, macro
+    update, Newton correction); returns the last iterate, the mean and the sample variance
+    (n - 1 in the denominator) of the n_steps iterates, and the mean face power.
+    Plain two-pass statistics over the stored iterates."""
+    T = np.array(T0, dtype=np.float64, copy=True)
+    Ts, Fs = [], []
+    for k in range(n_steps):
+        r = sweep(p, T, epoch_first + k)
+        T_half, _ = macro(p, r.R, r.W)
+        T = newton(p, T, T_half, r.R)[0] if newton_on else T_half
+        Ts.append(T.copy())
+        Fs.append(r.F.copy())
+    Ts = np.array(Ts)
+    var = Ts.var(axis=0, ddof=1) if n_steps > 1 else np.zeros(p.ncells)
+    return T, Ts.mean(axis=0), var, np.array(Fs).mean(axis=0)
+
+
 def adjoint_apply(p: Problem, lam: np.ndarray, epoch: int = 0):
     """Returns (A^T lam over cells, B_wall^T lam per wall) for one sweep's draws."""
     lam = np.ascontiguousarray(lam, dtype=np.float64)

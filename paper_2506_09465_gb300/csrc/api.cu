@@ -105,7 +105,7 @@ void free_all(Ctx* c) {
                   c->d_mg_cy, c->d_mg_cz, c->d_mg_cinv, c->d_mg_b, c->d_mg_x, c->d_mg_t, c->d_mg_r,
                   c->d_inst_beg, c->d_inst_end, c->d_inst_next, c->d_cost_prefix, c->d_window, c->d_wmax,
                   c->d_group_rcp, c->d_rcp, c->d_wall_unit, c->d_all_beg, c->d_all_end, c->d_all_cost_prefix,
-                  c->d_all_group_rcp, c->d_R32, c->d_W32, c->d_F32};
+                  c->d_all_group_rcp, c->d_R32, c->d_W32, c->d_F32, c->d_m2};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (c->h_pinned) cudaFreeHost(c->h_pinned);
@@ -1068,6 +1068,39 @@ iugkp_status iugkp_solve_steady(iugkp_ctx* ctx, double* T_inout_dev, double tol,
   if (res_out) *res_out = res;
   if (!(res <= tol)) return fail(c, IUGKP_ENOCONV, "max_iter reached before tol");
   return IUGKP_OK;
+}
+
+iugkp_status iugkp_average(iugkp_ctx* ctx, double* T_inout_dev, int n_steps, unsigned epoch_first,
+                           double* T_mean_dev, double* T_var_dev, double* F_mean_dev, void* cuda_stream) {
+  if (!ctx) return IUGKP_EINVAL;
+  Ctx* c = &ctx->c;
+  if (!T_inout_dev || !T_mean_dev || n_steps < 1) return fail(c, IUGKP_EINVAL, "bad argument");
+  cudaStream_t s = (cudaStream_t)cuda_stream;
+  double* m2 = T_var_dev;
+  if (!m2) {
+    if (!c->d_m2) {
+      iugkp_status st = dalloc(c, &c->d_m2, (size_t)c->total_cells);
+      if (st != IUGKP_OK) return st;
+    }
+    m2 = c->d_m2;
+  }
+  const size_t cb = (size_t)c->total_cells * sizeof(double);
+  CK(cudaMemsetAsync(T_mean_dev, 0, cb, s), "clear mean");
+  CK(cudaMemsetAsync(m2, 0, cb, s), "clear m2");
+  if (F_mean_dev) CK(cudaMemsetAsync(F_mean_dev, 0, (size_t)c->total_faces * sizeof(double), s), "clear F mean");
+  double* cur = T_inout_dev;
+  double* nxt = c->d_T2;
+  for (int k = 0; k < n_steps; ++k) {
+    // the solve's update with fresh draws: epoch_first + k
+    iugkp_status st = iteration_async(c, cur, nxt, epoch_first + (unsigned)k, c->d_scalar + 4, s);
+    if (st != IUGKP_OK) return st;
+    CK(launch_welford(c, nxt, T_mean_dev, m2, c->total_cells, k + 1, s), "welford");
+    if (F_mean_dev) CK(launch_welford(c, c->d_F, F_mean_dev, nullptr, c->total_faces, k + 1, s), "flux mean");
+    std::swap(cur, nxt);
+  }
+  if (T_var_dev) CK(launch_scale(c, T_var_dev, c->total_cells, n_steps > 1 ? 1.0 / (n_steps - 1) : 0.0, s), "variance");
+  if (cur != T_inout_dev) CK(cudaMemcpyAsync(T_inout_dev, cur, cb, cudaMemcpyDeviceToDevice, s), "copy result");
+  return check_device(c, s);
 }
 
 }  // extern "C"

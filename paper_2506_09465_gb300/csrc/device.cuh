@@ -39,6 +39,14 @@ __device__ __forceinline__ Real word_uniform(uint32_t a) {
   return (Real)((a >> 9) * 2u + 1u) * (Real)(1.0 / 16777216.0);
 }
 
+// The same value in FP32 without an integer-to-float conversion (those issue at a fraction
+// of the FP32 rate): 1 + m 2^-23 from the mantissa bits, minus 1 - 2^-24, is exactly
+// m 2^-23 + 2^-24 = (2m + 1) 2^-24 (representable, so the subtraction is exact).
+template <>
+__device__ __forceinline__ float word_uniform<float>(uint32_t a) {
+  return __int_as_float(0x3F800000u | (a >> 9)) - 0.99999994f;
+}
+
 // The uniform stream of one particle: uniform j is word (j mod 4) of block j / 4,
 // block k = Philox(counter (k, particle, emitter, band<<24 | epoch), key). Emission
 // consumes an even number of uniforms, so every later (path, accept) pair of a

@@ -107,6 +107,7 @@ struct Ctx {
   int* d_pcg_iters = nullptr;    // [n_inst]
   double* d_scalar = nullptr;    // [8] small results
   double* d_adj = nullptr;       // [4 * cells] adjoint iteration buffers (allocated on first use)
+  double* d_m2 = nullptr;        // [cells] averaging: sum of squared deviations (allocated on first use)
   double* h_pinned = nullptr;    // [8 + n_inst] host readback
   // multigrid preconditioner of the Newton correction (mg_setup.cu, mgpcg.cu)
   struct InstMG* d_mg = nullptr;
@@ -172,5 +173,8 @@ cudaError_t launch_mgpcg(const Ctx* c, const double* rhs, cudaStream_t s);
 iugkp_status build_multigrid(Ctx* c, const std::vector<double>& diag, const std::vector<double>& cx,
                              const std::vector<double>& cy, const std::vector<double>& cz);
 cudaError_t launch_grad_source(const Ctx* c, const double* at, double* grad, cudaStream_t s);
+cudaError_t launch_welford(const Ctx* c, const double* x, double* mean, double* m2, long long n, int k,
+                           cudaStream_t s);
+cudaError_t launch_scale(const Ctx* c, double* x, long long n, double a, cudaStream_t s);
 
 }  // namespace iugkp

@@ -271,6 +271,33 @@ cudaError_t launch_pcg_check(const Ctx* c, cudaStream_t s) {
   return cudaGetLastError();
 }
 
+// Statistical averaging (Sec. 4.4-4.5): the k-th sample x updates the running mean and the
+// sum of squared deviations M2 (Welford's one-pass update; FP64).
+__global__ void welford_kernel(long long total, const double* x, double* mean, double* m2, double inv_k) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total; i += (long long)gridDim.x * blockDim.x) {
+    const double d = x[i] - mean[i];
+    const double mu = mean[i] + d * inv_k;
+    mean[i] = mu;
+    if (m2) m2[i] += d * (x[i] - mu);
+  }
+}
+
+__global__ void scale_kernel(long long total, double* x, double a) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total; i += (long long)gridDim.x * blockDim.x)
+    x[i] *= a;
+}
+
+cudaError_t launch_welford(const Ctx* c, const double* x, double* mean, double* m2, long long n, int k,
+                           cudaStream_t s) {
+  welford_kernel<<<grid_for(c, n), 256, 0, s>>>(n, x, mean, m2, 1.0 / (double)k);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_scale(const Ctx* c, double* x, long long n, double a, cudaStream_t s) {
+  scale_kernel<<<grid_for(c, n), 256, 0, s>>>(n, x, a);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_axpy_grad(const Ctx* c, const double* at, const double* g, double* lam_half, cudaStream_t s) {
   add_kernel<<<grid_for(c, c->total_cells), 256, 0, s>>>(c->total_cells, at, g, lam_half);
   return cudaGetLastError();

@@ -76,9 +76,15 @@ __device__ __forceinline__ void axis_init(float s, float xi, float h, float& t, 
   t = (s > 0.f ? 1.f - xi : xi) * d;
 }
 
+// ceil(max(u, 0)) for u < 2^23 without a float-to-integer conversion: adding 2^23 with
+// rounding upwards lands on 2^23 + ceil(u), whose bits minus those of 2^23 are the count.
+__device__ __forceinline__ int ceil_count(float u) {
+  return __float_as_int(__fadd_ru(fmaxf(u, 0.f), 8388608.f)) - 0x4B000000;
+}
+
 // Faces normal to one axis reached before path length L: #{k >= 0 : t + k d < L}.
 __device__ __forceinline__ int faces_before(float L, float t, float d) {
-  return L > t ? (int)ceilf(__fdividef(L - t, d)) : 0;
+  return L > t ? ceil_count(__fdividef(L - t, d)) : 0;
 }
 
 // Faces up to and including the wall along one axis, and the path length of the wall face.
@@ -511,7 +517,7 @@ __global__ void __launch_bounds__(STAGED_NT, 1) sweep_staged_kernel(SweepArgs A,
             kcur = 0;
             kend = c0 + (ex == 0 ? 1 : 0);
             if (DIM == 3) {
-              f.tex = __int_as_float(kend);  // first y-face item
+              f.tex = (float)kend;  // first y-face item
               kend += c1 + (ex == 1 ? 1 : 0);
             } else if (DIM == 2) {
               // rows of the x-face crossings, incrementally: faces normal to y before the
@@ -529,12 +535,15 @@ __global__ void __launch_bounds__(STAGED_NT, 1) sweep_staged_kernel(SweepArgs A,
       }
       // ---- face tallies of ended particles: up to walk_k per lane ----
       if (tally) {
+        const int kstop = min(kend, kcur + S.walk_k);
+        float fk = (float)kcur;  // the item index in FP32, advanced without conversions
 #pragma unroll 1
-        for (int it = 0; it < S.walk_k && kcur < kend; ++it, ++kcur) {
-          if (DIM == 3 && kcur >= __float_as_int(f.tex)) {
+        for (; kcur < kstop; ++kcur, fk += 1.f) {
+          if (DIM == 3 && fk >= f.tex) {
             // y-face item: the (kcur - kx)-th face normal to y along the segment
-            const int mm = kcur - __float_as_int(f.tex);
-            const float tm = fmaf((float)mm, f.d1, f.t1);
+            const float fm = fk - f.tex;  // exact: both are small integers
+            const int mm = ceil_count(fm);
+            const float tm = fmaf(fm, f.d1, f.t1);
             const int col = clampi(f.i0 + f.s0 * faces_before(tm, f.t0, f.d0), n0);
             const int lay = clampi(f.i2 + f.s2 * faces_before(tm, f.t2, f.d2), n2);
             const int jf = f.s1 > 0 ? f.i1 + 1 + mm : f.i1 - mm;
@@ -545,10 +554,9 @@ __global__ void __launch_bounds__(STAGED_NT, 1) sweep_staged_kernel(SweepArgs A,
           }
           int xface = f.s0 > 0 ? f.i0 + 1 + kcur : f.i0 - kcur;
           if (DIM == 2) {
-            const float u = fmaf((float)kcur, f.tex, f.D);
-            xface += sy_xf * clampi(f.i1 + f.s1 * (u > 0.f ? (int)ceilf(u) : 0), n1);
+            xface += sy_xf * clampi(f.i1 + f.s1 * ceil_count(fmaf(fk, f.tex, f.D)), n1);
           } else if (DIM == 3) {
-            const float tk = fmaf((float)kcur, f.d0, f.t0);
+            const float tk = fmaf(fk, f.d0, f.t0);
             xface += sy_xf * clampi(f.i1 + f.s1 * faces_before(tk, f.t1, f.d1), n1) +
                      sz_xf * clampi(f.i2 + f.s2 * faces_before(tk, f.t2, f.d2), n2);
           }

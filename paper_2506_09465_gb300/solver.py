@@ -163,6 +163,16 @@ class Solver:
                                        _stream_ptr(stream)), self.ctx)
         return gs, gw, lam
 
+    def average(self, T, n_steps, epoch_first, want_var=True, want_F=False, stream=None):
+        """Statistical averaging after convergence (iugkp_average): n_steps fresh-draw
+        iterations from T (updated in place to the last iterate); returns (mean, var, F_mean)."""
+        mean = self.zeros(self.total_cells)
+        var = self.zeros(self.total_cells) if want_var else None
+        Fm = self.zeros(self.total_faces) if want_F else None
+        L.check(self.lib.iugkp_average(self.ctx, _dptr(T), int(n_steps), int(epoch_first), _dptr(mean), _dptr(var),
+                                       _dptr(Fm), _stream_ptr(stream)), self.ctx)
+        return mean, var, Fm
+
     def autotune(self, T, epoch=0, allow_k32=False, stream=None):
         """Times the staged sweep over its tunables and keeps the fastest (see iugkp_autotune)."""
         t = L.Tuning()

@@ -76,6 +76,7 @@ def test_null_arguments_rejected(lib):
     assert L.iugkp_solve_steady(None, None, 1e-8, 10, None, None, None) == 1
     assert L.iugkp_adjoint(None, None, None, 1e-8, 10, None, None, None, None) == 1
     assert L.iugkp_autotune(None, None, 0, 0, None, None) == 1
+    assert L.iugkp_average(None, None, 1, 0, None, None, None, None) == 1
     L.iugkp_destroy(None)  # no-op
 
 
@@ -94,3 +95,14 @@ def test_default_options(lib):
     assert o.warp_grab == 0 and o.walk_k == 0 and o.refill_lanes == 0
     with pytest.raises(AttributeError):
         lib.default_options(no_such_option=1)
+
+
+def test_fp32_uniform_from_mantissa_bits_is_exact():
+    # The fast path forms its FP32 uniforms as (1 + m 2^-23) - (1 - 2^-24) from the top 23
+    # bits m of a Philox word; this equals (2m + 1) 2^-24, the value the oracle and the FP64
+    # path use, for every m (IEEE round-to-nearest FP32, as on the GPU).
+    m = np.arange(1 << 23, dtype=np.uint32)
+    fast = (0x3F800000 | m).view(np.float32) - np.float32(0.99999994)
+    ref = ((2 * m.astype(np.float64) + 1) / 16777216.0).astype(np.float32)
+    assert np.float32(0.99999994) == np.float32(1.0 - 2.0 ** -24)
+    assert np.array_equal(fast, ref) and np.array_equal(ref.astype(np.float64), (2 * m.astype(np.float64) + 1) / 16777216.0)

@@ -93,3 +93,33 @@ def test_case_A_thick_half_follows_fourier():
     sel = (x > 0.65) & (x < 0.85)
     slope = np.polyfit(x[sel], T[sel], 1)[0]
     assert abs(slope / (-q / (0.1 / 3.0)) - 1.0) < 0.01
+
+
+def test_oracle_statistical_average_matches_expected_steady_state(orc):
+    # Averaging after convergence (Sec. 4.4): with fresh draws each iteration is a random
+    # affine map whose expectation has the stored steady state as fixed point, so the mean
+    # of the iterates converges to it. Standard error from 20 batch means of 20 steps
+    # (successive iterates are correlated); the face flux averages to the stored flux.
+    T_gold = load_slab()
+    q_gold = float([l for l in open(os.path.join(GOLDEN, "slab_kn1_50cells.txt")) if "heat flux" in l][0]
+                   .split(":")[1])
+    n = 50
+    p = orc.Problem(1, (n,), (1.0,), np.array([1.0]), np.array([1.0]), np.ones((1, n)), np.array([1.0, -1.0]),
+                    np.array([200]), np.array([200]), seed=4)
+    T0, _, _, _ = orc.solve_steady(p, np.zeros(n), 1e-8, 200, frozen=True, newton=True, dT_ref=2.0)
+    nb, bl = 20, 20
+    means, fluxes = [], []
+    T = T0
+    for b in range(nb):
+        T, Tm, Tv, Fm = orc.average(p, T, bl, 1000 + b * bl)
+        means.append(Tm)
+        fluxes.append(Fm.mean())
+        assert np.all(Tv > 0)
+    means = np.array(means)
+    z = (means.mean(0) - T_gold) / (means.std(0, ddof=1) / np.sqrt(nb))
+    assert np.abs(z).max() < 4.5
+    fluxes = np.array(fluxes)
+    assert abs(fluxes.mean() - q_gold) < 4.5 * fluxes.std(ddof=1) / np.sqrt(nb)
+    # one call over all the steps = the pooled batches (same draws, same order)
+    _, Tm_all, _, _ = orc.average(p, T0, nb * bl, 1000)
+    assert np.allclose(Tm_all, means.mean(0), rtol=1e-12, atol=1e-14)

@@ -213,6 +213,28 @@ def test_full_size_conservation_every_mode():
         assert abs((g["wall"].cpu().numpy().sum() - wall_em) - (emitted.sum() - R.sum())) <= 1e-6 * emitted.sum()
 
 
+def test_statistical_average_matches_oracle(orc):
+    # Averaging after convergence (Sec. 4.4): 12 fresh-draw iterations from the converged
+    # state; the FP64 path takes the oracle's draws and update, so the mean, the sample
+    # variance of the iterates and the mean face power agree; the fast FP32 path's mean is
+    # within 5e-4 of the wall span.
+    inst = WL.cavity(24, 0.1).instances[0]
+    N = 256
+    p = oracle_problem(inst, [1.0], [1.0], N, N, seed=8)
+    T0, _, _, _ = orc.solve_steady(p, np.zeros(inst.ncells), 1e-9, 300, frozen=True, newton=True, dT_ref=1.0)
+    T_last, Tm, Tv, Fm = orc.average(p, T0, 12, 500)
+    s = gpu_solver(inst, [1.0], [1.0], N, N, precision=0, tally=0, schedule=0, seed=8, cg_rtol=1e-12)
+    T = cuda_T(T0)
+    mean, var, F = s.average(T, 12, 500, want_F=True)
+    for got, ref, tol in ((T, T_last, 1e-9), (mean, Tm, 1e-9), (F, Fm, 1e-9), (var, Tv, 1e-6)):
+        ok, err = normwise_close(got.cpu().numpy(), ref, tol)
+        assert ok, err
+    assert np.all(Tv > 0)
+    s32 = gpu_solver(inst, [1.0], [1.0], N, N, seed=8)
+    m32, _, _ = s32.average(cuda_T(T0), 12, 500, want_var=False)
+    assert np.abs(m32.cpu().numpy() - Tm).max() <= 5e-4
+
+
 def test_compensated_fp32_tallies_match_fp64_tallies():
     # Same particles and FP32 walks, tallies either FP64 atomics or compensated FP32 pairs:
     # the two differ by rounding only (about n 2^-48 relative after n additions), far below
