@@ -148,6 +148,10 @@ struct OrcProblem {
   unsigned long long seed;
   unsigned int instance;
   long long budget;        // max steps (crossings + candidates) per particle
+  const double* wall_face_T;  // [boundary faces] temperature of every boundary face, or
+                              // NULL (each wall uniform at wall_T). Walls in the order of
+                              // wall_T; on wall (a, side) the faces run over the two other
+                              // axes o1 = (a+1)%3, o2 = (a+2)%3, o1 fastest.
 };
 
 }  // extern "C"
@@ -304,7 +308,7 @@ bool valid(const OrcProblem* p) {
 // emitter id, particle index, unit-temperature weight coefficient, start state.
 template <typename F>
 void for_each_particle(const OrcProblem& p, const Geo& g, uint32_t epoch, bool skip_zero,
-                       const double* T_emit, const double* wall_T, F&& fn) {
+                       const double* T_emit, const double* wall_T, const double* wall_face_T, F&& fn) {
   // Thermal emission (Sec. 3.1 step (1)): N_b particles per cell and band, power
   // C_b T V / tau_b shared equally.
   for (int b = 0; b < p.nb; ++b) {
@@ -330,7 +334,13 @@ void for_each_particle(const OrcProblem& p, const Geo& g, uint32_t epoch, bool s
       }
     }
   }
-  // Wall emission: every boundary face emits the hemispherical power C_b v_b T_w A / 4.
+  // Wall emission: every boundary face emits the hemispherical power C_b v_b T_w A / 4,
+  // T_w the temperature of its wall, or of the face itself when wall_face_T is given.
+  long long wall_face_off[7] = {0, 0, 0, 0, 0, 0, 0};
+  for (int wl = 0; wl < 2 * g.dim; ++wl) {
+    int a = wl / 2;
+    wall_face_off[wl + 1] = wall_face_off[wl] + (long long)g.n[(a + 1) % 3] * g.n[(a + 2) % 3];
+  }
   for (int b = 0; b < p.nb; ++b) {
     long long nwp = p.n_wall_band[b];
     if (nwp <= 0) continue;
@@ -339,12 +349,14 @@ void for_each_particle(const OrcProblem& p, const Geo& g, uint32_t epoch, bool s
         int wall = 2 * a + side;
         double Tw = wall_T ? wall_T[wall] : 0.0;
         double coef = p.C[b] * p.v[b] * g.A[a] / (4.0 * (double)nwp);
-        double w = coef * Tw;
-        if (skip_zero && w == 0.0) continue;
+        if (skip_zero && !wall_face_T && coef * Tw == 0.0) continue;
         int o1 = (a + 1) % 3, o2 = (a + 2) % 3;
         // Faces on this wall: all (i_o1, i_o2) with the a-index at 0 or n[a].
         for (int j2 = 0; j2 < g.n[o2]; ++j2) {
           for (int j1 = 0; j1 < g.n[o1]; ++j1) {
+            double Tf = wall_face_T ? wall_face_T[wall_face_off[wall] + (long long)j2 * g.n[o1] + j1] : Tw;
+            double w = coef * Tf;
+            if (skip_zero && w == 0.0) continue;
             int f[3];
             f[a] = side == 0 ? 0 : g.n[a];
             f[o1] = j1; f[o2] = j2;
@@ -423,7 +435,7 @@ int orc_sweep(const OrcProblem* p, const double* T, uint32_t epoch, double* R, d
   std::fill(F, F + g.nfaces_total, 0.0);
   std::fill(wall, wall + 2 * p->dim, 0.0);
   Tallies t{R, W, F, wall, {0, 0, 0, 0, 0, 0}};
-  for_each_particle(*p, g, epoch, true, T_emit.data(), p->wall_T,
+  for_each_particle(*p, g, epoch, true, T_emit.data(), p->wall_T, p->wall_face_T,
                     [&](int kind, int b, long long emitter, long long face_or_cell, double, double w, Stream& st,
                         double* x, int* idx, const double* s) {
                       t.counters[0] += 1;
@@ -671,7 +683,7 @@ int orc_adjoint_apply(const OrcProblem* p, const double* lambda, uint32_t epoch,
   cell_m(*p, g, m);
   std::fill(out, out + g.ncells, 0.0);
   std::fill(grad_wall, grad_wall + 2 * p->dim, 0.0);
-  for_each_particle(*p, g, epoch, false, nullptr, nullptr,
+  for_each_particle(*p, g, epoch, false, nullptr, nullptr, nullptr,
                     [&](int kind, int b, long long emitter, long long, double coef, double, Stream& st,
                         double* x, int* idx, const double* s) {
                       double gv = trace_particle(*p, g, b, tmaj[b], m.data(), st, x, idx, s, 0.0, nullptr, lambda);
@@ -693,7 +705,7 @@ int orc_emit(const OrcProblem* p, int kind, int band, long long emitter, uint32_
   majorants(*p, g, tmaj);
   std::vector<double> ones(g.ncells, 1.0), wones(2 * p->dim, 1.0);
   long long k = 0;
-  for_each_particle(*p, g, epoch, false, ones.data(), wones.data(),
+  for_each_particle(*p, g, epoch, false, ones.data(), wones.data(), nullptr,
                     [&](int knd, int b, long long, long long face_or_cell, double, double, Stream& st,
                         double* x, int*, const double* s) {
                       if (knd != kind || b != band || face_or_cell != emitter) return;

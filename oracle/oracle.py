@@ -45,6 +45,7 @@ class _Problem(ctypes.Structure):
         ("wall_T", ctypes.c_void_p), ("source", ctypes.c_void_p),
         ("n_band", ctypes.c_void_p), ("n_wall_band", ctypes.c_void_p),
         ("seed", ctypes.c_ulonglong), ("instance", ctypes.c_uint), ("budget", ctypes.c_longlong),
+        ("wall_face_T", ctypes.c_void_p),
     ]
 
 
@@ -89,7 +90,9 @@ class Problem:
     dim, n = (nx, ny, nz), L = (lx, ly, lz): uniform structured grid on [0, L];
     C, v: per band-branch; tau: [nb, ncells] (x fastest); wall_T: [2*dim] in the order
     -x, +x, -y, +y, -z, +z; source: [ncells] power density or None;
-    n_band / n_wall_band: particles per cell / per boundary face for each band.
+    n_band / n_wall_band: particles per cell / per boundary face for each band;
+    wall_face_T: temperature of every boundary face (walls in wall_T order; on the wall
+    normal to axis a the faces run over axes (a+1)%3, (a+2)%3, the first fastest), or None.
     """
     dim: int
     n: Sequence[int]
@@ -104,6 +107,7 @@ class Problem:
     seed: int = 0
     instance: int = 0
     budget: int = 1 << 24
+    wall_face_T: Optional[np.ndarray] = None
     _keep: list = field(default_factory=list, repr=False)
 
     def __post_init__(self):
@@ -118,6 +122,8 @@ class Problem:
         self.n_wall_band = np.ascontiguousarray(self.n_wall_band, dtype=np.int64)
         if self.source is not None:
             self.source = np.ascontiguousarray(self.source, dtype=np.float64)
+        if self.wall_face_T is not None:
+            self.wall_face_T = np.ascontiguousarray(self.wall_face_T, dtype=np.float64)
 
     @property
     def nb(self) -> int:
@@ -137,7 +143,13 @@ class Problem:
         s.wall_T, s.source = _ptr(self.wall_T), _ptr(self.source)
         s.n_band, s.n_wall_band = _ptr(self.n_band), _ptr(self.n_wall_band)
         s.seed, s.instance, s.budget = self.seed, self.instance, self.budget
+        s.wall_face_T = _ptr(self.wall_face_T)
         return s
+
+    def wall_faces(self):
+        """Boundary faces per wall, in wall order."""
+        n = self.n
+        return [n[(a + 1) % 3] * n[(a + 2) % 3] for a in range(self.dim) for _ in (0, 1)]
 
     def nfaces(self) -> int:
         return int(lib().orc_nfaces(ctypes.byref(self.c_struct())))

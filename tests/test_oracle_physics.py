@@ -275,3 +275,73 @@ def test_band_split(orc):
     assert np.all(np.abs(s - ideal) <= 1.0)
     with pytest.raises(ValueError):
         orc.band_split(3, r)
+
+
+# ---------------------------------------------------------------------------
+# Per-face wall temperatures (the non-uniform boundary of Sec. 4.5)
+# ---------------------------------------------------------------------------
+
+def _rect(orc, n=(20, 10), L=(5.0, 2.5), tau=1e9, N=64, face_T=None, wall_T=(0.0, 0.0, 0.0, 0.0), seed=3):
+    nc = n[0] * n[1]
+    return orc.Problem(2, n, L, np.array([1.0]), np.array([1.0]), np.full((1, nc), tau), np.array(wall_T),
+                       np.array([N]), np.array([N]), seed=seed, wall_face_T=face_T)
+
+
+def test_face_temperatures_equal_to_wall_values_reproduce_wall_sweep(orc):
+    wall_T = np.array([0.3, -0.2, 0.1, 1.0])
+    base = _rect(orc, tau=0.7, wall_T=wall_T)
+    faces = np.concatenate([np.full(m, t) for m, t in zip(base.wall_faces(), wall_T)])
+    per_face = _rect(orc, tau=0.7, wall_T=wall_T, face_T=faces)
+    T = np.linspace(0, 1, 200)
+    a, b = orc.sweep(base, T, 0), orc.sweep(per_face, T, 0)
+    for x, y in ((a.R, b.R), (a.W, b.W), (a.F, b.F), (a.wall, b.wall)):
+        assert np.array_equal(x, y)
+
+
+def test_face_temperatures_superpose(orc):
+    # The sweep is linear in the emission and draws are keyed by (emitter, particle): the
+    # sum over the top wall's faces of one-hot-face sweeps is the uniform-wall sweep.
+    n, L = (6, 4), (1.5, 1.0)
+    base = _rect(orc, n=n, L=L, tau=0.4, wall_T=(0.0, 0.0, 0.0, 1.0))
+    nf = base.wall_faces()
+    off = sum(nf[:3])
+    acc = None
+    for j in range(nf[3]):
+        ft = np.zeros(sum(nf))
+        ft[off + j] = 1.0
+        r = orc.sweep(_rect(orc, n=n, L=L, tau=0.4, face_T=ft), np.zeros(24), 0)
+        v = np.concatenate([r.R.ravel(), r.W.ravel(), r.F, r.wall])
+        acc = v if acc is None else acc + v
+    r = orc.sweep(base, np.zeros(24), 0)
+    ref = np.concatenate([r.R.ravel(), r.W.ravel(), r.F, r.wall])
+    assert np.allclose(acc, ref, rtol=1e-12, atol=1e-15)
+
+
+def test_hot_segment_ballistic_view_factors(orc):
+    # Sec. 4.5 geometry, L_x = 2 L_y = 5 L_1: a hot segment of length L_1 centred on the top
+    # wall, no collisions (tau = 1e9). The power it emits is absorbed by the other walls in
+    # the proportions of the 2D (crossed-strings) view factors of a diffuse emitter.
+    Lx, Ly = 5.0, 2.5
+    n = (20, 10)
+    ft = np.zeros(2 * n[1] + 2 * n[0])
+    top = 2 * n[1] + n[0]
+    ft[top + 8: top + 12] = 1.0                      # x in [2, 3]
+    N = 4000
+    r = orc.sweep(_rect(orc, n=n, L=(Lx, Ly), N=N, face_T=ft), np.zeros(200), 0)
+    emitted = 1.0 * 1.0 * 1.0 / 4.0                  # C v T L_1 / 4 per unit depth
+    assert abs(r.wall.sum() - emitted) < 1e-12
+    d = lambda p, q: np.hypot(p[0] - q[0], p[1] - q[1])
+
+    def view(a1, a2, b1, b2):  # crossed strings, segment a1-a2 to b1-b2, per unit length of a
+        return (d(a1, b2) + d(a2, b1) - d(a1, b1) - d(a2, b2)) / (2.0 * d(a1, a2))
+
+    a1, a2 = (2.0, Ly), (3.0, Ly)
+    F = {0: abs(view(a1, a2, (0.0, Ly), (0.0, 0.0))),    # left wall
+         1: abs(view(a1, a2, (Lx, 0.0), (Lx, Ly))),      # right wall
+         2: abs(view(a1, a2, (0.0, 0.0), (Lx, 0.0)))}    # bottom wall
+    assert abs(sum(F.values()) - 1.0) < 1e-12
+    for wall, f in F.items():
+        frac = r.wall[wall] / emitted
+        se = np.sqrt(f * (1 - f) / (4 * N))
+        assert abs(frac - f) < 4.5 * se, (wall, frac, f)
+    assert r.wall[3] == 0.0
