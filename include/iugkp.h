@@ -142,13 +142,20 @@ typedef struct {
   int n_inst, dim, nb;
   long long total_cells, total_faces, total_walls; /* walls = 2*dim per instance */
   long long total_particles;                       /* per sweep, every emitter counted */
+  long long total_wall_faces;                      /* boundary faces of all instances */
 } iugkp_layout;
 iugkp_status iugkp_get_layout(const iugkp_ctx *ctx, iugkp_layout *lay, long long *cell_off,
                               long long *face_off);
 
 /* Replaces a field. which: IUGKP_FIELD_SOURCE ([total_cells] power density),
- * IUGKP_FIELD_WALL_T ([total_walls]). `data` is host memory unless on_device != 0. */
-enum { IUGKP_FIELD_SOURCE = 0, IUGKP_FIELD_WALL_T = 1 };
+ * IUGKP_FIELD_WALL_T ([total_walls]: every face of each wall takes its wall's value),
+ * IUGKP_FIELD_WALL_FACE_T ([total_wall_faces]: the temperature of every boundary face, for
+ * non-uniform walls such as the heated segment of Sec. 4.5; instance-major, walls in the
+ * order -x, +x, -y, +y, -z, +z, on the wall normal to axis a the faces run over the axes
+ * (a+1)%3 and (a+2)%3, the first fastest). Wall emission per face is C_b v_b T_face A / 4
+ * (Sec. 4 black isothermal walls, per face). `data` is host memory unless on_device != 0
+ * (then read back, synchronising cuda_stream). Values must be finite (EINVAL). */
+enum { IUGKP_FIELD_SOURCE = 0, IUGKP_FIELD_WALL_T = 1, IUGKP_FIELD_WALL_FACE_T = 2 };
 iugkp_status iugkp_set_field(iugkp_ctx *ctx, int which, const double *data, int on_device,
                              void *cuda_stream);
 

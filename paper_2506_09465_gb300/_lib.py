@@ -16,7 +16,7 @@ TRACK_FP64, TRACK_FP32 = 0, 1
 TALLY_FP64, TALLY_STAGED, TALLY_STAGED_K32 = 0, 1, 2
 DRAWS_FRESH, DRAWS_FROZEN = 0, 1
 SCHED_PLAIN, SCHED_PERSISTENT = 0, 1
-FIELD_SOURCE, FIELD_WALL_T = 0, 1
+FIELD_SOURCE, FIELD_WALL_T, FIELD_WALL_FACE_T = 0, 1, 2
 
 
 class Grid(ctypes.Structure):
@@ -46,7 +46,8 @@ class Tuning(ctypes.Structure):
 class Layout(ctypes.Structure):
     _fields_ = [("n_inst", ctypes.c_int), ("dim", ctypes.c_int), ("nb", ctypes.c_int),
                 ("total_cells", ctypes.c_longlong), ("total_faces", ctypes.c_longlong),
-                ("total_walls", ctypes.c_longlong), ("total_particles", ctypes.c_longlong)]
+                ("total_walls", ctypes.c_longlong), ("total_particles", ctypes.c_longlong),
+                ("total_wall_faces", ctypes.c_longlong)]
 
 
 # Every exported symbol of include/iugkp.h with its ctypes signature.

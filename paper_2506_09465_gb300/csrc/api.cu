@@ -105,7 +105,7 @@ void free_all(Ctx* c) {
                   c->d_mg_cy, c->d_mg_cz, c->d_mg_cinv, c->d_mg_b, c->d_mg_x, c->d_mg_t, c->d_mg_r,
                   c->d_inst_beg, c->d_inst_end, c->d_inst_next, c->d_cost_prefix, c->d_window, c->d_wmax,
                   c->d_group_rcp, c->d_rcp, c->d_wall_unit, c->d_all_beg, c->d_all_end, c->d_all_cost_prefix,
-                  c->d_all_group_rcp, c->d_R32, c->d_W32, c->d_F32, c->d_m2};
+                  c->d_all_group_rcp, c->d_R32, c->d_W32, c->d_F32, c->d_m2, c->d_wallTf};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (c->h_pinned) cudaFreeHost(c->h_pinned);
@@ -180,14 +180,30 @@ void staged_tables(const Ctx* c, const std::vector<Group>& groups, std::vector<l
   }
 }
 
-// Forward groups leave out walls at zero temperature (their particles weigh zero).
+// Per-face wall temperatures from the per-wall values (every face of a wall alike).
+void broadcast_wall_T(Ctx* c) {
+  c->h_wallTf.assign((size_t)c->total_bfaces, 0.0);
+  for (const InstDesc& in : c->h_inst)
+    for (int w = 0; w < 2 * in.dim; ++w) {
+      const int a = w >> 1;
+      const int nf = in.n[(a + 1) % 3] * in.n[(a + 2) % 3];
+      for (int j = 0; j < nf; ++j) c->h_wallTf[in.bface_off + in.wface_off[w] + j] = c->h_wallT[in.wall_off + w];
+    }
+}
+
+// Forward groups leave out walls whose faces are all at zero temperature (their
+// particles weigh zero).
 iugkp_status rebuild_forward_groups(Ctx* c) {
   c->h_groups_fwd.clear();
   long long off = 0;
   for (const Group& g0 : c->h_groups_all) {
     if (g0.kind > 0) {
       const InstDesc& in = c->h_inst[g0.inst];
-      if (c->h_wallT[in.wall_off + g0.kind - 1] == 0.0) continue;
+      const int wl = g0.kind - 1;
+      const long long f0 = in.bface_off + in.wface_off[wl];
+      bool hot = false;
+      for (long long j = 0; j < g0.n_emitters && !hot; ++j) hot = c->h_wallTf[f0 + j] != 0.0;
+      if (!hot) continue;
     }
     Group g = g0;
     g.first_particle = off;
@@ -366,6 +382,15 @@ iugkp_status iugkp_create_batch(int n, const iugkp_grid* g, const double* const*
     }
     in.nfaces = fo;
     in.wall_off = 2 * dim * k;
+    in.bface_off = c->total_bfaces;
+    {
+      int wf = 0;
+      for (int w = 0; w < 6; ++w) {
+        in.wface_off[w] = wf;
+        if (w < 2 * dim) wf += in.n[((w >> 1) + 1) % 3] * in.n[((w >> 1) + 2) % 3];
+      }
+      c->total_bfaces += wf;
+    }
     in.inst_id = o->instance_base + (unsigned)k;
     c->h_inst.push_back(in);
     cell_off += in.ncells;
@@ -544,6 +569,7 @@ iugkp_status iugkp_create_batch(int n, const iugkp_grid* g, const double* const*
   }
   c->total_particles = total_particles;
   c->h_wallT = wallTv;
+  broadcast_wall_T(c);
 
   iugkp_status s;
 #define UP(ptr, vec)                                 \
@@ -563,6 +589,7 @@ iugkp_status iugkp_create_batch(int n, const iugkp_grid* g, const double* const*
   UP(c->d_v, c->h_v);
   UP(c->d_wcoef, wcoef);
   UP(c->d_wallT, wallTv);
+  UP(c->d_wallTf, c->h_wallTf);
   UP(c->d_m, m);
   UP(c->d_Vm, Vm);
   UP(c->d_invVm, invVm);
@@ -667,6 +694,7 @@ iugkp_status iugkp_get_layout(const iugkp_ctx* ctx, iugkp_layout* lay, long long
     lay->total_faces = c->total_faces;
     lay->total_walls = c->total_walls;
     lay->total_particles = c->total_particles;
+    lay->total_wall_faces = c->total_bfaces;
   }
   for (int k = 0; k <= c->n_inst; ++k) {
     if (cell_off) cell_off[k] = k < c->n_inst ? c->h_inst[k].cell_off : c->total_cells;
@@ -693,6 +721,7 @@ SweepArgs base_args(Ctx* c) {
   a.v = c->d_v;
   a.wcoef = c->d_wcoef;
   a.wallT = c->d_wallT;
+  a.wallTf = c->d_wallTf;
   a.seed = c->opt.seed;
   a.budget = c->opt.step_budget;
   a.err = c->d_err;
@@ -770,7 +799,7 @@ iugkp_status sweep_async(Ctx* c, const double* T, unsigned epoch, double* R, dou
 
 double dT_ref_of(const Ctx* c) {
   double lo = INFINITY, hi = -INFINITY, amax = 0.0;
-  for (double t : c->h_wallT) {
+  for (double t : c->h_wallTf) {
     lo = std::min(lo, t);
     hi = std::max(hi, t);
     amax = std::max(amax, std::fabs(t));
@@ -814,7 +843,8 @@ iugkp_status iugkp_set_field(iugkp_ctx* ctx, int which, const double* data, int 
   Ctx* c = &ctx->c;
   cudaStream_t s = (cudaStream_t)cuda_stream;
   size_t count = which == IUGKP_FIELD_SOURCE ? (size_t)c->total_cells
-                 : which == IUGKP_FIELD_WALL_T ? (size_t)c->total_walls : 0;
+                 : which == IUGKP_FIELD_WALL_T ? (size_t)c->total_walls
+                 : which == IUGKP_FIELD_WALL_FACE_T ? (size_t)c->total_bfaces : 0;
   if (!count) return fail(c, IUGKP_EINVAL, "unknown field");
   std::vector<double> h(count);
   if (on_device) {
@@ -832,8 +862,15 @@ iugkp_status iugkp_set_field(iugkp_ctx* ctx, int which, const double* data, int 
     CK(cudaMemcpy(m.data(), c->d_m, count * sizeof(double), cudaMemcpyDeviceToHost), "m readback");
     return set_source(c, h, m);
   }
-  c->h_wallT = h;
-  CK(cudaMemcpy(c->d_wallT, h.data(), count * sizeof(double), cudaMemcpyHostToDevice), "wall upload");
+  if (which == IUGKP_FIELD_WALL_T) {  // every face of a wall takes the wall's value
+    c->h_wallT = h;
+    CK(cudaMemcpy(c->d_wallT, h.data(), count * sizeof(double), cudaMemcpyHostToDevice), "wall upload");
+    broadcast_wall_T(c);
+  } else {
+    c->h_wallTf = h;
+  }
+  CK(cudaMemcpy(c->d_wallTf, c->h_wallTf.data(), c->h_wallTf.size() * sizeof(double), cudaMemcpyHostToDevice),
+     "wall face upload");
   return rebuild_forward_groups(c);
 }
 

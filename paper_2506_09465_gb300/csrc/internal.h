@@ -32,6 +32,7 @@ struct SweepArgs {
   const float* vtm32;      // [inst * nb] v_b tau_maj in FP32
   const double* wcoef;     // [inst * nb * 6] C_b v_b A / (4 N_w) per wall
   const double* wallT;     // [walls]
+  const double* wallTf;    // [boundary faces] temperature of every boundary face
   double* R;
   double* W;
   double* F;
@@ -61,6 +62,8 @@ struct Ctx {
   std::vector<Group> h_groups_fwd;  // walls at T_w = 0 left out (forward)
   long long fwd_particles = 0;
   std::vector<double> h_wallT;      // [walls]
+  std::vector<double> h_wallTf;     // [boundary faces]
+  long long total_bfaces = 0;
   std::vector<double> h_C, h_v;
   std::vector<long long> h_nband, h_nwall;
   std::vector<double> h_theta;      // per instance damping of the Newton correction
@@ -78,6 +81,7 @@ struct Ctx {
   double* d_v = nullptr;
   double* d_wcoef = nullptr;
   double* d_wallT = nullptr;
+  double* d_wallTf = nullptr;    // [total_bfaces]
   double* d_srcshift = nullptr;  // null when no source
   double* d_source = nullptr;    // Q (kept for set_field)
   double* d_m = nullptr;         // [cells] sum_b C_b / tau_b

@@ -22,6 +22,9 @@ struct InstDesc {
   uint32_t inst_id;   // Philox instance id
   float hf[3];        // cell size per axis in FP32 (the FP32 walk)
   int refill;         // staged sweep: refill a warp's lanes once this many are idle
+  long long bface_off;   // offset into per-boundary-face arrays
+  int wface_off[6];      // start of each wall's faces within the instance (faces of wall
+                         // a run over axes (a+1)%3, (a+2)%3, the first fastest)
 };
 
 // A run of emitters sharing (instance, band, kind). kind 0 = the instance's cells;

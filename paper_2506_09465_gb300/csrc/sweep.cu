@@ -64,7 +64,7 @@ __device__ __forceinline__ bool emit_particle(const SweepArgs& A, long long pid,
     emit_thermal<Real, DIM>(wk, st, in, e);
   } else {
     const int wl = G.kind - 1;
-    w = A.wcoef[((long long)G.inst * A.nb + b) * 6 + wl] * A.wallT[in.wall_off + wl];
+    w = A.wcoef[((long long)G.inst * A.nb + b) * 6 + wl] * A.wallTf[in.bface_off + in.wface_off[wl] + e];
     if (w == 0.0) return false;
     const int a = wl >> 1, side = wl & 1;
     const int o1 = (a + 1) % 3, o2 = (a + 2) % 3;

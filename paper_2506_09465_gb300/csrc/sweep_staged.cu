@@ -112,9 +112,11 @@ __global__ void group_wmax_kernel(SweepArgs A, unsigned long long* wmax_bits) {
       if (A.srcshift) Te += A.srcshift[in.cell_off + e];
       m = fmax(m, fabs(coef[e] * Te));
     }
-  } else if (threadIdx.x == 0) {
+  } else {
     const int wl = G.kind - 1;
-    m = fabs(A.wcoef[((long long)G.inst * A.nb + G.band) * 6 + wl] * A.wallT[in.wall_off + wl]);
+    const double wc = A.wcoef[((long long)G.inst * A.nb + G.band) * 6 + wl];
+    const double* tf = A.wallTf + in.bface_off + in.wface_off[wl];
+    for (int j = threadIdx.x; j < G.n_emitters; j += blockDim.x) m = fmax(m, fabs(wc * tf[j]));
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_down_sync(0xffffffffu, m, o));
@@ -228,10 +230,10 @@ __device__ __forceinline__ bool staged_emit(const SweepArgs& A, const StagedArgs
   } else {
     const int wl = kind - 1;
     if (ec.e != -2) {
-      ec.w = A.wcoef[((long long)k * A.nb + b) * 6 + wl] * (ADJ ? 1.0 : A.wallT[in.wall_off + wl]);
-      ec.e = -2;  // one weight for the whole wall group
+      ec.w = A.wcoef[((long long)k * A.nb + b) * 6 + wl];  // per unit face temperature
+      ec.e = -2;
     }
-    w = ec.w;
+    w = ADJ ? ec.w : ec.w * A.wallTf[in.bface_off + in.wface_off[wl] + e];
     if (w == 0.0) return false;
     emitter = -1 - wl;
     const int a = wl >> 1, side = wl & 1;
@@ -661,38 +663,53 @@ __device__ __forceinline__ int wall_faces(const InstDesc& in, int a) {
 // Power entering through every boundary face from its wall's emission (N_w particles of
 // weight C_b v_b A T_w / (4 N_w) per face and band), except on the high side of the
 // derived axis (that axis is rebuilt from conservation). Grid: (faces, walls, instances).
-__global__ void boundary_emission_kernel(const InstDesc* inst, int dim, const double* wall_unit, const double* wallT,
+__global__ void boundary_emission_kernel(const InstDesc* inst, int dim, const double* wall_unit, const double* wallTf,
                                          double* F) {
   const int k = blockIdx.z, wl = blockIdx.y;
   const int a = wl >> 1, side = wl & 1;
   if (dim >= 2 && a == dim - 1 && side == 1) return;
   const InstDesc& in = inst[k];
-  const double e = wall_unit[k * 6 + wl] * wallT[in.wall_off + wl];
-  if (e == 0.0) return;
+  const double u = wall_unit[k * 6 + wl];
+  const double* tf = wallTf + in.bface_off + in.wface_off[wl];
   const int nf = wall_faces(in, a);
-  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < nf; j += gridDim.x * blockDim.x)
-    F[in.face_off + wall_face(in, a, side, j)] += side ? -e : e;
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < nf; j += gridDim.x * blockDim.x) {
+    const double e = u * tf[j];
+    if (e != 0.0) F[in.face_off + wall_face(in, a, side, j)] += side ? -e : e;
+  }
 }
 
 // Absorbed power of each wall = its emission + the outward net flux through its faces.
 // One block per (wall, instance); fixed-order reduction.
 __global__ void __launch_bounds__(256) wall_absorbed_kernel(const InstDesc* inst, const double* wall_unit,
-                                                            const double* wallT, const double* F, double* wall) {
-  __shared__ double sh[8];
+                                                            const double* wallTf, const double* F, double* wall) {
+  __shared__ double sh[8], shT[8];
   const int k = blockIdx.y, wl = blockIdx.x;
   const int a = wl >> 1, side = wl & 1;
   const InstDesc& in = inst[k];
   const int nf = wall_faces(in, a);
-  double sum = 0.0;
-  for (int j = threadIdx.x; j < nf; j += 256) sum += F[in.face_off + wall_face(in, a, side, j)];
+  const double* tf = wallTf + in.bface_off + in.wface_off[wl];
+  double sum = 0.0, tsum = 0.0;
+  for (int j = threadIdx.x; j < nf; j += 256) {
+    sum += F[in.face_off + wall_face(in, a, side, j)];
+    tsum += tf[j];
+  }
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) sum += __shfl_down_sync(0xffffffffu, sum, o);
-  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = sum;
+  for (int o = 16; o > 0; o >>= 1) {
+    sum += __shfl_down_sync(0xffffffffu, sum, o);
+    tsum += __shfl_down_sync(0xffffffffu, tsum, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    sh[threadIdx.x >> 5] = sum;
+    shT[threadIdx.x >> 5] = tsum;
+  }
   __syncthreads();
   if (threadIdx.x == 0) {
-    double t = 0.0;
-    for (int w = 0; w < 8; ++w) t += sh[w];
-    const double emitted = wall_unit[k * 6 + wl] * (double)nf * wallT[in.wall_off + wl];
+    double t = 0.0, ts = 0.0;
+    for (int w = 0; w < 8; ++w) {
+      t += sh[w];
+      ts += shT[w];
+    }
+    const double emitted = wall_unit[k * 6 + wl] * ts;  // sum over faces of their emission
     wall[in.wall_off + wl] = emitted + (side ? t : -t);
   }
 }
@@ -751,7 +768,7 @@ cudaError_t launch_sweep_staged(const Ctx* c, const SweepArgs& a, cudaStream_t s
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   if (a.F) {
     boundary_emission_kernel<<<dim3(8, 2 * c->dim, c->n_inst), 256, 0, s>>>(c->d_inst, c->dim, c->d_wall_unit,
-                                                                           c->d_wallT, a.F);
+                                                                           c->d_wallTf, a.F);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
   if (a.F && c->dim >= 2) {
@@ -765,7 +782,7 @@ cudaError_t launch_sweep_staged(const Ctx* c, const SweepArgs& a, cudaStream_t s
     if (e != cudaSuccess) return e;
   }
   if (a.F && a.wall) {
-    wall_absorbed_kernel<<<dim3(2 * c->dim, c->n_inst), 256, 0, s>>>(c->d_inst, c->d_wall_unit, c->d_wallT, a.F,
+    wall_absorbed_kernel<<<dim3(2 * c->dim, c->n_inst), 256, 0, s>>>(c->d_inst, c->d_wall_unit, c->d_wallTf, a.F,
                                                                     a.wall);
     e = cudaGetLastError();
   }

@@ -187,6 +187,10 @@ class Solver:
     def set_wall_T(self, Tw, stream=None):
         self._set(L.FIELD_WALL_T, Tw, stream)
 
+    def set_wall_face_T(self, Tf, stream=None):
+        """Temperature of every boundary face ([total_wall_faces], instance-major)."""
+        self._set(L.FIELD_WALL_FACE_T, Tf, stream)
+
     def _set(self, which, data, stream):
         if isinstance(data, torch.Tensor) and data.is_cuda:
             d = data.to(torch.float64).contiguous()

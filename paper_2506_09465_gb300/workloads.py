@@ -19,6 +19,18 @@ class Instance:
     tau: np.ndarray          # [nb, ncells]
     wall_T: np.ndarray       # [2*dim]
     source: Optional[np.ndarray] = None
+    wall_face_T: Optional[np.ndarray] = None  # [boundary faces] or None (walls uniform)
+
+    def wall_faces(self):
+        """Boundary faces per wall, in the order -x, +x, -y, +y, -z, +z (the faces of the wall
+        normal to axis a run over the axes (a+1)%3, (a+2)%3, the first fastest)."""
+        n = list(self.n) + [1] * (3 - len(self.n))
+        return [n[(a + 1) % 3] * n[(a + 2) % 3] for a in range(self.dim) for _ in (0, 1)]
+
+    def face_temperatures(self) -> np.ndarray:
+        if self.wall_face_T is not None:
+            return np.asarray(self.wall_face_T, dtype=np.float64)
+        return np.concatenate([np.full(m, t) for m, t in zip(self.wall_faces(), self.wall_T)])
 
     @property
     def ncells(self) -> int:
@@ -76,6 +88,20 @@ def cavity(n=128, Kn=1.0, particles=1024) -> Workload:
     """2D gray square cavity (Sec. 4.4 shape): unit square, top wall T = 1, others 0."""
     inst = Instance(2, (n, n), (1.0, 1.0), np.full((1, n * n), Kn), np.array([0.0, 0.0, 0.0, 1.0]))
     return Workload(f"2D gray cavity {n}x{n} Kn={Kn}", np.array([1.0]), np.array([1.0]), [inst], particles, particles)
+
+
+def hot_segment_rectangle(Kn: float = 10.0, nx: int = 100, ny: int = 50, particles: int = 200) -> Workload:
+    """2D gray rectangle with a heated segment (Sec. 4.5 shape): L_x = 2 L_y = 5 L_1 with
+    L_1 = 1, a segment of length L_1 centred on the top wall at T = 1, every other boundary
+    face at T = 0, C = |v| = 1, tau = Kn (mean free path Kn L_1)."""
+    Lx, Ly = 5.0, 2.5
+    inst = Instance(2, (nx, ny), (Lx, Ly), np.full((1, nx * ny), Kn), np.zeros(4))
+    ft = np.zeros(2 * ny + 2 * nx)
+    xc = (np.arange(nx) + 0.5) * Lx / nx
+    ft[2 * ny + nx:] = np.where(np.abs(xc - Lx / 2) < 0.5, 1.0, 0.0)   # top wall faces
+    inst.wall_face_T = ft
+    return Workload(f"2D gray rectangle {nx}x{ny} hot top segment Kn={Kn}", np.array([1.0]), np.array([1.0]), [inst],
+                    particles, particles)
 
 
 def cavity_sweep(n=128, Kns=(0.01, 0.1, 1.0, 10.0), particles=1024) -> Workload:

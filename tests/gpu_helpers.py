@@ -12,7 +12,8 @@ def oracle_problem(inst, C, v, N, Nw, seed=0, instance=0):
     n_band = O.band_split(N, r) if len(C) > 1 else np.array([N])
     n_wall = O.band_split(Nw, C * v) if len(C) > 1 else np.array([Nw])
     return O.Problem(inst.dim, inst.n, inst.L, C, v, inst.tau, inst.wall_T, n_band, n_wall,
-                     source=inst.source, seed=seed, instance=instance)
+                     source=inst.source, seed=seed, instance=instance,
+                     wall_face_T=getattr(inst, "wall_face_T", None))
 
 
 def gpu_solver(insts, C, v, N, Nw, **opt):
@@ -20,8 +21,11 @@ def gpu_solver(insts, C, v, N, Nw, **opt):
     if not isinstance(insts, (list, tuple)):
         insts = [insts]
     grids = [GridSpec(i.dim, i.n, i.L) for i in insts]
-    return Solver(grids, [i.tau for i in insts], C, v, [i.wall_T for i in insts], [i.source for i in insts],
-                  particles_per_cell=N, particles_per_wall_face=Nw, **opt)
+    s = Solver(grids, [i.tau for i in insts], C, v, [i.wall_T for i in insts], [i.source for i in insts],
+               particles_per_cell=N, particles_per_wall_face=Nw, **opt)
+    if any(getattr(i, "wall_face_T", None) is not None for i in insts):
+        s.set_wall_face_T(np.concatenate([i.face_temperatures() for i in insts]))
+    return s
 
 
 def normwise_close(gpu, ora, rtol):

@@ -1,0 +1,85 @@
+"""Non-uniform walls (per-boundary-face temperatures) on the GPU: the heated-segment
+rectangle of Sec. 4.5 (L_x = 2 L_y = 5, a unit segment centred on the top wall at T = 1,
+every other face at T = 0). The FP64 path reproduces the oracle's tallies; the fast path
+conserves power per cell, matches the oracle's steady state within 5e-4, and in the
+ballistic limit sends the segment's power to the other walls in the proportions of the
+crossed-strings view factors."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from paper_2506_09465_gb300 import workloads as WL  # noqa: E402
+from gpu_helpers import gpu_solver, normwise_close, oracle_problem  # noqa: E402
+
+
+def cuda(x):
+    return torch.as_tensor(np.asarray(x, dtype=np.float64), device="cuda")
+
+
+@pytest.mark.parametrize("Kn", [10.0, 0.3])
+def test_hot_segment_sweep_fp64_matches_oracle(orc, Kn):
+    wl = WL.hot_segment_rectangle(Kn, 20, 10, 64)
+    inst = wl.instances[0]
+    rng = np.random.default_rng(5)
+    T = rng.uniform(0, 0.5, inst.ncells)
+    p = oracle_problem(inst, wl.C, wl.v, 64, 64, seed=2)
+    r = orc.sweep(p, T, 0)
+    s = gpu_solver(inst, wl.C, wl.v, 64, 64, precision=0, tally=0, schedule=0, seed=2)
+    assert s.layout.total_wall_faces == 60
+    g = s.sweep(cuda(T), 0)
+    for key, ora in (("R", r.R), ("W", r.W), ("F", r.F), ("wall", r.wall)):
+        ok, err = normwise_close(g[key].cpu().numpy(), ora, 1e-10)
+        assert ok, (key, err)
+    assert g["counters"].cpu().numpy().tolist() == r.counters.astype(np.int64).tolist()
+    s32 = gpu_solver(inst, wl.C, wl.v, 64, 64, seed=2)
+    g32 = s32.sweep(cuda(T), 0)
+    for key, ora in (("R", r.R), ("F", r.F), ("wall", r.wall)):
+        ok, err = normwise_close(g32[key].cpu().numpy(), ora, 2e-3)
+        assert ok, (key, err)
+
+
+def test_hot_segment_fast_path_conserves_and_reaches_oracle_steady_state(orc):
+    wl = WL.hot_segment_rectangle(1.0, 100, 50, 64)
+    inst = wl.instances[0]
+    s = gpu_solver(inst, wl.C, wl.v, 64, 64, seed=3)
+    T, it, res = s.solve_steady(None, 1e-8, 200)
+    assert res <= 1e-8
+    g = s.sweep(T, 0)
+    F = g["F"].cpu().numpy()
+    R = g["R"].cpu().numpy()
+    nx, ny = 100, 50
+    Fx = F[: (nx + 1) * ny].reshape(ny, nx + 1)
+    Fy = F[(nx + 1) * ny:].reshape(ny + 1, nx)
+    inflow = (Fx[:, :-1] - Fx[:, 1:] + Fy[:-1, :] - Fy[1:, :]).ravel()
+    V = 0.05 * 0.05
+    emitted = T.cpu().numpy() * V / 1.0
+    assert np.abs(inflow - (R - emitted)).max() <= 1e-6 * np.abs(emitted).max() + 1e-12
+    seg = 1.0 / 4.0   # power the segment emits per unit depth (C v T L_1 / 4)
+    # x-face tallies carry the window rounding (2^-27 of the largest weight per particle)
+    assert abs(g["wall"].cpu().numpy().sum() - seg - (emitted.sum() - R.sum())) <= 1e-7
+    p = oracle_problem(inst, wl.C, wl.v, 64, 64, seed=3)
+    T_o, _, res_o, _ = orc.solve_steady(p, np.zeros(inst.ncells), 1e-8, 200, frozen=True, newton=True, dT_ref=1.0)
+    assert np.abs(T.cpu().numpy() - T_o).max() <= 5e-4
+
+
+def test_hot_segment_ballistic_view_factors_on_gpu():
+    wl = WL.hot_segment_rectangle(1e9, 100, 50, 2048)
+    inst = wl.instances[0]
+    s = gpu_solver(inst, wl.C, wl.v, 2048, 2048, seed=4)
+    g = s.sweep(torch.zeros(inst.ncells, dtype=torch.float64, device="cuda"), 0)
+    wall = g["wall"].cpu().numpy()
+    emitted = 0.25
+    assert abs(wall.sum() - emitted) < 1e-9
+    d = lambda p, q: np.hypot(p[0] - q[0], p[1] - q[1])
+    a1, a2 = (2.0, 2.5), (3.0, 2.5)
+
+    def view(b1, b2):
+        return abs(d(a1, b2) + d(a2, b1) - d(a1, b1) - d(a2, b2)) / 2.0
+
+    F = {0: view((0.0, 2.5), (0.0, 0.0)), 1: view((5.0, 0.0), (5.0, 2.5)), 2: view((0.0, 0.0), (5.0, 0.0))}
+    n = 20 * 2048
+    for w, f in F.items():
+        assert abs(wall[w] / emitted - f) < 4.5 * np.sqrt(f * (1 - f) / n), (w, wall[w] / emitted, f)
+    assert abs(wall[3]) < 1e-12
