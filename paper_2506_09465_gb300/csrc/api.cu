@@ -45,6 +45,9 @@ namespace {
 
 iugkp_status ensure_k32(Ctx* c);
 
+// Multiplier of the device's exact division by d (>= 1): M = floor((2^32 - 1) / d).
+unsigned div_magic(int d) { return (unsigned)(0xFFFFFFFFull / (unsigned long long)std::max(1, d)); }
+
 // Largest-remainder split of N over weights r (r > 0, N >= nb): one particle per band
 // first, the remaining N - nb in proportion to r, leftovers to the largest fractional
 // parts (lower band first on ties).
@@ -104,8 +107,8 @@ void free_all(Ctx* c) {
                   c->d_pcg_iters, c->d_scalar, c->d_adj, c->d_mg, c->d_mg_diag, c->d_mg_dinv, c->d_mg_cx,
                   c->d_mg_cy, c->d_mg_cz, c->d_mg_cinv, c->d_mg_b, c->d_mg_x, c->d_mg_t, c->d_mg_r,
                   c->d_inst_beg, c->d_inst_end, c->d_inst_next, c->d_cost_prefix, c->d_window, c->d_wmax,
-                  c->d_group_rcp, c->d_rcp, c->d_wall_unit, c->d_all_beg, c->d_all_end, c->d_all_cost_prefix,
-                  c->d_all_group_rcp, c->d_R32, c->d_W32, c->d_F32, c->d_m2, c->d_wallTf};
+                  c->d_group_mag, c->d_mag, c->d_wall_unit, c->d_all_beg, c->d_all_end, c->d_all_cost_prefix,
+                  c->d_all_group_mag, c->d_R32, c->d_W32, c->d_F32, c->d_m2, c->d_wallTf};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (c->h_pinned) cudaFreeHost(c->h_pinned);
@@ -150,14 +153,15 @@ iugkp_status set_source(Ctx* c, const std::vector<double>& Q, const std::vector<
 // prefix sums of the estimated cost (particles x expected events per particle) and the
 // reciprocal of each group's emitter count.
 void staged_tables(const Ctx* c, const std::vector<Group>& groups, std::vector<long long>& beg,
-                   std::vector<long long>& end, std::vector<double>& prefix, double& total, std::vector<float>& grcp) {
+                   std::vector<long long>& end, std::vector<double>& prefix, double& total,
+                   std::vector<unsigned>& gmag) {
   beg.assign(c->n_inst, 0);
   end.assign(c->n_inst, 0);
   std::vector<double> cost(c->n_inst, 0.0);
   std::vector<int> seen(c->n_inst, 0);
-  grcp.clear();
+  gmag.clear();
   for (const Group& g : groups) {
-    grcp.push_back(1.0f / (float)std::max(1, g.n_emitters));
+    gmag.push_back(div_magic(g.n_emitters));
     const long long np = (long long)g.n_emitters * g.per_emitter;
     if (!seen[g.inst]) {
       beg[g.inst] = g.first_particle;
@@ -225,9 +229,9 @@ iugkp_status rebuild_forward_groups(Ctx* c) {
   // by instance); blocks start on instances in proportion to the estimated cost.
   std::vector<long long> beg, end;
   std::vector<double> prefix;
-  std::vector<float> grcp;
+  std::vector<unsigned> gmag;
   double tot = 0.0;
-  staged_tables(c, c->h_groups_fwd, beg, end, prefix, tot, grcp);
+  staged_tables(c, c->h_groups_fwd, beg, end, prefix, tot, gmag);
   c->cost_total = tot;
   // x-face window: all x-faces when they fit, else a centred run of them (the rest take
   // global atomics)
@@ -238,14 +242,14 @@ iugkp_status rebuild_forward_groups(Ctx* c) {
     const long long len = std::min<long long>(X, c->staged_cap);
     window[k] = make_int2((int)((X - len) / 2), (int)len);
   }
-  void* olds[] = {c->d_inst_beg, c->d_inst_end, c->d_cost_prefix, c->d_window, c->d_group_rcp};
+  void* olds[] = {c->d_inst_beg, c->d_inst_end, c->d_cost_prefix, c->d_window, c->d_group_mag};
   for (void* p : olds)
     if (p) cudaFree(p);
   c->d_inst_beg = c->d_inst_end = nullptr;
   c->d_cost_prefix = nullptr;
   c->d_window = nullptr;
-  c->d_group_rcp = nullptr;
-  if ((s = upload(c, &c->d_group_rcp, grcp)) != IUGKP_OK) return s;
+  c->d_group_mag = nullptr;
+  if ((s = upload(c, &c->d_group_mag, gmag)) != IUGKP_OK) return s;
   if ((s = upload(c, &c->d_inst_beg, beg)) != IUGKP_OK) return s;
   if ((s = upload(c, &c->d_inst_end, end)) != IUGKP_OK) return s;
   if ((s = upload(c, &c->d_cost_prefix, prefix)) != IUGKP_OK) return s;
@@ -616,22 +620,22 @@ iugkp_status iugkp_create_batch(int n, const iugkp_grid* g, const double* const*
   {
     std::vector<long long> beg, end;
     std::vector<double> prefix;
-    std::vector<float> grcp;
-    staged_tables(c, c->h_groups_all, beg, end, prefix, c->all_cost_total, grcp);
+    std::vector<unsigned> gmag;
+    staged_tables(c, c->h_groups_all, beg, end, prefix, c->all_cost_total, gmag);
     UP(c->d_all_beg, beg);
     UP(c->d_all_end, end);
     UP(c->d_all_cost_prefix, prefix);
-    UP(c->d_all_group_rcp, grcp);
+    UP(c->d_all_group_mag, gmag);
   }
   {
-    std::vector<float> rcp((size_t)5 * n);
+    std::vector<unsigned> mag((size_t)5 * n);
     for (int k = 0; k < n; ++k) {
       const InstDesc& in = c->h_inst[k];
-      rcp[k] = 1.0f / (float)in.n[0];
-      rcp[n + k] = 1.0f / (float)in.n[1];
-      for (int a = 0; a < 3; ++a) rcp[2 * n + 3 * k + a] = 1.0f / (float)in.n[(a + 1) % 3];
+      mag[k] = div_magic(in.n[0]);
+      mag[n + k] = div_magic(in.n[1]);
+      for (int a = 0; a < 3; ++a) mag[2 * n + 3 * k + a] = div_magic(in.n[(a + 1) % 3]);
     }
-    UP(c->d_rcp, rcp);
+    UP(c->d_mag, mag);
   }
   if ((s = dalloc(c, &c->d_inst_next, n)) != IUGKP_OK) return bail(s);
   if ((s = dalloc(c, &c->d_wmax, n)) != IUGKP_OK) return bail(s);

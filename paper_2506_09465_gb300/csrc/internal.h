@@ -134,16 +134,16 @@ struct Ctx {
   double cost_total = 0.0;
   int2* d_window = nullptr;      // [n_inst] {first x-face, count} of the shared-memory window
   unsigned long long* d_wmax = nullptr;  // [n_inst] bit patterns of the largest weight
-  float* d_group_rcp = nullptr;      // [forward groups]
+  unsigned* d_group_mag = nullptr;   // [forward groups] division magic of the emitter count
   double* d_wall_unit = nullptr;     // [n_inst * 6] power entering per face per unit wall T
   // adjoint re-trace over all groups (staged kernel)
   long long* d_all_beg = nullptr;
   long long* d_all_end = nullptr;
   double* d_all_cost_prefix = nullptr;
   double all_cost_total = 0.0;
-  float* d_all_group_rcp = nullptr;
+  unsigned* d_all_group_mag = nullptr;
   int adj_blocks_per_sm = 1;
-  float* d_rcp = nullptr;            // [n_inst * 5]: 1/n_x, 1/n_y, 1/n(o1) for walls normal to x, y, z
+  unsigned* d_mag = nullptr;         // [n_inst * 5]: division magics of n_x, n_y, n(o1) for walls normal to x, y, z
   int staged_cap = 0;           // x-faces per shared-memory window
   int staged_blocks_per_sm = 1;
   std::vector<double> h_taumean;  // [inst * nb]

@@ -23,10 +23,11 @@ struct StagedArgs {
   int warp_grab;                  // particles a warp claims at a time
   int refill;                     // idle lanes that trigger a refill (0: per-instance default)
   int walk_k;                     // crossings per lane between bulk steps
-  const float* group_rcp;         // [forward groups] 1 / particles per emitter
-  const float* rcp_n0;            // [n_inst] 1 / n_x
-  const float* rcp_n1;            // [n_inst] 1 / n_y
-  const float* rcp_wall;          // [n_inst * 3] 1 / (cells along the first tangential axis of each wall)
+  // division magics M = floor((2^32 - 1) / d) of the divisors d below
+  const unsigned* group_mag;      // [forward groups] d = emitters of the group
+  const unsigned* mag_n0;         // [n_inst] d = n_x
+  const unsigned* mag_n1;         // [n_inst] d = n_y
+  const unsigned* mag_wall;       // [n_inst * 3] d = cells along the first tangential axis of each wall
   // compensated FP32 tallies (IUGKP_TALLY_STAGED_K32): {high word, error word} per entry
   float2* R32;                    // [nb * total_cells]
   float2* W32;                    // [nb * total_cells] or null

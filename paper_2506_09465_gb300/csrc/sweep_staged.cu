@@ -44,14 +44,12 @@ __device__ __forceinline__ void flush_lcounts(LCounts& c, unsigned long long* ou
   }
 }
 
-// Exact n / d for n < 2^31 and d >= 1 from an FP32 reciprocal and integer fix-ups.
-__device__ __forceinline__ unsigned udiv(unsigned n, unsigned d, float rcp) {
-  unsigned q = (unsigned)((float)n * rcp);
-  int r = (int)(n - q * d);
-  q += (int)((float)r * rcp);
-  r = (int)(n - q * d);
-  if (r < 0) q -= 1;
-  else if (r >= (int)d) q += 1;
+// Exact n / d for n < 2^31 and d >= 1 with M = floor((2^32 - 1) / d) from the host: since
+// 2^32/d - 1 <= M < 2^32/d, umulhi(n, M) is floor(n/d) or one less, and one comparison of
+// the remainder fixes it. Integer operations only (conversions issue at a low rate here).
+__device__ __forceinline__ unsigned udiv(unsigned n, unsigned d, unsigned M) {
+  unsigned q = __umulhi(n, M);
+  q += (n - q * d >= d) ? 1u : 0u;
   return q;
 }
 
@@ -136,7 +134,7 @@ __global__ void group_wmax_kernel(SweepArgs A, unsigned long long* wmax_bits) {
 struct EmitCache {
   unsigned g_first, g_end;  // forward particle range of the cached group
   int g_idx, g_ne, g_kind, g_band;
-  float g_rcp;              // 1 / n_emitters
+  unsigned g_mag;           // division magic of n_emitters
   int e;
   double w;
 };
@@ -159,7 +157,7 @@ __device__ __forceinline__ bool staged_emit(const SweepArgs& A, const StagedArgs
     ec.g_ne = G.n_emitters;
     ec.g_kind = G.kind;
     ec.g_band = G.band;
-    ec.g_rcp = S.group_rcp[gi];
+    ec.g_mag = S.group_mag[gi];
     ec.e = -1;
   }
   band = ec.g_band;
@@ -169,7 +167,7 @@ __device__ __forceinline__ bool staged_emit(const SweepArgs& A, const StagedArgs
   // tallies rarely hit the same address at the same time. Draws are keyed by (emitter,
   // particle), so the order changes nothing else.
   const unsigned local = pid - ec.g_first;
-  const int q = (int)udiv(local, (unsigned)ec.g_ne, ec.g_rcp);
+  const int q = (int)udiv(local, (unsigned)ec.g_ne, ec.g_mag);
   const int e = (int)(local - (unsigned)q * (unsigned)ec.g_ne);
   const int n0 = in.n[0], n1 = in.n[1], n2 = in.n[2];
   const int kind = ec.g_kind;
@@ -190,13 +188,13 @@ __device__ __forceinline__ bool staged_emit(const SweepArgs& A, const StagedArgs
       f.i1 = 0;
       f.i2 = 0;
     } else {
-      const int r = (int)udiv((unsigned)e, (unsigned)n0, S.rcp_n0[k]);
+      const int r = (int)udiv((unsigned)e, (unsigned)n0, S.mag_n0[k]);
       f.i0 = e - r * n0;
       if (DIM == 2) {
         f.i1 = r;
         f.i2 = 0;
       } else {
-        f.i2 = (int)udiv((unsigned)r, (unsigned)n1, S.rcp_n1[k]);
+        f.i2 = (int)udiv((unsigned)r, (unsigned)n1, S.mag_n1[k]);
         f.i1 = r - f.i2 * n1;
       }
     }
@@ -239,7 +237,7 @@ __device__ __forceinline__ bool staged_emit(const SweepArgs& A, const StagedArgs
     const int a = wl >> 1, side = wl & 1;
     // faces of wall a are enumerated over (o1, o2) = ((a+1)%3, (a+2)%3), o1 fastest
     const int no1 = a == 0 ? n1 : (a == 1 ? n2 : n0);
-    const int j2 = (int)udiv((unsigned)e, (unsigned)no1, S.rcp_wall[k * 3 + a]);
+    const int j2 = (int)udiv((unsigned)e, (unsigned)no1, S.mag_wall[k * 3 + a]);
     const int j1 = e - j2 * no1;
     long long face;
     if (a == 0) {
@@ -377,6 +375,7 @@ __global__ void __launch_bounds__(STAGED_NT, 1) sweep_staged_kernel(SweepArgs A,
     const int2 wd = useF ? S.window[k] : make_int2(0, 0);
     const int wbase = wd.x;
     const unsigned wlen = (unsigned)wd.y;
+    const bool wfull = wbase == 0 && (long long)wlen == (long long)(n0 + 1) * n1 * n2;
     for (unsigned i = threadIdx.x; i < wlen; i += STAGED_NT) win[i] = WIN_BIAS;
     __syncthreads();
     const double wmax = S.wmax[k];
@@ -527,6 +526,7 @@ __global__ void __launch_bounds__(STAGED_NT, 1) sweep_staged_kernel(SweepArgs A,
               const bool flat = !(f.d1 < INFINITY);
               f.D = flat ? -1.f : __fdividef(f.t0 - f.t1, f.d1);
               f.tex = flat ? 0.f : __fdividef(f.d0, f.d1);
+              f.i2 = m1 - 1;  // largest count of y-faces a row index may take
             }
             tally = kend > 0;
             alive = tally;
@@ -539,41 +539,51 @@ __global__ void __launch_bounds__(STAGED_NT, 1) sweep_staged_kernel(SweepArgs A,
       if (tally) {
         const int kstop = min(kend, kcur + S.walk_k);
         float fk = (float)kcur;  // the item index in FP32, advanced without conversions
+        // 64-bit sums kept as 32-bit low words in the window plus carries added to the FP64
+        // face: the old word tells whether an addition wrapped (rare: words start at 2^31
+        // and one contribution is at most 2^26)
+        auto window_add = [&](int xface, unsigned rel) {
+          const unsigned old = atomicAdd(&win[rel], qwx);
+          const int carry = ((int)qwx >> 31) + (old + qwx < old ? 1 : 0);
+          if (carry) atomicAdd(&A.F[face_off + xface], (double)carry * S.wmax[k] * WIN_CARRY);
+        };
+        if (DIM == 2 && wfull) {
+          // every x-face of the instance is in the window; rows need only the upper bound
+          // f.i2 = faces before the y-wall (the lower bound holds by construction)
 #pragma unroll 1
-        for (; kcur < kstop; ++kcur, fk += 1.f) {
-          if (DIM == 3 && fk >= f.tex) {
-            // y-face item: the (kcur - kx)-th face normal to y along the segment
-            const float fm = fk - f.tex;  // exact: both are small integers
-            const int mm = ceil_count(fm);
-            const float tm = fmaf(fm, f.d1, f.t1);
-            const int col = clampi(f.i0 + f.s0 * faces_before(tm, f.t0, f.d0), n0);
-            const int lay = clampi(f.i2 + f.s2 * faces_before(tm, f.t2, f.d2), n2);
-            const int jf = f.s1 > 0 ? f.i1 + 1 + mm : f.i1 - mm;
-            const long long fi = face_off + fax1 + col + (long long)n0 * (jf + (long long)(n1 + 1) * lay);
-            if (K32) tally_k32(&S.F32[fi], f.s1 > 0 ? w : -w);
-            else atomicAdd(&A.F[fi], f.s1 > 0 ? w : -w);
-            continue;
+          for (; kcur < kstop; ++kcur, fk += 1.f) {
+            const int row = f.i1 + f.s1 * min(ceil_count(fmaf(fk, f.tex, f.D)), f.i2);
+            const int xface = (f.s0 > 0 ? f.i0 + 1 + kcur : f.i0 - kcur) + sy_xf * row;
+            window_add(xface, (unsigned)xface);
           }
-          int xface = f.s0 > 0 ? f.i0 + 1 + kcur : f.i0 - kcur;
-          if (DIM == 2) {
-            xface += sy_xf * clampi(f.i1 + f.s1 * ceil_count(fmaf(fk, f.tex, f.D)), n1);
-          } else if (DIM == 3) {
-            const float tk = fmaf(fk, f.d0, f.t0);
-            xface += sy_xf * clampi(f.i1 + f.s1 * faces_before(tk, f.t1, f.d1), n1) +
-                     sz_xf * clampi(f.i2 + f.s2 * faces_before(tk, f.t2, f.d2), n2);
-          }
-          const unsigned rel = (unsigned)(xface - wbase);
-          if (rel < wlen) {
-            // 64-bit sum kept as a 32-bit low word here plus carries added to the FP64
-            // face: the old word tells whether this addition wrapped (rare: the word
-            // starts at 2^31 and one contribution is at most 2^26)
-            const unsigned old = atomicAdd(&win[rel], qwx);
-            const int carry = ((int)qwx >> 31) + (old + qwx < old ? 1 : 0);
-            if (carry) atomicAdd(&A.F[face_off + xface], (double)carry * S.wmax[k] * WIN_CARRY);
-          } else if (K32) {
-            tally_k32(&S.F32[face_off + xface], f.s0 > 0 ? w : -w);
-          } else {
-            atomicAdd(&A.F[face_off + xface], f.s0 > 0 ? w : -w);
+        } else {
+#pragma unroll 1
+          for (; kcur < kstop; ++kcur, fk += 1.f) {
+            if (DIM == 3 && fk >= f.tex) {
+              // y-face item: the (kcur - kx)-th face normal to y along the segment
+              const float fm = fk - f.tex;  // exact: both are small integers
+              const int mm = ceil_count(fm);
+              const float tm = fmaf(fm, f.d1, f.t1);
+              const int col = clampi(f.i0 + f.s0 * faces_before(tm, f.t0, f.d0), n0);
+              const int lay = clampi(f.i2 + f.s2 * faces_before(tm, f.t2, f.d2), n2);
+              const int jf = f.s1 > 0 ? f.i1 + 1 + mm : f.i1 - mm;
+              const long long fi = face_off + fax1 + col + (long long)n0 * (jf + (long long)(n1 + 1) * lay);
+              if (K32) tally_k32(&S.F32[fi], f.s1 > 0 ? w : -w);
+              else atomicAdd(&A.F[fi], f.s1 > 0 ? w : -w);
+              continue;
+            }
+            int xface = f.s0 > 0 ? f.i0 + 1 + kcur : f.i0 - kcur;
+            if (DIM == 2) {
+              xface += sy_xf * (f.i1 + f.s1 * min(ceil_count(fmaf(fk, f.tex, f.D)), f.i2));
+            } else if (DIM == 3) {
+              const float tk = fmaf(fk, f.d0, f.t0);
+              xface += sy_xf * clampi(f.i1 + f.s1 * faces_before(tk, f.t1, f.d1), n1) +
+                       sz_xf * clampi(f.i2 + f.s2 * faces_before(tk, f.t2, f.d2), n2);
+            }
+            const unsigned rel = (unsigned)(xface - wbase);
+            if (rel < wlen) window_add(xface, rel);
+            else if (K32) tally_k32(&S.F32[face_off + xface], f.s0 > 0 ? w : -w);
+            else atomicAdd(&A.F[face_off + xface], f.s0 > 0 ? w : -w);
           }
         }
         if (kcur >= kend) {
@@ -726,10 +736,10 @@ cudaError_t launch_sweep_staged(const Ctx* c, const SweepArgs& a, cudaStream_t s
   S.warp_grab = c->opt.warp_grab > 0 ? c->opt.warp_grab : 256;
   S.walk_k = c->opt.walk_k > 0 ? c->opt.walk_k : 16;
   S.refill = c->opt.refill_lanes;
-  S.group_rcp = c->d_group_rcp;
-  S.rcp_n0 = c->d_rcp;
-  S.rcp_n1 = c->d_rcp + c->n_inst;
-  S.rcp_wall = c->d_rcp + 2 * c->n_inst;
+  S.group_mag = c->d_group_mag;
+  S.mag_n0 = c->d_mag;
+  S.mag_n1 = c->d_mag + c->n_inst;
+  S.mag_wall = c->d_mag + 2 * c->n_inst;
   cudaError_t e = cudaMemcpyAsync(c->d_inst_next, c->d_inst_beg, c->n_inst * sizeof(long long),
                                   cudaMemcpyDeviceToDevice, s);
   if (e != cudaSuccess) return e;
@@ -802,10 +812,10 @@ cudaError_t launch_adjoint_staged(const Ctx* c, const SweepArgs& a, cudaStream_t
   S.warp_grab = c->opt.warp_grab > 0 ? c->opt.warp_grab : 256;
   S.walk_k = c->opt.walk_k > 0 ? c->opt.walk_k : 16;
   S.refill = c->opt.refill_lanes;
-  S.group_rcp = c->d_all_group_rcp;
-  S.rcp_n0 = c->d_rcp;
-  S.rcp_n1 = c->d_rcp + c->n_inst;
-  S.rcp_wall = c->d_rcp + 2 * c->n_inst;
+  S.group_mag = c->d_all_group_mag;
+  S.mag_n0 = c->d_mag;
+  S.mag_n1 = c->d_mag + c->n_inst;
+  S.mag_wall = c->d_mag + 2 * c->n_inst;
   cudaError_t e = cudaMemcpyAsync(c->d_inst_next, c->d_all_beg, c->n_inst * sizeof(long long),
                                   cudaMemcpyDeviceToDevice, s);
   if (e != cudaSuccess) return e;

@@ -106,3 +106,22 @@ def test_fp32_uniform_from_mantissa_bits_is_exact():
     ref = ((2 * m.astype(np.float64) + 1) / 16777216.0).astype(np.float32)
     assert np.float32(0.99999994) == np.float32(1.0 - 2.0 ** -24)
     assert np.array_equal(fast, ref) and np.array_equal(ref.astype(np.float64), (2 * m.astype(np.float64) + 1) / 16777216.0)
+
+
+def test_integer_division_by_multiply_high_is_exact():
+    # The fast path divides particle and cell indices n < 2^31 by d >= 1 as
+    # q = umulhi(n, M) + [n - q d >= d] with M = floor((2^32 - 1) / d); checked here with
+    # exact integers on divisors and indices that include the extremes and exact multiples.
+    rng = np.random.default_rng(0)
+    ds = [1, 2, 3, 7, 100, 101, 128, 255, 256, 1023, 16384, 65535, 65536, 1000003, 2 ** 30, 2 ** 31 - 1]
+    ds += [int(x) for x in rng.integers(1, 2 ** 31, 40)]
+    for d in ds:
+        M = (2 ** 32 - 1) // d
+        ns = {0, 1, d - 1, d, d + 1, 2 ** 31 - 1, (2 ** 31 - 1) // d * d, (2 ** 31 - 1) // d * d - 1}
+        ns |= {int(x) for x in rng.integers(0, 2 ** 31, 200)}
+        for n in ns:
+            if n < 0 or n >= 2 ** 31:
+                continue
+            q = (n * M) >> 32
+            q += 1 if n - q * d >= d else 0
+            assert q == n // d, (n, d)
