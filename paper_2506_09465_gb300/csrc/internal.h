@@ -115,6 +115,7 @@ struct Ctx {
   double* h_pinned = nullptr;    // [8 + n_inst] host readback
   // multigrid preconditioner of the Newton correction (mg_setup.cu, mgpcg.cu)
   struct InstMG* d_mg = nullptr;
+  size_t mg_smem_bytes = 0;      // dynamic shared memory of the PCG kernel (CTA 0's coarse levels)
   float* d_mg_diag = nullptr;
   float* d_mg_dinv = nullptr;
   float* d_mg_cx = nullptr;
@@ -174,6 +175,8 @@ cudaError_t launch_sweep_staged(const Ctx* c, const SweepArgs& a, cudaStream_t s
 cudaError_t configure_staged(Ctx* c);
 cudaError_t launch_adjoint_staged(const Ctx* c, const SweepArgs& a, cudaStream_t s);
 cudaError_t launch_mgpcg(const Ctx* c, const double* rhs, cudaStream_t s);
+size_t mg_solo_smem_bytes(const std::vector<InstMG>& h_mg);
+cudaError_t configure_mgpcg(Ctx* c, size_t smem);
 iugkp_status build_multigrid(Ctx* c, const std::vector<double>& diag, const std::vector<double>& cx,
                              const std::vector<double>& cy, const std::vector<double>& cz);
 cudaError_t launch_grad_source(const Ctx* c, const double* at, double* grad, cudaStream_t s);

@@ -157,6 +157,8 @@ iugkp_status build_multigrid(Ctx* c, const std::vector<double>& diag, const std:
   if ((s = up(&c->d_mg_x, zeros)) != IUGKP_OK) return s;
   if ((s = up(&c->d_mg_t, zeros)) != IUGKP_OK) return s;
   if ((s = up(&c->d_mg_r, zeros)) != IUGKP_OK) return s;
+  const cudaError_t e = configure_mgpcg(c, mg_solo_smem_bytes(mgs));
+  if (e != cudaSuccess) return fail(c, IUGKP_ECUDA, std::string("multigrid kernel set-up: ") + cudaGetErrorString(e));
   return IUGKP_OK;
 }
 

@@ -89,46 +89,98 @@ __device__ __forceinline__ void level_coords(const int* n, long long i, int& x, 
   z = (int)(t / n[1]);
 }
 
-// y = A_l x on level l (FP32 stencil), for one cell.
+// y = A_l x on level l (FP32 stencil), for one cell; LD loads x (through L2 when other
+// CTAs of the cluster wrote it, plainly when it is in this CTA's shared memory).
+template <class LD>
 __device__ __forceinline__ float level_apply(const float* dg, const float* cx, const float* cy, const float* cz,
                                              const float* x, const int* n, int dim, long long i, long long nc) {
   const long long sy = n[0], sz = (long long)n[0] * n[1];
-  float q = dg[i] * __ldcg(&x[i]);
-  if (i + 1 < nc) q -= cx[i] * __ldcg(&x[i + 1]);
-  if (i >= 1) q -= cx[i - 1] * __ldcg(&x[i - 1]);
+  float q = dg[i] * LD::ld(&x[i]);
+  if (i + 1 < nc) q -= cx[i] * LD::ld(&x[i + 1]);
+  if (i >= 1) q -= cx[i - 1] * LD::ld(&x[i - 1]);
   if (dim >= 2) {
-    if (i + sy < nc) q -= cy[i] * __ldcg(&x[i + sy]);
-    if (i >= sy) q -= cy[i - sy] * __ldcg(&x[i - sy]);
+    if (i + sy < nc) q -= cy[i] * LD::ld(&x[i + sy]);
+    if (i >= sy) q -= cy[i - sy] * LD::ld(&x[i - sy]);
   }
   if (dim >= 3) {
-    if (i + sz < nc) q -= cz[i] * __ldcg(&x[i + sz]);
-    if (i >= sz) q -= cz[i - sz] * __ldcg(&x[i - sz]);
+    if (i + sz < nc) q -= cz[i] * LD::ld(&x[i + sz]);
+    if (i >= sz) q -= cz[i - sz] * LD::ld(&x[i - sz]);
   }
   return q;
 }
 
-// Damped Jacobi sweeps on level l from the iterate in x: ping-pong between x and t;
-// returns the buffer that holds the result. Every sweep ends with a cluster barrier.
-template <int NT, int CS>
-__device__ __forceinline__ float* jacobi(const MGArgs& A, const InstMG& m, int l, cg::cluster_group& cl, int rank,
-                                         int sweeps, float* x, float* t) {
-  const long long nc = m.nc[l];
-  const long long chunk = (nc + CS - 1) / CS, lo = rank * chunk, hi = min(nc, lo + chunk);
+// Who works on a level: the whole cluster (cells split in contiguous ranges over the CTAs,
+// level vectors in global memory read through L2, cluster barriers) or CTA 0 alone (level
+// vectors in its shared memory, block barriers). Levels of at most MG_SOLO_CELLS cells go
+// to CTA 0: their work is small, and every phase of a level waits for the previous one, so
+// the latency of a barrier and of an L2 round trip is what they would cost on the cluster.
+struct ClusterTeam {
+  int part;
+  static constexpr bool solo = false;
+  __device__ static float ld(const float* p) { return __ldcg(p); }
+};
+struct SoloTeam {
+  static constexpr bool solo = true;
+  __device__ static float ld(const float* p) { return *p; }
+};
+
+// The vectors of one level (b, x, t, r) and its operator coefficients.
+struct LevelView {
+  const float *dg, *dinv, *cx, *cy, *cz;
+  float *b, *x, *t, *r;
+};
+
+__device__ __forceinline__ LevelView global_view(const MGArgs& A, const InstMG& m, int l) {
   const long long o = m.off[l];
-  const float* dg = A.ldiag + o;
-  const float* dinv = A.ldiag_inv + o;
-  const float* cx = A.lcx + o;
-  const float* cy = A.lcy + o;
-  const float* cz = A.lcz + o;
-  const float* b = A.lb + o;
-  float* src = x;
-  float* dst = t;
-  for (int s = 0; s < sweeps; ++s) {
+  return {A.ldiag + o, A.ldiag_inv + o, A.lcx + o, A.lcy + o, A.lcz + o, A.lb + o, A.lx + o, A.lt + o, A.lr + o};
+}
+
+// Shared-memory layout of CTA 0's levels ls .. L-1: per level b, x, t, r of nc floats.
+__device__ __forceinline__ LevelView solo_view(const MGArgs& A, const InstMG& m, int l, int ls, float* smem) {
+  const long long o = m.off[l];
+  long long so = 0;
+  for (int j = ls; j < l; ++j) so += 4 * m.nc[j];
+  float* base = smem + so;
+  const long long nc = m.nc[l];
+  return {A.ldiag + o, A.ldiag_inv + o, A.lcx + o, A.lcy + o, A.lcz + o, base, base + nc, base + 2 * nc, base + 3 * nc};
+}
+
+template <class TM, int NT, int CS>
+__device__ __forceinline__ void team_range(const TM& tm, long long nc, long long& lo, long long& hi) {
+  if constexpr (TM::solo) {
+    lo = 0;
+    hi = nc;
+  } else {
+    const long long chunk = (nc + CS - 1) / CS;
+    lo = (long long)tm.part * chunk;
+    hi = min(nc, lo + chunk);
+  }
+}
+
+template <class TM>
+__device__ __forceinline__ void team_sync(cg::cluster_group& cl) {
+  if constexpr (TM::solo) __syncthreads();
+  else cl.sync();
+}
+
+constexpr long long MG_SOLO_CELLS = 4096;
+
+// Damped Jacobi sweeps on a level from the iterate in v.x: ping-pong between v.x and v.t;
+// returns the buffer that holds the result. Every sweep ends with a team barrier.
+template <class TM, int NT, int CS>
+__device__ __forceinline__ float* jacobi(const MGArgs& A, const InstMG& m, int l, const LevelView& v, const TM& tm,
+                                         cg::cluster_group& cl, int sweeps) {
+  const long long nc = m.nc[l];
+  long long lo, hi;
+  team_range<TM, NT, CS>(tm, nc, lo, hi);
+  float* src = v.x;
+  float* dst = v.t;
+  for (int sw = 0; sw < sweeps; ++sw) {
     for (long long i = lo + threadIdx.x; i < hi; i += NT) {
-      const float ax = level_apply(dg, cx, cy, cz, src, m.n[l], m.dim, i, nc);
-      dst[i] = src[i] + A.omega * (b[i] - ax) * dinv[i];
+      const float ax = level_apply<TM>(v.dg, v.cx, v.cy, v.cz, src, m.n[l], m.dim, i, nc);
+      dst[i] = src[i] + A.omega * (v.b[i] - ax) * v.dinv[i];
     }
-    cl.sync();
+    team_sync<TM>(cl);
     float* tmp = src;
     src = dst;
     dst = tmp;
@@ -136,99 +188,127 @@ __device__ __forceinline__ float* jacobi(const MGArgs& A, const InstMG& m, int l
   return src;
 }
 
-// One V-cycle: Z = M^{-1} Rr over this instance (all CTAs of the cluster take part).
+// Downward half of the V-cycle on level l: pre-smoothing from x = 0, residual, and its
+// restriction into vc.b, the right-hand side of level l + 1 (sum over the children, P^T r).
+template <class TM, int NT, int CS>
+__device__ void vdown(const MGArgs& A, const InstMG& m, int l, const LevelView& v, const LevelView& vc, const TM& tm,
+                      cg::cluster_group& cl) {
+  const long long nc = m.nc[l];
+  long long lo, hi;
+  team_range<TM, NT, CS>(tm, nc, lo, hi);
+  // first sweep from x = 0: x = omega D^{-1} b (no neighbour reads)
+  for (long long i = lo + threadIdx.x; i < hi; i += NT) v.x[i] = A.omega * v.b[i] * v.dinv[i];
+  team_sync<TM>(cl);
+  float* src = jacobi<TM, NT, CS>(A, m, l, v, tm, cl, A.nu - 1);
+  // residual of the smoothed iterate; the iterate is moved into x if it ended in t
+  for (long long i = lo + threadIdx.x; i < hi; i += NT) {
+    const float ax = level_apply<TM>(v.dg, v.cx, v.cy, v.cz, src, m.n[l], m.dim, i, nc);
+    v.r[i] = v.b[i] - ax;
+    if (src != v.x) v.x[i] = src[i];
+  }
+  team_sync<TM>(cl);
+  const long long ncc = m.nc[l + 1];
+  long long clo, chi;
+  team_range<TM, NT, CS>(tm, ncc, clo, chi);
+  for (long long I = clo + threadIdx.x; I < chi; I += NT) {
+    int X0, Y0, Z0;
+    level_coords(m.n[l + 1], I, X0, Y0, Z0);
+    float sum = 0.f;
+    for (int dz = 0; dz < (m.dim >= 3 ? 2 : 1); ++dz)
+      for (int dy = 0; dy < (m.dim >= 2 ? 2 : 1); ++dy)
+        for (int dx = 0; dx < 2; ++dx) {
+          const int fx = 2 * X0 + dx, fy = 2 * Y0 + dy, fz = 2 * Z0 + dz;
+          if (fx < m.n[l][0] && fy < m.n[l][1] && fz < m.n[l][2])
+            sum += TM::ld(&v.r[fx + (long long)m.n[l][0] * (fy + (long long)m.n[l][1] * fz)]);
+        }
+    vc.b[I] = sum;
+  }
+  team_sync<TM>(cl);
+}
+
+// Coarsest level: x = Ainv b (dense).
+template <class TM, int NT, int CS>
+__device__ void vcoarsest(const MGArgs& A, const InstMG& m, const LevelView& v, const TM& tm, cg::cluster_group& cl) {
+  const int l = m.levels - 1;
+  const long long nc = m.nc[l];
+  long long lo, hi;
+  team_range<TM, NT, CS>(tm, nc, lo, hi);
+  const float* inv = A.cinv + m.cinv_off;
+  for (long long i = lo + threadIdx.x; i < hi; i += NT) {
+    float sum = 0.f;
+    for (long long j = 0; j < nc; ++j) sum += inv[i * nc + j] * TM::ld(&v.b[j]);
+    v.x[i] = sum;
+  }
+  team_sync<TM>(cl);
+}
+
+// Upward half on level l: prolongation of the level l + 1 correction vc.x (injection
+// scaled by alpha), then post-smoothing.
+template <class TM, int NT, int CS>
+__device__ void vup(const MGArgs& A, const InstMG& m, int l, const LevelView& v, const LevelView& vc, const TM& tm,
+                    cg::cluster_group& cl) {
+  const long long nc = m.nc[l];
+  long long lo, hi;
+  team_range<TM, NT, CS>(tm, nc, lo, hi);
+  for (long long i = lo + threadIdx.x; i < hi; i += NT) {
+    int X0, Y0, Z0;
+    level_coords(m.n[l], i, X0, Y0, Z0);
+    const long long I = (X0 >> 1) + (long long)m.n[l + 1][0] * ((Y0 >> 1) + (long long)m.n[l + 1][1] * (Z0 >> 1));
+    v.x[i] += A.alpha * TM::ld(&vc.x[I]);
+  }
+  team_sync<TM>(cl);
+  float* src = jacobi<TM, NT, CS>(A, m, l, v, tm, cl, A.nu);
+  if (src != v.x) {
+    for (long long i = lo + threadIdx.x; i < hi; i += NT) v.x[i] = src[i];
+    team_sync<TM>(cl);
+  }
+}
+
+// First level of an instance that CTA 0 handles alone (the coarsest at the latest).
+__host__ __device__ __forceinline__ int solo_level(const InstMG& m) {
+  int ls = 0;
+  while (ls < m.levels - 1 && m.nc[ls] > MG_SOLO_CELLS) ++ls;
+  return ls;
+}
+
+// One V-cycle: Z = M^{-1} Rr over this instance. The cluster shares the levels above
+// solo_level; CTA 0 copies that level's right-hand side into its shared memory, runs the
+// rest of the cycle there, and writes the level's correction back for the cluster.
 template <int NT, int CS>
-__device__ void vcycle(const MGArgs& A, const InstMG& m, cg::cluster_group& cl, int rank, long long cell_off) {
+__device__ void vcycle(const MGArgs& A, const InstMG& m, cg::cluster_group& cl, int rank, long long cell_off,
+                       float* smem) {
+  const ClusterTeam all{rank};
+  const SoloTeam solo;
   const int L = m.levels;
+  const int ls = solo_level(m);
   {
-    const long long nc = m.nc[0];
-    const long long chunk = (nc + CS - 1) / CS, lo = rank * chunk, hi = min(nc, lo + chunk);
+    long long lo, hi;
+    team_range<ClusterTeam, NT, CS>(all, m.nc[0], lo, hi);
     float* b = A.lb + m.off[0];
     for (long long i = lo + threadIdx.x; i < hi; i += NT) b[i] = (float)A.Rr[cell_off + i];
   }
   cl.sync();
-  for (int l = 0; l < L - 1; ++l) {
-    const long long nc = m.nc[l];
-    const long long chunk = (nc + CS - 1) / CS, lo = rank * chunk, hi = min(nc, lo + chunk);
-    const long long o = m.off[l];
-    const float* dg = A.ldiag + o;
-    const float* dinv = A.ldiag_inv + o;
-    const float* cx = A.lcx + o;
-    const float* cy = A.lcy + o;
-    const float* cz = A.lcz + o;
-    const float* b = A.lb + o;
-    float* x = A.lx + o;
-    float* t = A.lt + o;
-    float* r = A.lr + o;
-    // first sweep from x = 0: x = omega D^{-1} b (no neighbour reads)
-    for (long long i = lo + threadIdx.x; i < hi; i += NT) x[i] = A.omega * b[i] * dinv[i];
-    cl.sync();
-    float* src = jacobi<NT, CS>(A, m, l, cl, rank, A.nu - 1, x, t);
-    // residual of the smoothed iterate; the iterate is moved into x if it ended in t
-    for (long long i = lo + threadIdx.x; i < hi; i += NT) {
-      const float ax = level_apply(dg, cx, cy, cz, src, m.n[l], m.dim, i, nc);
-      r[i] = b[i] - ax;
-      if (src != x) x[i] = src[i];
-    }
-    cl.sync();
-    // restrict: b_{l+1}[I] = sum of the children's residuals (P^T r)
-    const long long ncc = m.nc[l + 1];
-    const long long cchunk = (ncc + CS - 1) / CS, clo = rank * cchunk, chi = min(ncc, clo + cchunk);
-    float* bc = A.lb + m.off[l + 1];
-    for (long long I = clo + threadIdx.x; I < chi; I += NT) {
-      int X0, Y0, Z0;
-      level_coords(m.n[l + 1], I, X0, Y0, Z0);
-      float s = 0.f;
-      for (int dz = 0; dz < (m.dim >= 3 ? 2 : 1); ++dz)
-        for (int dy = 0; dy < (m.dim >= 2 ? 2 : 1); ++dy)
-          for (int dx = 0; dx < 2; ++dx) {
-            const int fx = 2 * X0 + dx, fy = 2 * Y0 + dy, fz = 2 * Z0 + dz;
-            if (fx < m.n[l][0] && fy < m.n[l][1] && fz < m.n[l][2])
-              s += __ldcg(&r[fx + (long long)m.n[l][0] * (fy + (long long)m.n[l][1] * fz)]);
-          }
-      bc[I] = s;
-    }
-    cl.sync();
+  for (int l = 0; l < ls; ++l) vdown<ClusterTeam, NT, CS>(A, m, l, global_view(A, m, l), global_view(A, m, l + 1), all, cl);
+  if (rank == 0) {
+    const LevelView top = solo_view(A, m, ls, ls, smem);
+    const float* gb = A.lb + m.off[ls];
+    for (long long i = threadIdx.x; i < m.nc[ls]; i += NT) top.b[i] = __ldcg(&gb[i]);
+    __syncthreads();
+    for (int l = ls; l < L - 1; ++l)
+      vdown<SoloTeam, NT, CS>(A, m, l, solo_view(A, m, l, ls, smem), solo_view(A, m, l + 1, ls, smem), solo, cl);
+    vcoarsest<SoloTeam, NT, CS>(A, m, solo_view(A, m, L - 1, ls, smem), solo, cl);
+    for (int l = L - 2; l >= ls; --l)
+      vup<SoloTeam, NT, CS>(A, m, l, solo_view(A, m, l, ls, smem), solo_view(A, m, l + 1, ls, smem), solo, cl);
+    float* gx = A.lx + m.off[ls];
+    for (long long i = threadIdx.x; i < m.nc[ls]; i += NT) gx[i] = top.x[i];
   }
-  {  // coarsest level: x = Ainv b (dense)
-    const int l = L - 1;
-    const long long nc = m.nc[l];
-    const long long chunk = (nc + CS - 1) / CS, lo = rank * chunk, hi = min(nc, lo + chunk);
-    const float* inv = A.cinv + m.cinv_off;
-    const float* b = A.lb + m.off[l];
-    float* x = A.lx + m.off[l];
-    for (long long i = lo + threadIdx.x; i < hi; i += NT) {
-      float s = 0.f;
-      for (long long j = 0; j < nc; ++j) s += inv[i * nc + j] * __ldcg(&b[j]);
-      x[i] = s;
-    }
-    cl.sync();
-  }
-  for (int l = L - 2; l >= 0; --l) {
-    const long long nc = m.nc[l];
-    const long long chunk = (nc + CS - 1) / CS, lo = rank * chunk, hi = min(nc, lo + chunk);
-    const long long o = m.off[l];
-    float* x = A.lx + o;
-    float* t = A.lt + o;
-    const float* xc = A.lx + m.off[l + 1];
-    for (long long i = lo + threadIdx.x; i < hi; i += NT) {
-      int X0, Y0, Z0;
-      level_coords(m.n[l], i, X0, Y0, Z0);
-      const long long I = (X0 >> 1) + (long long)m.n[l + 1][0] * ((Y0 >> 1) + (long long)m.n[l + 1][1] * (Z0 >> 1));
-      x[i] += A.alpha * __ldcg(&xc[I]);
-    }
-    cl.sync();
-    float* src = jacobi<NT, CS>(A, m, l, cl, rank, A.nu, x, t);
-    if (src != x) {
-      for (long long i = lo + threadIdx.x; i < hi; i += NT) x[i] = src[i];
-      cl.sync();
-    }
-  }
+  cl.sync();
+  for (int l = ls - 1; l >= 0; --l) vup<ClusterTeam, NT, CS>(A, m, l, global_view(A, m, l), global_view(A, m, l + 1), all, cl);
   {
-    const long long nc = m.nc[0];
-    const long long chunk = (nc + CS - 1) / CS, lo = rank * chunk, hi = min(nc, lo + chunk);
+    long long lo, hi;
+    team_range<ClusterTeam, NT, CS>(all, m.nc[0], lo, hi);
     const float* x = A.lx + m.off[0];
-    for (long long i = lo + threadIdx.x; i < hi; i += NT) A.Z[cell_off + i] = (double)x[i];
+    for (long long i = lo + threadIdx.x; i < hi; i += NT) A.Z[cell_off + i] = (double)__ldcg(&x[i]);
   }
 }
 
@@ -236,6 +316,7 @@ template <int NT, int CS>
 __global__ void __launch_bounds__(NT) mgpcg_kernel(MGArgs A) {
   __shared__ double sh[4 * 32];
   __shared__ double slot[8];
+  extern __shared__ float mg_smem[];  // CTA 0: the levels it handles alone
   cg::cluster_group cl = cg::this_cluster();
   const int rank = (int)cl.block_rank();
   const int k = blockIdx.x / CS;
@@ -260,7 +341,7 @@ __global__ void __launch_bounds__(NT) mgpcg_kernel(MGArgs A) {
     return;
   }
   const double tol2 = A.rtol * A.rtol * bb;
-  vcycle<NT, CS>(A, m, cl, rank, off);
+  vcycle<NT, CS>(A, m, cl, rank, off, mg_smem);
   v[0] = 0.0;
   for (long long i = lo + threadIdx.x; i < hi; i += NT) {
     const double zi = A.Z[off + i];
@@ -305,7 +386,7 @@ __global__ void __launch_bounds__(NT) mgpcg_kernel(MGArgs A) {
       done = true;
       break;
     }
-    vcycle<NT, CS>(A, m, cl, rank, off);
+    vcycle<NT, CS>(A, m, cl, rank, off, mg_smem);
     // Flexible (Polak-Ribiere) beta = z_new . (r_new - r_old) / (z_old . r_old), with
     // r_new - r_old = -alpha q: robust to the FP32 preconditioner's rounding.
     v[0] = 0.0;
@@ -326,6 +407,22 @@ __global__ void __launch_bounds__(NT) mgpcg_kernel(MGArgs A) {
 
 constexpr int MG_NT = 512;
 constexpr int MG_CS = 8;
+
+// Shared memory of CTA 0: b, x, t, r of every level from solo_level down (host side).
+size_t mg_solo_smem_bytes(const std::vector<InstMG>& h_mg) {
+  size_t best = 0;
+  for (const InstMG& m : h_mg) {
+    size_t cells = 0;
+    for (int l = solo_level(m); l < m.levels; ++l) cells += (size_t)m.nc[l];
+    best = std::max(best, 4 * cells * sizeof(float));
+  }
+  return best;
+}
+
+cudaError_t configure_mgpcg(Ctx* c, size_t smem) {
+  c->mg_smem_bytes = smem;
+  return cudaFuncSetAttribute(mgpcg_kernel<MG_NT, MG_CS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+}
 
 cudaError_t launch_mgpcg(const Ctx* c, const double* rhs, cudaStream_t s) {
   MGArgs a;
@@ -359,7 +456,7 @@ cudaError_t launch_mgpcg(const Ctx* c, const double* rhs, cudaStream_t s) {
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(c->n_inst * MG_CS, 1, 1);
   cfg.blockDim = dim3(MG_NT, 1, 1);
-  cfg.dynamicSmemBytes = 0;
+  cfg.dynamicSmemBytes = c->mg_smem_bytes;
   cfg.stream = s;
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeClusterDimension;

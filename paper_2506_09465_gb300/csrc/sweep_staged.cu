@@ -612,8 +612,35 @@ __global__ void __launch_bounds__(STAGED_NT, 1) sweep_staged_kernel(SweepArgs A,
 // S_k = V m T_emit (emitted thermal and source power), starting from the tallied low
 // boundary face.
 template <int DIM>
-__global__ void derive_last_axis_kernel(const InstDesc* inst, int n_inst, int nb, const double* T,
-                                        const double* srcshift, const double* Vm, const double* R, double* F) {
+__device__ __forceinline__ double column_step(const InstDesc& in, int nb, const double* T, const double* srcshift,
+                                              const double* Vm, const double* R, const double* Fi, long long c) {
+  const int n0 = in.n[0], n1 = in.n[1];
+  const long long g = in.cell_off + c;
+  double r = 0.0;
+  for (int b = 0; b < nb; ++b) r += R[in.bc_off + (long long)b * in.ncells + c];
+  double te = T[g];
+  if (srcshift) te += srcshift[g];
+  const long long row = c / n0;  // x-face index of the cell's low face = c + row
+  double inflow = Fi[in.fax_off[0] + c + row] - Fi[in.fax_off[0] + c + row + 1];
+  if (DIM == 3) {
+    const int cz = (int)(c / ((long long)n0 * n1));
+    const long long fy = in.fax_off[1] + c + (long long)n0 * cz;
+    inflow += Fi[fy] - Fi[fy + n0];
+  }
+  return inflow - (r - Vm[g] * te);
+}
+
+// Block: 32 adjacent columns x DERIVE_SEG segments (one warp per segment, so loads are
+// coalesced across columns). Each thread sums its segment's increments, the segments'
+// offsets follow from a prefix over the block's shared sums, then each thread writes its
+// segment's running values.
+constexpr int DERIVE_SEG = 8;
+
+template <int DIM>
+__global__ void __launch_bounds__(32 * DERIVE_SEG) derive_last_axis_kernel(const InstDesc* inst, int n_inst, int nb,
+                                                                         const double* T, const double* srcshift,
+                                                                         const double* Vm, const double* R, double* F) {
+  __shared__ double segsum[DERIVE_SEG][32];
   const int k = blockIdx.y;
   if (k >= n_inst) return;
   const InstDesc& in = inst[k];
@@ -621,33 +648,35 @@ __global__ void derive_last_axis_kernel(const InstDesc* inst, int n_inst, int nb
   const int nlast = DIM == 2 ? n1 : n2;
   const int ncol = in.ncells / nlast;
   double* Fi = F + in.face_off;
-  for (int col = blockIdx.x * blockDim.x + threadIdx.x; col < ncol; col += gridDim.x * blockDim.x) {
-    double acc;
-    int ix = col % n0, iy = DIM == 3 ? col / n0 : 0;
+  const int lane = threadIdx.x & 31, seg = threadIdx.x >> 5;
+  const int seglen = (nlast + DERIVE_SEG - 1) / DERIVE_SEG;
+  const int k0 = seg * seglen, k1 = min(nlast, k0 + seglen);
+  for (int cbase = blockIdx.x * 32; cbase < ncol; cbase += gridDim.x * 32) {
+    const int col = cbase + lane;
+    const bool ok = col < ncol;
+    const int ix = ok ? col % n0 : 0, iy = (ok && DIM == 3) ? col / n0 : 0;
     const long long stride = DIM == 2 ? n0 : (long long)n0 * n1;
     const long long base_cell = DIM == 2 ? ix : ix + (long long)n0 * iy;
-    // low boundary face of this column
-    const long long f0 = DIM == 2 ? in.fax_off[1] + ix : in.fax_off[2] + ix + (long long)n0 * iy;
-    acc = Fi[f0];
-    for (int kk = 0; kk < nlast; ++kk) {
-      const long long c = base_cell + kk * stride;
-      const long long g = in.cell_off + c;
-      double r = 0.0;
-      for (int b = 0; b < nb; ++b) r += R[in.bc_off + (long long)b * in.ncells + c];
-      double te = T[g];
-      if (srcshift) te += srcshift[g];
-      const long long row = c / n0;  // x-face index of the cell's low face = c + row
-      double inflow = Fi[in.fax_off[0] + c + row] - Fi[in.fax_off[0] + c + row + 1];
-      if (DIM == 3) {
-        const int cz = (int)(c / ((long long)n0 * n1));
-        const long long fy = in.fax_off[1] + c + (long long)n0 * cz;
-        inflow += Fi[fy] - Fi[fy + n0];
+    double part = 0.0;
+    if (ok)
+      for (int kk = k0; kk < k1; ++kk) part += column_step<DIM>(in, nb, T, srcshift, Vm, R, Fi, base_cell + kk * stride);
+    segsum[seg][lane] = part;
+    __syncthreads();
+    if (ok) {
+      // low boundary face of this column, then the segments below this one
+      const long long f0 = DIM == 2 ? in.fax_off[1] + ix : in.fax_off[2] + ix + (long long)n0 * iy;
+      double acc = Fi[f0];
+      for (int sg = 0; sg < seg; ++sg) acc += segsum[sg][lane];
+      for (int kk = k0; kk < k1; ++kk) {
+        const long long c = base_cell + kk * stride;
+        acc += column_step<DIM>(in, nb, T, srcshift, Vm, R, Fi, c);
+        const long long fn = DIM == 2 ? in.fax_off[1] + c + n0 : in.fax_off[2] + c + (long long)n0 * n1;
+        Fi[fn] = acc;
       }
-      acc = acc + inflow - (r - Vm[g] * te);
-      const long long fn = DIM == 2 ? in.fax_off[1] + c + n0 : in.fax_off[2] + c + (long long)n0 * n1;
-      Fi[fn] = acc;
     }
+    __syncthreads();
   }
+  (void)n2;
 }
 
 // Faces of wall w = 2a + side of an instance, enumerated as j1 + n(o1) j2 (o1 = (a+1)%3,
@@ -782,12 +811,16 @@ cudaError_t launch_sweep_staged(const Ctx* c, const SweepArgs& a, cudaStream_t s
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
   if (a.F && c->dim >= 2) {
-    dim3 grid((unsigned)((c->max_inst_cells + 255) / 256), (unsigned)c->n_inst);
-    if (grid.x > 64) grid.x = 64;
+    // one block per 32 columns of the largest instance (columns of the last axis)
+    long long maxcol = 0;
+    for (const InstDesc& in : c->h_inst) maxcol = std::max<long long>(maxcol, in.ncells / (c->dim == 2 ? in.n[1] : in.n[2]));
+    dim3 grid((unsigned)std::min<long long>((maxcol + 31) / 32, 4096), (unsigned)c->n_inst);
     if (c->dim == 2)
-      derive_last_axis_kernel<2><<<grid, 256, 0, s>>>(c->d_inst, c->n_inst, c->nb, a.T, a.srcshift, c->d_Vm, a.R, a.F);
+      derive_last_axis_kernel<2><<<grid, 32 * DERIVE_SEG, 0, s>>>(c->d_inst, c->n_inst, c->nb, a.T, a.srcshift,
+                                                                  c->d_Vm, a.R, a.F);
     else
-      derive_last_axis_kernel<3><<<grid, 256, 0, s>>>(c->d_inst, c->n_inst, c->nb, a.T, a.srcshift, c->d_Vm, a.R, a.F);
+      derive_last_axis_kernel<3><<<grid, 32 * DERIVE_SEG, 0, s>>>(c->d_inst, c->n_inst, c->nb, a.T, a.srcshift,
+                                                                  c->d_Vm, a.R, a.F);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }
