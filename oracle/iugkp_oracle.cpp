@@ -304,6 +304,35 @@ bool valid(const OrcProblem* p) {
   return true;
 }
 
+// Start state of a wall particle on the boundary face with lower corner f of wall (a, side)
+// (Sec. 4 black walls): position uniform along the in-domain tangential axes (taken in
+// axis order), direction cosine-weighted about the inward normal, mu_n = sqrt(u_n), the
+// tangential part sqrt(1 - u_n) (cos 2 pi u_phi, sin 2 pi u_phi) on the axes (a+1)%3, (a+2)%3.
+// Consumes emission_uniforms_wall(dim) uniforms.
+void wall_start(const Geo& g, int a, int side, const int f[3], Stream& st, double x[3], double s[3], int idx[3]) {
+  const int o1 = (a + 1) % 3, o2 = (a + 2) % 3;
+  x[0] = x[1] = x[2] = 0.0;
+  int tang[2] = {std::min(o1, o2), std::max(o1, o2)};
+  for (int k = 0; k < 2; ++k) {
+    int ax = tang[k];
+    if (ax < g.dim) x[ax] = (f[ax] + st.uniform()) * g.h[ax];
+  }
+  x[a] = f[a] * g.h[a];
+  double u_n = st.uniform();
+  double u_phi = g.dim >= 2 ? st.uniform() : 0.5;
+  double mu_n = std::sqrt(u_n);
+  double st_ = std::sqrt(1.0 - u_n);
+  double phi = 2.0 * M_PI * u_phi;
+  s[a] = side == 0 ? mu_n : -mu_n;
+  s[o1] = g.dim >= 2 ? st_ * std::cos(phi) : 0.0;
+  s[o2] = g.dim >= 2 ? st_ * std::sin(phi) : 0.0;
+  for (int ax = g.dim; ax < 3; ++ax) s[ax] = 0.0;
+  st.skip_to(emission_uniforms_wall(g.dim));
+  idx[0] = f[0]; idx[1] = f[1]; idx[2] = f[2];
+  if (side == 1) idx[a] = g.n[a] - 1;
+  for (int ax = g.dim; ax < 3; ++ax) idx[ax] = 0;
+}
+
 // Visit every particle of one sweep. For each: emitter kind (0 cell, 1 wall), band,
 // emitter id, particle index, unit-temperature weight coefficient, start state.
 template <typename F>
@@ -364,29 +393,9 @@ void for_each_particle(const OrcProblem& p, const Geo& g, uint32_t epoch, bool s
             uint32_t emitter = (uint32_t)(g.ncells + face);
             for (long long q = 0; q < nwp; ++q) {
               Stream st(p.seed, p.instance, (uint32_t)b, epoch, emitter, (uint32_t)q);
-              double x[3] = {0.0, 0.0, 0.0};
-              // Position on the face: uniform along the in-domain tangential axes,
-              // taken in axis order.
-              int tang[2] = {std::min(o1, o2), std::max(o1, o2)};
-              for (int k = 0; k < 2; ++k) {
-                int ax = tang[k];
-                if (ax < g.dim) x[ax] = (f[ax] + st.uniform()) * g.h[ax];
-              }
-              x[a] = f[a] * g.h[a];
-              double u_n = st.uniform();
-              double u_phi = g.dim >= 2 ? st.uniform() : 0.5;
-              double mu_n = std::sqrt(u_n);
-              double st_ = std::sqrt(1.0 - u_n);
-              double phi = 2.0 * M_PI * u_phi;
-              double s[3];
-              s[a] = side == 0 ? mu_n : -mu_n;
-              s[o1] = g.dim >= 2 ? st_ * std::cos(phi) : 0.0;
-              s[o2] = g.dim >= 2 ? st_ * std::sin(phi) : 0.0;
-              for (int ax = g.dim; ax < 3; ++ax) s[ax] = 0.0;
-              st.skip_to(emission_uniforms_wall(g.dim));
-              int idx[3] = {f[0], f[1], f[2]};
-              if (side == 1) idx[a] = g.n[a] - 1;
-              for (int ax = g.dim; ax < 3; ++ax) idx[ax] = 0;
+              double x[3], s[3];
+              int idx[3];
+              wall_start(g, a, side, f, st, x, s, idx);
               fn(1, b, wall, face, coef, w, st, x, idx, s);
             }
           }
@@ -744,6 +753,128 @@ int orc_band_split(int nb, long long N, const double* r, long long* out) {
   for (int b = 0; b < nb; ++b) order[b] = b;
   std::stable_sort(order.begin(), order.end(), [&](int a, int c) { return frac[a] > frac[c]; });
   for (long long k = 0; k < left; ++k) out[order[(size_t)(k % nb)]] += 1;
+  return 0;
+}
+
+// ---------------------------------------------------------------------------
+// Persistent null-collision population (Sec. 3.2 steps (1)-(6)). A fixed population of
+// particles (Sec. 4.1: the count stays fixed, so a plain array holds it) makes one candidate
+// flight per iteration. Each particle has a home: the cell of its last real collision or
+// the boundary face through which a wall last absorbed it. A particle whose last flight
+// ended at home is re-emitted from there (step (2)) with the home's equilibrium power shared
+// by the particles that ended there: w = S_{b,c} / N_rc(b, c) in a cell
+// (S = C_b T_emit V / tau_b, T_emit = T + Q/m from the current macro state), and
+// w = (C_b v_b T_face A / 4) / N_abs(b, face) on a face (a black wall absorbs what reaches
+// it and emits at its temperature). A null candidate keeps position, direction and weight
+// and flies again (step (6)).
+// Slots: N_b per (band, cell) in band-major, cell order, then N_w,b per (band, wall, face).
+// Draws of slot k in iteration it: Stream(seed, instance, band, it, 0x80000000, k):
+// emission uniforms if re-emitted, then the (path, accept) pair.
+// Per slot: x[3], s[3], w, home (cell index, or ncells + boundary-face index in wall
+// order), due (1: re-emit this iteration). n_home_prev / n_home_new: [nb * (ncells +
+// boundary faces)] particles that ended at each home in the previous / this iteration.
+// Outputs R, W, wall (overwritten), counters {flights, candidates, real, 0, wall exits, 0}.
+int orc_persistent_step(const OrcProblem* p, const double* T, uint32_t it, long long n_slots, double* x, double* s,
+                        double* w, const int* band, long long* home, int* due, const uint32_t* n_home_prev,
+                        uint32_t* n_home_new, double* R, double* W, double* wall, unsigned long long* counters) {
+  if (!valid(p)) return -1;
+  Geo g(*p);
+  std::vector<double> tmaj, m;
+  majorants(*p, g, tmaj);
+  cell_m(*p, g, m);
+  long long wall_face_off[7] = {0, 0, 0, 0, 0, 0, 0};
+  for (int wl = 0; wl < 2 * g.dim; ++wl) {
+    int a = wl / 2;
+    wall_face_off[wl + 1] = wall_face_off[wl] + (long long)g.n[(a + 1) % 3] * g.n[(a + 2) % 3];
+  }
+  const long long nbf = wall_face_off[2 * g.dim];
+  const long long nh = g.ncells + nbf;  // homes per band
+  const long long bc = (long long)p->nb * g.ncells;
+  std::fill(R, R + bc, 0.0);
+  std::fill(W, W + bc, 0.0);
+  std::fill(wall, wall + 2 * p->dim, 0.0);
+  std::fill(n_home_new, n_home_new + (long long)p->nb * nh, 0u);
+  for (int k = 0; k < 6; ++k) counters[k] = 0;
+  for (long long i = 0; i < n_slots; ++i) {
+    const int b = band[i];
+    Stream st(p->seed, p->instance, (uint32_t)b, it, 0x80000000u, (uint32_t)i);
+    double* xi = &x[3 * i];
+    double* si = &s[3 * i];
+    if (due[i]) {
+      const long long h = home[i];
+      const double nprev = (double)n_home_prev[(long long)b * nh + h];
+      if (h < g.ncells) {  // step (2): re-emission in the cell of the real collision
+        const int ci[3] = {(int)(h % g.n[0]), (int)((h / g.n[0]) % g.n[1]), (int)(h / ((long long)g.n[0] * g.n[1]))};
+        for (int a = 0; a < g.dim; ++a) xi[a] = (ci[a] + st.uniform()) * g.h[a];
+        for (int a = g.dim; a < 3; ++a) xi[a] = 0.0;
+        const double u_mu = st.uniform();
+        const double u_phi = g.dim >= 2 ? st.uniform() : 0.5;
+        thermal_direction(g.dim, u_mu, u_phi, si);
+        st.skip_to(emission_uniforms_thermal(g.dim));
+        const double te = T[h] + (p->source ? p->source[h] / m[h] : 0.0);
+        w[i] = p->C[b] * te * g.V / p->tau[(long long)b * g.ncells + h] / nprev;
+      } else {  // re-emission from the boundary face that absorbed it
+        const long long bf = h - g.ncells;
+        int wl = 0;
+        while (bf >= wall_face_off[wl + 1]) ++wl;
+        const int a = wl / 2, side = wl % 2, o1 = (a + 1) % 3, o2 = (a + 2) % 3;
+        const long long j = bf - wall_face_off[wl];
+        int f[3];
+        f[a] = side == 0 ? 0 : g.n[a];
+        f[o1] = (int)(j % g.n[o1]);
+        f[o2] = (int)(j / g.n[o1]);
+        int idx[3];
+        wall_start(g, a, side, f, st, xi, si, idx);
+        const double Tf = p->wall_face_T ? p->wall_face_T[bf] : p->wall_T[wl];
+        w[i] = p->C[b] * p->v[b] * g.A[a] * Tf / 4.0 / nprev;
+      }
+    }
+    // step (3): one flight, path length -ln(u) v tau_maj
+    counters[0] += 1;
+    const double u_path = st.uniform();
+    const double u_acc = st.uniform();
+    const double ell = -std::log(u_path) * p->v[b] * tmaj[b];
+    double tw = INFINITY;
+    int wl = -1;
+    for (int a = 0; a < g.dim; ++a) {
+      if (si[a] == 0.0) continue;
+      const double t = si[a] > 0.0 ? (g.L[a] - xi[a]) / si[a] : -xi[a] / si[a];
+      if (t < tw) {
+        tw = t;
+        wl = 2 * a + (si[a] > 0.0 ? 1 : 0);
+      }
+    }
+    if (wl >= 0 && tw < ell) {  // absorbed by the wall it reaches first
+      wall[wl] += w[i];
+      counters[4] += 1;
+      const int a = wl / 2, o1 = (a + 1) % 3, o2 = (a + 2) % 3;
+      int j1 = 0, j2 = 0;
+      if (o1 < g.dim) j1 = std::min(std::max((int)std::floor((xi[o1] + tw * si[o1]) / g.h[o1]), 0), g.n[o1] - 1);
+      if (o2 < g.dim) j2 = std::min(std::max((int)std::floor((xi[o2] + tw * si[o2]) / g.h[o2]), 0), g.n[o2] - 1);
+      home[i] = g.ncells + wall_face_off[wl] + (long long)j2 * g.n[o1] + j1;
+      due[i] = 1;
+      n_home_new[(long long)b * nh + home[i]] += 1;
+      continue;
+    }
+    for (int a = 0; a < g.dim; ++a) xi[a] += ell * si[a];
+    int ci[3] = {0, 0, 0};
+    for (int a = 0; a < g.dim; ++a) ci[a] = std::min(std::max((int)std::floor(xi[a] / g.h[a]), 0), g.n[a] - 1);
+    const long long c = g.cell(ci);
+    // steps (4)-(5): candidate at the destination; W from every candidate, W^h and N_rc
+    // from real ones
+    counters[1] += 1;
+    const long long jb = (long long)b * g.ncells + c;
+    W[jb] += w[i] * tmaj[b];
+    if (u_acc < tmaj[b] / p->tau[jb]) {
+      counters[2] += 1;
+      R[jb] += w[i];
+      home[i] = c;
+      due[i] = 1;
+      n_home_new[(long long)b * nh + c] += 1;
+    } else {
+      due[i] = 0;  // step (6): same direction and weight, a new path next iteration
+    }
+  }
   return 0;
 }
 

@@ -76,6 +76,8 @@ def lib():
         _lib.orc_emit.argtypes = [P, i32, i32, i64, u32, vp, vp, vp]
         _lib.orc_newton_theta.argtypes = [P]
         _lib.orc_newton_theta.restype = d
+        _lib.orc_persistent_step.argtypes = [P, vp, u32, i64, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp]
+        _lib.orc_persistent_step.restype = i32
     return _lib
 
 
@@ -298,6 +300,55 @@ def average(p: Problem, T0: np.ndarray, n_steps: int, epoch_first: int, newton_o
     Ts = np.array(Ts)
     var = Ts.var(axis=0, ddof=1) if n_steps > 1 else np.zeros(p.ncells)
     return T, Ts.mean(axis=0), var, np.array(Fs).mean(axis=0)
+
+
+class Population:
+    """Fixed particle population of the persistent null-collision scheme (Sec. 3.2 steps
+    (1)-(6)): per slot position, direction, weight, band, home (cell, or ncells + boundary
+    face in wall order) and whether it is re-emitted this iteration; with the number of
+    particles that ended at each home in the last iteration."""
+
+    def __init__(self, p: Problem):
+        nc, nb = p.ncells, p.nb
+        nbf = sum(p.wall_faces())
+        slots_b, homes = [], []
+        for b in range(nb):
+            slots_b.append(np.full(int(p.n_band[b]) * nc, b))
+            homes.append(np.repeat(np.arange(nc), int(p.n_band[b])))
+        for b in range(nb):
+            slots_b.append(np.full(int(p.n_wall_band[b]) * nbf, b))
+            homes.append(nc + np.repeat(np.arange(nbf), int(p.n_wall_band[b])))
+        self.band = np.ascontiguousarray(np.concatenate(slots_b), dtype=np.int32)
+        self.home = np.ascontiguousarray(np.concatenate(homes), dtype=np.int64)
+        self.n = len(self.band)
+        self.x = np.zeros(3 * self.n)
+        self.s = np.zeros(3 * self.n)
+        self.w = np.zeros(self.n)
+        self.due = np.ones(self.n, dtype=np.int32)
+        # step (1): every home starts with its own N particles
+        counts = np.zeros((nb, nc + nbf), dtype=np.uint32)
+        for b in range(nb):
+            counts[b, :nc] = p.n_band[b]
+            counts[b, nc:] = p.n_wall_band[b]
+        self.n_home = counts.reshape(-1)
+
+
+def persistent_step(p: Problem, T: np.ndarray, it: int, pop: Population):
+    """One iteration of the persistent scheme: returns (R, W, wall, counters); pop is
+    updated in place."""
+    T = np.ascontiguousarray(T, dtype=np.float64)
+    R = np.zeros((p.nb, p.ncells))
+    W = np.zeros((p.nb, p.ncells))
+    wall = np.zeros(2 * p.dim)
+    cnt = np.zeros(6, dtype=np.uint64)
+    n_new = np.zeros_like(pop.n_home)
+    rc = lib().orc_persistent_step(ctypes.byref(p.c_struct()), _ptr(T), it, pop.n, _ptr(pop.x), _ptr(pop.s),
+                                   _ptr(pop.w), _ptr(pop.band), _ptr(pop.home), _ptr(pop.due), _ptr(pop.n_home),
+                                   _ptr(n_new), _ptr(R), _ptr(W), _ptr(wall), _ptr(cnt))
+    if rc != 0:
+        raise ValueError("orc_persistent_step failed")
+    pop.n_home = n_new
+    return R, W, wall, cnt
 
 
 def adjoint_apply(p: Problem, lam: np.ndarray, epoch: int = 0):

@@ -1,0 +1,89 @@
+"""The persistent null-collision population of Sec. 3.2 (steps (1)-(6)), in the oracle:
+its first iteration is a sweep of the closed-form E_3 expectation, every iteration balances
+power exactly, and its stationary state is the expected steady state of the stateless
+sweep (the chain of candidates that the paper spreads over iterations is the same
+thinning law), for constant tau and across a tau jump with 99 % null candidates."""
+import os
+
+import numpy as np
+import pytest
+
+from oracle import expected as X
+
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+
+
+def slab(orc, n, tau, N, seed, wall_T=(1.0, -1.0)):
+    return orc.Problem(1, (n,), (1.0,), np.array([1.0]), np.array([1.0]), tau, np.array(wall_T), np.array([N]),
+                       np.array([N]), seed=seed)
+
+
+def golden(name, col):
+    rows = np.array([[float(v) for v in l.split()] for l in open(os.path.join(GOLDEN, name)) if l[0] != "#"])
+    return rows[:, col]
+
+
+def test_first_iteration_is_a_sweep_in_expectation(orc):
+    # Constant tau (every candidate real): from the initial population every particle is
+    # emitted from its home and makes one flight, which is one sweep of Sec. 3.1.
+    n = 12
+    T = np.linspace(0.8, -0.3, n)
+    Rs = []
+    for seed in range(40):
+        p = slab(orc, n, np.ones((1, n)), 200, seed)
+        pop = orc.Population(p)
+        R, W, wall, cnt = orc.persistent_step(p, T, 0, pop)
+        Rs.append(np.concatenate([R.ravel(), wall]))
+    Rs = np.array(Rs)
+    Re, _, _, walle = X.slab_expected_sweep(1.0, [1.0], [1.0], np.ones((1, n)), T, [1.0, -1.0])
+    z = (Rs.mean(0) - np.concatenate([Re.ravel(), walle])) / (Rs.std(0, ddof=1) / np.sqrt(40))
+    assert np.abs(z).max() < 4.5
+
+
+def test_every_iteration_balances_power(orc):
+    # Power carried by null particles in flight + power (re-)emitted this iteration = power
+    # absorbed in cells (R) + absorbed by walls + power still in flight, exactly.
+    n = 20
+    x = (np.arange(n) + 0.5) / n
+    tau = np.where(x < 0.5, 2.0, 0.2).reshape(1, n)
+    p = slab(orc, n, tau, 50, 3, wall_T=(1.0, 0.3))
+    pop = orc.Population(p)
+    T = np.linspace(0.9, 0.2, n)
+    nc, V = n, 1.0 / n
+    for it in range(6):
+        carried = pop.w[pop.due == 0].sum()
+        counts = pop.n_home.reshape(1, -1)
+        emitted = sum(T[c] * V / tau[0, c] for c in range(nc) if counts[0, c] > 0)
+        emitted += sum(t / 4.0 for k, t in enumerate((1.0, 0.3)) if counts[0, nc + k] > 0)
+        R, W, wall, cnt = orc.persistent_step(p, T, it, pop)
+        after = pop.w[pop.due == 0].sum()
+        assert abs((carried + emitted) - (R.sum() + wall.sum() + after)) <= 1e-12 * (carried + emitted)
+        assert cnt[0] == pop.n and cnt[2] + cnt[4] == (pop.due == 1).sum()
+
+
+@pytest.mark.parametrize("case", ["kn1", "caseA"])
+def test_stationary_state_is_the_expected_steady_state(orc, case):
+    # Fresh draws every iteration (iteration k draws with epoch k), the Newton-corrected
+    # update of the solve; the energy temperature T^E = W / (V C) averaged over 200
+    # iterations after 100 agrees with the expected steady state (standard error from 20
+    # batch means).
+    if case == "kn1":
+        n, tau, Tg = 50, np.ones((1, 50)), golden("slab_kn1_50cells.txt", 1)
+    else:
+        n = 100
+        x = (np.arange(n) + 0.5) / n
+        tau = np.where(x < 0.5, 10.0, 0.1).reshape(1, n)
+        Tg = golden("slab_jump_caseA_100cells.txt", 2)
+    p = slab(orc, n, tau, 400, 5)
+    pop = orc.Population(p)
+    T = np.zeros(n)
+    TE_hist = []
+    for it in range(300):
+        R, W, wall, cnt = orc.persistent_step(p, T, it, pop)
+        Th, TE = orc.macro(p, R, W)
+        T = orc.newton(p, T, Th, R)[0]
+        if it >= 100:
+            TE_hist.append(TE)
+    bm = np.array(TE_hist).reshape(20, 10, n).mean(1)
+    z = (bm.mean(0) - Tg) / (bm.std(0, ddof=1) / np.sqrt(20))
+    assert np.abs(z).max() < 4.5, np.abs(z).max()
