@@ -205,6 +205,29 @@ iugkp_status iugkp_newton_step(iugkp_ctx *ctx, const double *T_n_dev, double *T_
 iugkp_status iugkp_average(iugkp_ctx *ctx, double *T_inout_dev, int n_steps, unsigned epoch_first,
                            double *T_mean_dev, double *T_var_dev, double *F_mean_dev, void *cuda_stream);
 
+/* Persistent null-collision population (Sec. 3.2 steps (1)-(6)): the paper's own form of the
+ * variable-tau iteration, next to the stateless sweep of iugkp_sweep. A fixed population
+ * (N_b slots per (band, cell) and N_w,b per (band, boundary face)) makes one candidate
+ * flight per iteration. A particle whose flight ended in a real collision (or at a wall) is
+ * re-emitted next iteration from that cell (or boundary face) with the home's power shared
+ * by the particles that ended there: w = (C_b T_emit V / tau_b) / N in a cell, T_emit = T +
+ * Q/m, and (C_b v_b T_face A / 4) / N on a face; a null candidate keeps position, direction
+ * and weight. FP64 throughout; state in structure-of-arrays form (7 doubles and 3 ints per
+ * slot, allocated by the reset). Draws of slot k (within its instance) in iteration it:
+ * Philox counter (block, k, 0x80000000, band << 24 | it), key (seed, seed_hi ^ instance id).
+ * iugkp_persistent_reset: (re)builds the population, every slot due for emission from its
+ * home and every home counted with its own slots; synchronises cuda_stream.
+ * iugkp_persistent_step: one iteration with the macro temperature T_dev (device FP64
+ * [total_cells]); writes R_dev (real collisions, required), W_dev (w tau_maj of every
+ * candidate), wall_dev (absorbed per wall) and counters_dev {flights, candidates, real, 0,
+ * wall exits, 0} (each may be NULL) in the layouts of iugkp_sweep, and *slots_out (may be
+ * NULL); enqueued on cuda_stream without synchronising. The macro update and the Newton
+ * step are the caller's (iugkp_macro, iugkp_newton_step). EINVAL before a reset. */
+iugkp_status iugkp_persistent_reset(iugkp_ctx *ctx, void *cuda_stream);
+iugkp_status iugkp_persistent_step(iugkp_ctx *ctx, const double *T_dev, unsigned iteration, double *R_dev,
+                                   double *W_dev, double *wall_dev, unsigned long long *counters_dev,
+                                   long long *slots_out, void *cuda_stream);
+
 /* Tuning of the staged sweep (no counterpart in the paper; refill, claim size and walk
  * length change speed, not results; the tally mode changes results by rounding only).
  * iugkp_autotune times full sweeps from T_dev (device FP64 [total_cells]) on the caller's

@@ -68,6 +68,8 @@ SIGNATURES = {
     "iugkp_residual": (_i, [_vp, _vp, _vp, _vp, _vp]),
     "iugkp_autotune": (_i, [_vp, _vp, _u, _i, ctypes.POINTER(Tuning), _vp]),
     "iugkp_average": (_i, [_vp, _vp, _i, _u, _vp, _vp, _vp, _vp]),
+    "iugkp_persistent_reset": (_i, [_vp, _vp]),
+    "iugkp_persistent_step": (_i, [_vp, _vp, _u, _vp, _vp, _vp, _vp, ctypes.POINTER(ctypes.c_longlong), _vp]),
     "iugkp_solve_steady": (_i, [_vp, _vp, _d, _i, ctypes.POINTER(_i), ctypes.POINTER(_d), _vp]),
     "iugkp_adjoint": (_i, [_vp, _vp, _vp, _d, _i, _vp, _vp, _vp, _vp]),
     "iugkp_diffusion_solve_noalloc": (_i, [ctypes.POINTER(Grid), _vp, _d, _vp, _vp, _d, _i, ctypes.POINTER(_i), _vp]),

@@ -108,7 +108,9 @@ void free_all(Ctx* c) {
                   c->d_mg_cy, c->d_mg_cz, c->d_mg_cinv, c->d_mg_b, c->d_mg_x, c->d_mg_t, c->d_mg_r,
                   c->d_inst_beg, c->d_inst_end, c->d_inst_next, c->d_cost_prefix, c->d_window, c->d_wmax,
                   c->d_group_mag, c->d_mag, c->d_wall_unit, c->d_all_beg, c->d_all_end, c->d_all_cost_prefix,
-                  c->d_all_group_mag, c->d_R32, c->d_W32, c->d_F32, c->d_m2, c->d_wallTf};
+                  c->d_all_group_mag, c->d_R32, c->d_W32, c->d_F32, c->d_m2, c->d_wallTf,
+                  c->d_pslot_off, c->d_phome_off, c->d_pnband, c->d_pnwall, c->d_px, c->d_pband, c->d_phome,
+                  c->d_pdue, c->d_pcount};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (c->h_pinned) cudaFreeHost(c->h_pinned);
@@ -1108,6 +1110,72 @@ iugkp_status iugkp_solve_steady(iugkp_ctx* ctx, double* T_inout_dev, double tol,
   if (iters_out) *iters_out = it;
   if (res_out) *res_out = res;
   if (!(res <= tol)) return fail(c, IUGKP_ENOCONV, "max_iter reached before tol");
+  return IUGKP_OK;
+}
+
+iugkp_status iugkp_persistent_reset(iugkp_ctx* ctx, void* cuda_stream) {
+  if (!ctx) return IUGKP_EINVAL;
+  Ctx* c = &ctx->c;
+  cudaStream_t s = (cudaStream_t)cuda_stream;
+  std::vector<long long> slot_off(c->n_inst + 1, 0), home_off(c->n_inst + 1, 0);
+  for (int k = 0; k < c->n_inst; ++k) {
+    const InstDesc& in = c->h_inst[k];
+    long long nbf = 0;
+    for (int w = 0; w < 2 * in.dim; ++w) nbf += (long long)in.n[((w >> 1) + 1) % 3] * in.n[((w >> 1) + 2) % 3];
+    long long slots = 0;
+    for (int b = 0; b < c->nb; ++b) slots += c->h_nband[(size_t)k * c->nb + b] * in.ncells + c->h_nwall[b] * nbf;
+    slot_off[k + 1] = slot_off[k] + slots;
+    home_off[k + 1] = home_off[k] + (long long)c->nb * (in.ncells + nbf);
+  }
+  if (slot_off[c->n_inst] >= (1ll << 31)) return fail(c, IUGKP_EINVAL, "persistent population above 2^31 slots");
+  if (c->pers_n != slot_off[c->n_inst] || !c->d_px) {
+    void* olds[] = {c->d_pslot_off, c->d_phome_off, c->d_pnband, c->d_pnwall, c->d_px, c->d_pband, c->d_phome,
+                    c->d_pdue, c->d_pcount};
+    for (void* p : olds)
+      if (p) cudaFree(p);
+    c->d_pslot_off = c->d_phome_off = c->d_pnband = c->d_pnwall = nullptr;
+    c->d_px = nullptr;
+    c->d_pband = c->d_phome = c->d_pdue = nullptr;
+    c->d_pcount = nullptr;
+    c->pers_n = slot_off[c->n_inst];
+    c->pers_homes = home_off[c->n_inst];
+    iugkp_status st;
+    if ((st = upload(c, &c->d_pslot_off, slot_off)) != IUGKP_OK) return st;
+    if ((st = upload(c, &c->d_phome_off, home_off)) != IUGKP_OK) return st;
+    if ((st = upload(c, &c->d_pnband, c->h_nband)) != IUGKP_OK) return st;
+    if ((st = upload(c, &c->d_pnwall, c->h_nwall)) != IUGKP_OK) return st;
+    if ((st = dalloc(c, &c->d_px, (size_t)7 * c->pers_n)) != IUGKP_OK) return st;
+    if ((st = dalloc(c, &c->d_pband, (size_t)c->pers_n)) != IUGKP_OK) return st;
+    if ((st = dalloc(c, &c->d_phome, (size_t)c->pers_n)) != IUGKP_OK) return st;
+    if ((st = dalloc(c, &c->d_pdue, (size_t)c->pers_n)) != IUGKP_OK) return st;
+    if ((st = dalloc(c, &c->d_pcount, (size_t)2 * c->pers_homes)) != IUGKP_OK) return st;
+  }
+  c->pers_parity = 0;
+  CK(launch_persistent_init(c, s), "persistent init");
+  return check_device(c, s);
+}
+
+iugkp_status iugkp_persistent_step(iugkp_ctx* ctx, const double* T_dev, unsigned iteration, double* R_dev,
+                                   double* W_dev, double* wall_dev, unsigned long long* counters_dev,
+                                   long long* slots_out, void* cuda_stream) {
+  if (!ctx) return IUGKP_EINVAL;
+  Ctx* c = &ctx->c;
+  if (!T_dev || !R_dev) return fail(c, IUGKP_EINVAL, "T_dev and R_dev are required");
+  if (!c->d_px) return fail(c, IUGKP_EINVAL, "call iugkp_persistent_reset first");
+  cudaStream_t s = (cudaStream_t)cuda_stream;
+  const size_t bc = (size_t)c->nb * c->total_cells;
+  double* W = W_dev ? W_dev : c->d_W;
+  double* wall = wall_dev ? wall_dev : c->d_wall;
+  unsigned long long* cnt = counters_dev ? counters_dev : c->d_counters;
+  CK(cudaMemsetAsync(R_dev, 0, bc * sizeof(double), s), "clear R");
+  CK(cudaMemsetAsync(W, 0, bc * sizeof(double), s), "clear W");
+  CK(cudaMemsetAsync(wall, 0, (size_t)c->total_walls * sizeof(double), s), "clear wall");
+  CK(cudaMemsetAsync(cnt, 0, CNT_N * sizeof(unsigned long long), s), "clear counters");
+  CK(cudaMemsetAsync(c->d_pcount + (c->pers_parity ? 0 : c->pers_homes), 0, (size_t)c->pers_homes * sizeof(unsigned), s),
+     "clear counts");
+  CK(launch_persistent_step(c, T_dev, iteration, R_dev, W, wall, cnt, s), "persistent step");
+  c->pers_parity ^= 1;
+  if (slots_out) *slots_out = c->pers_n;
   return IUGKP_OK;
 }
 

@@ -112,6 +112,19 @@ struct Ctx {
   double* d_scalar = nullptr;    // [8] small results
   double* d_adj = nullptr;       // [4 * cells] adjoint iteration buffers (allocated on first use)
   double* d_m2 = nullptr;        // [cells] averaging: sum of squared deviations (allocated on first use)
+  // persistent null-collision population (persistent.cu), allocated by iugkp_persistent_reset
+  long long pers_n = 0;          // slots of all instances
+  long long pers_homes = 0;      // per-(band, home) counters of all instances
+  int pers_parity = 0;           // which half of d_pcount holds the previous iteration
+  long long* d_pslot_off = nullptr;
+  long long* d_phome_off = nullptr;
+  long long* d_pnband = nullptr;  // [n_inst * nb]
+  long long* d_pnwall = nullptr;  // [nb]
+  double* d_px = nullptr;         // [7 * pers_n]: x, y, z, s_x, s_y, s_z, w
+  int* d_pband = nullptr;
+  int* d_phome = nullptr;
+  int* d_pdue = nullptr;
+  unsigned* d_pcount = nullptr;   // [2 * pers_homes]
   double* h_pinned = nullptr;    // [8 + n_inst] host readback
   // multigrid preconditioner of the Newton correction (mg_setup.cu, mgpcg.cu)
   struct InstMG* d_mg = nullptr;
@@ -180,6 +193,9 @@ cudaError_t configure_mgpcg(Ctx* c, size_t smem);
 iugkp_status build_multigrid(Ctx* c, const std::vector<double>& diag, const std::vector<double>& cx,
                              const std::vector<double>& cy, const std::vector<double>& cz);
 cudaError_t launch_grad_source(const Ctx* c, const double* at, double* grad, cudaStream_t s);
+cudaError_t launch_persistent_init(Ctx* c, cudaStream_t s);
+cudaError_t launch_persistent_step(const Ctx* c, const double* T, unsigned it, double* R, double* W, double* wall,
+                                   unsigned long long* counters, cudaStream_t s);
 cudaError_t launch_welford(const Ctx* c, const double* x, double* mean, double* m2, long long n, int k,
                            cudaStream_t s);
 cudaError_t launch_scale(const Ctx* c, double* x, long long n, double a, cudaStream_t s);

@@ -173,6 +173,22 @@ class Solver:
                                        _dptr(Fm), _stream_ptr(stream)), self.ctx)
         return mean, var, Fm
 
+    def persistent_reset(self, stream=None):
+        """(Re)builds the persistent null-collision population (iugkp_persistent_reset)."""
+        L.check(self.lib.iugkp_persistent_reset(self.ctx, _stream_ptr(stream)), self.ctx)
+
+    def persistent_step(self, T, iteration, stream=None):
+        """One iteration of the persistent population (iugkp_persistent_step): returns
+        dict(R, W, wall, counters, slots)."""
+        R = self.zeros(self.nb * self.total_cells)
+        W = self.zeros(self.nb * self.total_cells)
+        wall = self.zeros(self.total_walls)
+        cnt = torch.zeros(6, dtype=torch.int64, device=self.device)
+        n = ctypes.c_longlong(0)
+        L.check(self.lib.iugkp_persistent_step(self.ctx, _dptr(T), int(iteration), _dptr(R), _dptr(W), _dptr(wall),
+                                               _dptr(cnt), ctypes.byref(n), _stream_ptr(stream)), self.ctx)
+        return {"R": R, "W": W, "wall": wall, "counters": cnt, "slots": n.value}
+
     def autotune(self, T, epoch=0, allow_k32=False, stream=None):
         """Times the staged sweep over its tunables and keeps the fastest (see iugkp_autotune)."""
         t = L.Tuning()

@@ -77,6 +77,8 @@ def test_null_arguments_rejected(lib):
     assert L.iugkp_adjoint(None, None, None, 1e-8, 10, None, None, None, None) == 1
     assert L.iugkp_autotune(None, None, 0, 0, None, None) == 1
     assert L.iugkp_average(None, None, 1, 0, None, None, None, None) == 1
+    assert L.iugkp_persistent_reset(None, None) == 1
+    assert L.iugkp_persistent_step(None, None, 0, None, None, None, None, None, None) == 1
     L.iugkp_destroy(None)  # no-op
 
 
