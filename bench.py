@@ -39,6 +39,7 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint-gradient timing")
     ap.add_argument("--no-tune", action="store_true", help="use the default staged-sweep parameters")
+    ap.add_argument("--no-persistent", action="store_true", help="skip the persistent-population timing")
     ap.add_argument("--profile", default=None, choices=["sweep", "step"],
                     help="run --warmup then --steps sweeps (or full steps) of the workload and exit; for ncu")
     ap.add_argument("--kn", type=float, default=None, help="profile one Knudsen number only")
@@ -279,6 +280,41 @@ def adjoint_gradient_time(WL, make_solver, tuned, with_plain):
     return out
 
 
+def persistent_scheme_time(wl, make_solver, steps=10, warmup=3):
+    """The paper-literal persistent null-collision population (Sec. 3.2 steps (1)-(6)) on the
+    same batch: FP64 state of every slot read and written once per iteration. Time per
+    iteration of the population kernel (CUDA events), flights/s, and the algorithmic state
+    traffic against the measured HBM bandwidth (2D: 5 doubles + 3 ints read, 5 doubles + 2
+    ints written per slot)."""
+    import torch
+    s = make_solver(wl, seed=0, precision=0, tally=0, schedule=0)
+    s.persistent_reset()
+    T = torch.full((s.total_cells,), 0.3, dtype=torch.float64, device="cuda")
+    for it in range(warmup):
+        g = s.persistent_step(T, it)
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record()
+    for it in range(warmup, warmup + steps):
+        g = s.persistent_step(T, it)
+    ev1.record()
+    torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1) / steps
+    slots = g["slots"]
+    flights = int(g["counters"][0].item())
+    bytes_per_step = slots * (5 * 8 + 3 * 4 + 5 * 8 + 2 * 4)
+    peak = 6783.5
+    try:
+        peak = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["hbm_gbs"]
+    except Exception:
+        pass
+    gbs = bytes_per_step / (ms * 1e-3) / 1e9
+    del s
+    return {"slots": slots, "ms_per_iteration": ms, "flights_per_s": flights / (ms * 1e-3),
+            "state_bytes_per_iteration": bytes_per_step, "achieved_gbs": gbs, "hbm_peak_gbs": peak,
+            "hbm_frac": gbs / peak, "precision": "fp64"}
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -434,6 +470,9 @@ def run_ours(args):
                 del sp1
             plain = {"sweep_crossings_per_s": ptot_cross / (ptot_ms / 1e3),
                      "steady_s_sequential": psteady if not args.no_steady else None, "steady_iters": piters}
+        persistent = None
+        if not args.no_persistent:
+            persistent = persistent_scheme_time(wl, make_solver)
         adjoint = None
         if not args.no_adjoint:
             adjoint = adjoint_gradient_time(WL, make_solver, tuned, not args.no_plain)
@@ -465,6 +504,7 @@ def run_ours(args):
             "sweep_ms": statistics.median(sweep_ms),
             "time_to_steady": steady,
             "adjoint_gradient": adjoint,
+            "persistent_scheme": persistent,
             "plain_fp64": plain,
             "speedup_vs_plain_fp64_sweep": (sweep_counts[3] / sw_s) / plain["sweep_crossings_per_s"] if plain else None,
             "e2e": {"value": e2e_value, "unit": "cell-crossings/s", "h2d_bytes_per_step": nc * 8,
