@@ -40,7 +40,8 @@ def parse():
     ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint-gradient timing")
     ap.add_argument("--no-tune", action="store_true", help="use the default staged-sweep parameters")
     ap.add_argument("--no-persistent", action="store_true", help="skip the persistent-population timing")
-    ap.add_argument("--profile", default=None, choices=["sweep", "step"],
+    ap.add_argument("--no-configs", action="store_true", help="skip the non-gray square and 3D box sweeps")
+    ap.add_argument("--profile", default=None, choices=["sweep", "step", "persistent"],
                     help="run --warmup then --steps sweeps (or full steps) of the workload and exit; for ncu")
     ap.add_argument("--kn", type=float, default=None, help="profile one Knudsen number only")
     ap.add_argument("--mode", default="fast", choices=["fast", "plain64", "plain32"], help="profiled path")
@@ -58,6 +59,22 @@ def run_profile(args):
     from paper_2506_09465_gb300 import workloads as WL
     torch.cuda.set_device(0)
     kns = KNS if args.kn is None else (args.kn,)
+    if args.profile == "persistent":
+        # one cavity instance (Kn from --kn, default 1): population steps only
+        wl = WL.cavity_sweep(NGRID, (args.kn if args.kn is not None else 1.0,), NPART)
+        s = make_solver(wl, seed=0, precision=0, tally=0, schedule=0)
+        s.persistent_reset()
+        T = torch.full((s.total_cells,), 0.3, dtype=torch.float64, device="cuda")
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        for k in range(args.warmup + args.steps):
+            if k == args.warmup:
+                ev0.record()
+            g = s.persistent_step(T, k)
+        ev1.record()
+        torch.cuda.synchronize()
+        print("profile run done", g["counters"].cpu().tolist(), "slots", g["slots"], "ms/iteration",
+              ev0.elapsed_time(ev1) / max(1, args.steps))
+        return
     wl = WL.cavity_sweep(NGRID, kns, NPART)
     opt = {"fast": {"refill_lanes": args.refill}, "plain64": {"precision": 0, "tally": 0, "schedule": 0},
            "plain32": {"precision": 1, "tally": 0, "schedule": 0}}[args.mode]
@@ -280,14 +297,54 @@ def adjoint_gradient_time(WL, make_solver, tuned, with_plain):
     return out
 
 
+def other_config_sweeps(WL, make_solver, reps=3):
+    """Sweep throughput of the two other sweep workloads on the fast path: the 2D non-gray
+    square (256^2, 40 bands x 2 branches, Gaussian source, 1024 particles per cell) and the
+    batch of 16 two-material 3D boxes (16^3 .. 64^3, 256 particles per cell), T = 0.3 in every
+    cell plus the sources; best of reps after one warm-up, CUDA events around the sweep call."""
+    import torch
+    out = {}
+    for name, wl in (("nongray_256x256_80bands", WL.nongray_square(256, 40, 1024)), ("box_batch_16", WL.box_batch(16))):
+        s = make_solver(wl, seed=0)
+        T = torch.full((s.total_cells,), 0.3, dtype=torch.float64, device="cuda")  # every emitter active
+        R = torch.empty(s.nb * s.total_cells, dtype=torch.float64, device="cuda")
+        W = torch.empty_like(R)
+        F = torch.empty(s.total_faces, dtype=torch.float64, device="cuda")
+        wall = torch.empty(s.total_walls, dtype=torch.float64, device="cuda")
+        cnt = torch.zeros(6, dtype=torch.int64, device="cuda")
+        best = None
+        for rep in range(reps + 1):
+            ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            ev0.record()
+            s.sweep_into(T, 0, R, W, F, wall, cnt)
+            ev1.record()
+            torch.cuda.synchronize()
+            if rep > 0:
+                best = ev0.elapsed_time(ev1) if best is None else min(best, ev0.elapsed_time(ev1))
+        c = cnt.cpu().numpy()
+        out[name] = {"cells": s.total_cells, "band_branches": s.nb, "flights": int(c[0]), "crossings": int(c[3]),
+                     "candidates": int(c[1]), "sweep_ms": best, "crossings_per_s": c[3] / (best * 1e-3),
+                     "flights_per_s": c[0] / (best * 1e-3)}
+        del s
+    return out
+
+
 def persistent_scheme_time(wl, make_solver, steps=10, warmup=3):
     """The paper-literal persistent null-collision population (Sec. 3.2 steps (1)-(6)) on the
-    same batch: FP64 state of every slot read and written once per iteration. Time per
-    iteration of the population kernel (CUDA events), flights/s, and the algorithmic state
-    traffic against the measured HBM bandwidth (2D: 5 doubles + 3 ints read, 5 doubles + 2
-    ints written per slot)."""
+    same batch, with FP32 and with FP64 tracking: the state of every slot is read and written
+    once per iteration. Time per iteration (CUDA events), flights/s, and the algorithmic
+    state traffic against the measured HBM bandwidth (2D: position and direction (4 words),
+    weight and 3 ints read; the same words and 2 ints written per slot)."""
     import torch
-    s = make_solver(wl, seed=0, precision=0, tally=0, schedule=0)
+    out = {}
+    for prec in ("fp32", "fp64"):
+        out[prec] = _persistent_time(wl, make_solver, prec, steps, warmup)
+    return out
+
+
+def _persistent_time(wl, make_solver, prec, steps, warmup):
+    import torch
+    s = make_solver(wl, seed=0, precision=1 if prec == "fp32" else 0, tally=0, schedule=0)
     s.persistent_reset()
     T = torch.full((s.total_cells,), 0.3, dtype=torch.float64, device="cuda")
     for it in range(warmup):
@@ -302,7 +359,8 @@ def persistent_scheme_time(wl, make_solver, steps=10, warmup=3):
     ms = ev0.elapsed_time(ev1) / steps
     slots = g["slots"]
     flights = int(g["counters"][0].item())
-    bytes_per_step = slots * (5 * 8 + 3 * 4 + 5 * 8 + 2 * 4)
+    rb = 4 if prec == "fp32" else 8   # position and direction words
+    bytes_per_step = slots * (4 * rb + 8 + 3 * 4 + 4 * rb + 8 + 2 * 4)
     peak = 6783.5
     try:
         peak = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["hbm_gbs"]
@@ -312,7 +370,7 @@ def persistent_scheme_time(wl, make_solver, steps=10, warmup=3):
     del s
     return {"slots": slots, "ms_per_iteration": ms, "flights_per_s": flights / (ms * 1e-3),
             "state_bytes_per_iteration": bytes_per_step, "achieved_gbs": gbs, "hbm_peak_gbs": peak,
-            "hbm_frac": gbs / peak, "precision": "fp64"}
+            "hbm_frac": gbs / peak, "tracking": prec}
 
 
 def run_ours(args):
@@ -470,6 +528,9 @@ def run_ours(args):
                 del sp1
             plain = {"sweep_crossings_per_s": ptot_cross / (ptot_ms / 1e3),
                      "steady_s_sequential": psteady if not args.no_steady else None, "steady_iters": piters}
+        others = None
+        if not args.no_configs:
+            others = other_config_sweeps(WL, make_solver)
         persistent = None
         if not args.no_persistent:
             persistent = persistent_scheme_time(wl, make_solver)
@@ -505,6 +566,7 @@ def run_ours(args):
             "time_to_steady": steady,
             "adjoint_gradient": adjoint,
             "persistent_scheme": persistent,
+            "other_workload_sweeps": others,
             "plain_fp64": plain,
             "speedup_vs_plain_fp64_sweep": (sweep_counts[3] / sw_s) / plain["sweep_crossings_per_s"] if plain else None,
             "e2e": {"value": e2e_value, "unit": "cell-crossings/s", "h2d_bytes_per_step": nc * 8,

@@ -207,7 +207,8 @@ iugkp_status iugkp_average(iugkp_ctx *ctx, double *T_inout_dev, int n_steps, uns
 
 /* Persistent null-collision population (Sec. 3.2 steps (1)-(6)): the paper's own form of the
  * variable-tau iteration, next to the stateless sweep of iugkp_sweep. A fixed population
- * (N_b slots per (band, cell) and N_w,b per (band, boundary face)) makes one candidate
+ * (per band, N_b slots per cell numbered q * ncells + cell, then N_w,b per boundary face
+ * numbered q * faces + face) makes one candidate
  * flight per iteration. A particle whose flight ended in a real collision (or at a wall) is
  * re-emitted next iteration from that cell (or boundary face) with the home's power shared
  * by the particles that ended there: w = (C_b T_emit V / tau_b) / N in a cell, T_emit = T +

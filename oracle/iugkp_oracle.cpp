@@ -767,7 +767,8 @@ int orc_band_split(int nb, long long N, const double* r, long long* out) {
 // w = (C_b v_b T_face A / 4) / N_abs(b, face) on a face (a black wall absorbs what reaches
 // it and emits at its temperature). A null candidate keeps position, direction and weight
 // and flies again (step (6)).
-// Slots: N_b per (band, cell) in band-major, cell order, then N_w,b per (band, wall, face).
+// Slots: per band N_b per cell in q-major order (slot q * ncells + cell), then per band
+// N_w,b per boundary face (slot q * faces + face).
 // Draws of slot k in iteration it: Stream(seed, instance, band, it, 0x80000000, k):
 // emission uniforms if re-emitted, then the (path, accept) pair.
 // Per slot: x[3], s[3], w, home (cell index, or ncells + boundary-face index in wall

@@ -312,12 +312,13 @@ class Population:
         nc, nb = p.ncells, p.nb
         nbf = sum(p.wall_faces())
         slots_b, homes = [], []
+        # slot q * ncells + cell of each band, then q * faces + face (q-major)
         for b in range(nb):
             slots_b.append(np.full(int(p.n_band[b]) * nc, b))
-            homes.append(np.repeat(np.arange(nc), int(p.n_band[b])))
+            homes.append(np.tile(np.arange(nc), int(p.n_band[b])))
         for b in range(nb):
             slots_b.append(np.full(int(p.n_wall_band[b]) * nbf, b))
-            homes.append(nc + np.repeat(np.arange(nbf), int(p.n_wall_band[b])))
+            homes.append(nc + np.tile(np.arange(nbf), int(p.n_wall_band[b])))
         self.band = np.ascontiguousarray(np.concatenate(slots_b), dtype=np.int32)
         self.home = np.ascontiguousarray(np.concatenate(homes), dtype=np.int64)
         self.n = len(self.band)

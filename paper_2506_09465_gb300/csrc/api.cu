@@ -110,7 +110,7 @@ void free_all(Ctx* c) {
                   c->d_group_mag, c->d_mag, c->d_wall_unit, c->d_all_beg, c->d_all_end, c->d_all_cost_prefix,
                   c->d_all_group_mag, c->d_R32, c->d_W32, c->d_F32, c->d_m2, c->d_wallTf,
                   c->d_pslot_off, c->d_phome_off, c->d_pnband, c->d_pnwall, c->d_px, c->d_pband, c->d_phome,
-                  c->d_pdue, c->d_pcount};
+                  c->d_pdue, c->d_pcount, c->d_phome_w};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (c->h_pinned) cudaFreeHost(c->h_pinned);
@@ -1130,13 +1130,14 @@ iugkp_status iugkp_persistent_reset(iugkp_ctx* ctx, void* cuda_stream) {
   if (slot_off[c->n_inst] >= (1ll << 31)) return fail(c, IUGKP_EINVAL, "persistent population above 2^31 slots");
   if (c->pers_n != slot_off[c->n_inst] || !c->d_px) {
     void* olds[] = {c->d_pslot_off, c->d_phome_off, c->d_pnband, c->d_pnwall, c->d_px, c->d_pband, c->d_phome,
-                    c->d_pdue, c->d_pcount};
+                    c->d_pdue, c->d_pcount, c->d_phome_w};
     for (void* p : olds)
       if (p) cudaFree(p);
     c->d_pslot_off = c->d_phome_off = c->d_pnband = c->d_pnwall = nullptr;
     c->d_px = nullptr;
     c->d_pband = c->d_phome = c->d_pdue = nullptr;
     c->d_pcount = nullptr;
+    c->d_phome_w = nullptr;
     c->pers_n = slot_off[c->n_inst];
     c->pers_homes = home_off[c->n_inst];
     iugkp_status st;
@@ -1149,6 +1150,7 @@ iugkp_status iugkp_persistent_reset(iugkp_ctx* ctx, void* cuda_stream) {
     if ((st = dalloc(c, &c->d_phome, (size_t)c->pers_n)) != IUGKP_OK) return st;
     if ((st = dalloc(c, &c->d_pdue, (size_t)c->pers_n)) != IUGKP_OK) return st;
     if ((st = dalloc(c, &c->d_pcount, (size_t)2 * c->pers_homes)) != IUGKP_OK) return st;
+    if ((st = dalloc(c, &c->d_phome_w, (size_t)c->pers_homes)) != IUGKP_OK) return st;
   }
   c->pers_parity = 0;
   CK(launch_persistent_init(c, s), "persistent init");

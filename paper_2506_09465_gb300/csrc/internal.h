@@ -120,7 +120,9 @@ struct Ctx {
   long long* d_phome_off = nullptr;
   long long* d_pnband = nullptr;  // [n_inst * nb]
   long long* d_pnwall = nullptr;  // [nb]
-  double* d_px = nullptr;         // [7 * pers_n]: x, y, z, s_x, s_y, s_z, w
+  double* d_px = nullptr;         // [7 * pers_n] doubles: x, y, z, s_x, s_y, s_z (FP64, or FP32 packed
+                                  // at the start), then w at 6 * pers_n
+  double* d_phome_w = nullptr;    // [pers_homes] power per re-emitted particle of each home
   int* d_pband = nullptr;
   int* d_phome = nullptr;
   int* d_pdue = nullptr;

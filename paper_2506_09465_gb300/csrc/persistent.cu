@@ -1,4 +1,6 @@
-// Persistent null-collision population (arXiv 2506.09465 Sec. 3.2 steps (1)-(6)), FP64.
+// Persistent null-collision population (arXiv 2506.09465 Sec. 3.2 steps (1)-(6)). Positions,
+// directions and flight lengths in FP64 or FP32 (the context's tracking precision), weights
+// and tallies in FP64.
 //
 // A fixed population of particles (the paper's count stays fixed, so one array holds it)
 // makes one candidate flight per iteration. Every particle has a home: the cell of its last
@@ -10,9 +12,11 @@
 // direction and weight and flies again. One thread per particle; state in structure-of-
 // arrays form, read and written once per iteration (coalesced).
 //
-// Slots of an instance: N_b per (band, cell), band-major then cell order, then N_w,b per
-// (band, boundary face) with faces in wall order (-x, +x, -y, +y, -z, +z; on the wall normal
-// to axis a the faces run over axes (a+1)%3 and (a+2)%3, the first fastest). Draws of slot
+// Slots of an instance: per band, N_b per cell in q-major order (slot q * ncells + cell, so
+// neighbouring slots start in different cells and their tallies rarely meet at one
+// address), then per band N_w,b per boundary face (slot q * faces + face), faces in wall
+// order (-x, +x, -y, +y, -z, +z; on the wall normal to axis a the faces run over axes
+// (a+1)%3 and (a+2)%3, the first fastest). Draws of slot
 // k of instance i in iteration it: Philox counter (block, k, 0x80000000, band << 24 | it),
 // key (seed low word, seed high word ^ instance id): the emission uniforms when the particle
 // is re-emitted, then the (path, accept) pair of its flight.
@@ -40,7 +44,9 @@ struct PArgs {
   const double* v;             // [nb]
   const double* wcoef;         // [inst * nb * 6] C_b v_b A / (4 N_w)
   const double* wallTf;        // [boundary faces]
-  double *px, *py, *pz, *sx, *sy, *sz, *pw;
+  void* state;                 // positions and directions: 6 arrays of n_slots Real
+  double* pw;                  // [n_slots] weights
+  const double* home_w;        // [homes] power per particle re-emitted from each home
   const int* band;
   int* home;
   int* due;
@@ -55,8 +61,14 @@ struct PArgs {
   long long n_slots;
 };
 
-template <int DIM>
+template <int DIM, typename Real>
 __global__ void __launch_bounds__(256) persistent_step_kernel(PArgs A) {
+  Real* px = reinterpret_cast<Real*>(A.state);
+  Real* py = px + A.n_slots;
+  Real* pz = px + 2 * A.n_slots;
+  Real* sx = px + 3 * A.n_slots;
+  Real* sy = px + 4 * A.n_slots;
+  Real* sz = px + 5 * A.n_slots;
   unsigned c_flights = 0, c_cand = 0, c_real = 0, c_exit = 0;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < A.n_slots;
        i += (long long)gridDim.x * blockDim.x) {
@@ -70,47 +82,44 @@ __global__ void __launch_bounds__(256) persistent_step_kernel(PArgs A) {
     const long long nh = (long long)in.ncells + nbf;  // homes per band
     Stream st;
     st.init(A.seed, in.inst_id, (uint32_t)b, A.it, 0x80000000u, (uint32_t)local);
-    double x[3] = {A.px[i], DIM >= 2 ? A.py[i] : 0.0, DIM >= 3 ? A.pz[i] : 0.0};
-    double s[3] = {A.sx[i], DIM >= 2 ? A.sy[i] : 0.0, DIM >= 3 ? A.sz[i] : 0.0};
+    Real x[3] = {px[i], DIM >= 2 ? py[i] : (Real)0, DIM >= 3 ? pz[i] : (Real)0};
+    Real s[3] = {sx[i], DIM >= 2 ? sy[i] : (Real)0, DIM >= 3 ? sz[i] : (Real)0};
     double w = A.pw[i];
     int h = A.home[i];
     st.j = 0;
     if (A.due[i]) {
-      const double nprev = (double)A.n_prev[A.home_off[k] + (long long)b * nh + h];
+      w = A.home_w[A.home_off[k] + (long long)b * nh + h];
       if (h < in.ncells) {
         // re-emission in the cell of the real collision (Sec. 3.2 step (2))
         const int ci[3] = {h % n0, (h / n0) % n1, h / (n0 * n1)};
-        double u_mu, u_phi = 0.5;
+        const Real hx = (Real)in.h[0], hy = (Real)in.h[1], hz = (Real)in.h[2];
+        Real u_mu, u_phi = (Real)0.5;
         if (DIM == 1) {
-          x[0] = (ci[0] + word_uniform<double>(st.buf.x)) * in.h[0];
-          u_mu = word_uniform<double>(st.buf.y);
+          x[0] = ((Real)ci[0] + word_uniform<Real>(st.buf.x)) * hx;
+          u_mu = word_uniform<Real>(st.buf.y);
         } else if (DIM == 2) {
-          x[0] = (ci[0] + word_uniform<double>(st.buf.x)) * in.h[0];
-          x[1] = (ci[1] + word_uniform<double>(st.buf.y)) * in.h[1];
-          u_mu = word_uniform<double>(st.buf.z);
-          u_phi = word_uniform<double>(st.buf.w);
+          x[0] = ((Real)ci[0] + word_uniform<Real>(st.buf.x)) * hx;
+          x[1] = ((Real)ci[1] + word_uniform<Real>(st.buf.y)) * hy;
+          u_mu = word_uniform<Real>(st.buf.z);
+          u_phi = word_uniform<Real>(st.buf.w);
         } else {
-          x[0] = (ci[0] + word_uniform<double>(st.buf.x)) * in.h[0];
-          x[1] = (ci[1] + word_uniform<double>(st.buf.y)) * in.h[1];
-          x[2] = (ci[2] + word_uniform<double>(st.buf.z)) * in.h[2];
-          u_mu = word_uniform<double>(st.buf.w);
+          x[0] = ((Real)ci[0] + word_uniform<Real>(st.buf.x)) * hx;
+          x[1] = ((Real)ci[1] + word_uniform<Real>(st.buf.y)) * hy;
+          x[2] = ((Real)ci[2] + word_uniform<Real>(st.buf.z)) * hz;
+          u_mu = word_uniform<Real>(st.buf.w);
           st.load_block(1);
-          u_phi = word_uniform<double>(st.buf.x);
+          u_phi = word_uniform<Real>(st.buf.x);
         }
-        const double mu = 2.0 * u_mu - 1.0;
+        const Real mu = (Real)2 * u_mu - (Real)1;
         s[0] = mu;
         if (DIM >= 2) {
-          const double sn = sqrt(1.0 - mu * mu);
-          double sp, cp;
-          RealTraits<double>::sincos2pi(u_phi, &sp, &cp);
+          const Real sn = sqrt((Real)1 - mu * mu);
+          Real sp, cp;
+          RealTraits<Real>::sincos2pi(u_phi, &sp, &cp);
           s[1] = sn * cp;
           s[2] = sn * sp;
         }
         st.j = thermal_uniforms(DIM);
-        double te = A.T[in.cell_off + h];
-        if (A.srcshift) te += A.srcshift[in.cell_off + h];
-        // C_b V / tau_{b,c} = coef * N_b
-        w = A.coef[in.bc_off + (long long)b * in.ncells + h] * (double)A.nband[(long long)k * A.nb + b] * te / nprev;
       } else {
         // re-emission from the boundary face that absorbed it (black wall)
         const int bf = h - in.ncells;
@@ -123,36 +132,35 @@ __global__ void __launch_bounds__(256) persistent_step_kernel(PArgs A) {
         f[a] = side ? in.n[a] : 0;
         f[o1] = j % no1;
         f[o2] = j / no1;
-        double u_n, u_phi = 0.5;
+        Real u_n, u_phi = (Real)0.5;
         if (DIM == 1) {
-          u_n = word_uniform<double>(st.buf.x);
+          u_n = word_uniform<Real>(st.buf.x);
         } else if (DIM == 2) {
           const int t = (o1 < 2) ? o1 : o2;
-          x[t] = (f[t] + word_uniform<double>(st.buf.x)) * in.h[t];
-          u_n = word_uniform<double>(st.buf.y);
-          u_phi = word_uniform<double>(st.buf.z);
+          x[t] = ((Real)f[t] + word_uniform<Real>(st.buf.x)) * (Real)in.h[t];
+          u_n = word_uniform<Real>(st.buf.y);
+          u_phi = word_uniform<Real>(st.buf.z);
         } else {
           const int t0 = o1 < o2 ? o1 : o2, t1 = o1 < o2 ? o2 : o1;
-          x[t0] = (f[t0] + word_uniform<double>(st.buf.x)) * in.h[t0];
-          x[t1] = (f[t1] + word_uniform<double>(st.buf.y)) * in.h[t1];
-          u_n = word_uniform<double>(st.buf.z);
-          u_phi = word_uniform<double>(st.buf.w);
+          x[t0] = ((Real)f[t0] + word_uniform<Real>(st.buf.x)) * (Real)in.h[t0];
+          x[t1] = ((Real)f[t1] + word_uniform<Real>(st.buf.y)) * (Real)in.h[t1];
+          u_n = word_uniform<Real>(st.buf.z);
+          u_phi = word_uniform<Real>(st.buf.w);
         }
-        x[a] = f[a] * in.h[a];
-        const double mn = sqrt(u_n);
+        x[a] = (Real)f[a] * (Real)in.h[a];
+        const Real mn = sqrt(u_n);
         s[a] = side ? -mn : mn;
         if (DIM >= 2) {
-          const double stn = sqrt(1.0 - u_n);
-          double sp, cp;
-          RealTraits<double>::sincos2pi(u_phi, &sp, &cp);
+          const Real stn = sqrt((Real)1 - u_n);
+          Real sp, cp;
+          RealTraits<Real>::sincos2pi(u_phi, &sp, &cp);
           s[o1] = stn * cp;
           s[o2] = stn * sp;
         } else {
-          s[o1] = 0.0;
-          s[o2] = 0.0;
+          s[o1] = (Real)0;
+          s[o2] = (Real)0;
         }
         st.j = wall_uniforms(DIM);
-        w = A.wcoef[((long long)k * A.nb + b) * 6 + wl] * (double)A.nwall[b] * A.wallTf[in.bface_off + bf] / nprev;
       }
     }
     // one flight (Sec. 3.2 step (3)): path -ln(u) v tau_maj
@@ -160,17 +168,17 @@ __global__ void __launch_bounds__(256) persistent_step_kernel(PArgs A) {
     uint32_t ua, ub;
     st.next_pair(ua, ub);
     const double tm = A.taumaj[(long long)k * A.nb + b];
-    const double ell = -log(word_uniform<double>(ua)) * A.v[b] * tm;
-    double tw = INFINITY;
+    const Real ell = -RealTraits<Real>::log_(word_uniform<Real>(ua)) * (Real)(A.v[b] * tm);
+    Real tw = RealTraits<Real>::inf();
     int wl = -1;
 #pragma unroll
     for (int a = 0; a < DIM; ++a) {
-      if (s[a] == 0.0) continue;
-      const double L = in.h[a] * in.n[a];
-      const double t = s[a] > 0.0 ? (L - x[a]) / s[a] : -x[a] / s[a];
+      if (s[a] == (Real)0) continue;
+      const Real L = (Real)(in.h[a] * in.n[a]);
+      const Real t = s[a] > (Real)0 ? (L - x[a]) / s[a] : -x[a] / s[a];
       if (t < tw) {
         tw = t;
-        wl = 2 * a + (s[a] > 0.0 ? 1 : 0);
+        wl = 2 * a + (s[a] > (Real)0 ? 1 : 0);
       }
     }
     int due = 1;
@@ -180,8 +188,8 @@ __global__ void __launch_bounds__(256) persistent_step_kernel(PArgs A) {
       atomicAdd(&A.wall[in.wall_off + wl], w);
       const int a = wl >> 1, o1 = (a + 1) % 3, o2 = (a + 2) % 3;
       int j1 = 0, j2 = 0;
-      if (o1 < DIM) j1 = min(max((int)floor((x[o1] + tw * s[o1]) / in.h[o1]), 0), in.n[o1] - 1);
-      if (o2 < DIM) j2 = min(max((int)floor((x[o2] + tw * s[o2]) / in.h[o2]), 0), in.n[o2] - 1);
+      if (o1 < DIM) j1 = min(max((int)floor((x[o1] + tw * s[o1]) / (Real)in.h[o1]), 0), in.n[o1] - 1);
+      if (o2 < DIM) j2 = min(max((int)floor((x[o2] + tw * s[o2]) / (Real)in.h[o2]), 0), in.n[o2] - 1);
       h = in.ncells + in.wface_off[wl] + j2 * in.n[o1] + j1;
       atomicAdd(&A.n_new[A.home_off[k] + (long long)b * nh + h], 1u);
     } else {
@@ -189,14 +197,14 @@ __global__ void __launch_bounds__(256) persistent_step_kernel(PArgs A) {
 #pragma unroll
       for (int a = 0; a < DIM; ++a) {
         x[a] += ell * s[a];
-        ci[a] = min(max((int)floor(x[a] / in.h[a]), 0), in.n[a] - 1);
+        ci[a] = min(max((int)floor(x[a] / (Real)in.h[a]), 0), in.n[a] - 1);
       }
       const int c = ci[0] + n0 * (ci[1] + n1 * ci[2]);
       // candidate (steps (4)-(5)): W from every candidate, R and the count from real ones
       c_cand += 1;
       const long long jb = in.bc_off + (long long)b * in.ncells + c;
       atomicAdd(&A.W[jb], w * tm);
-      if (word_uniform<double>(ub) < A.ratio64[jb]) {
+      if (word_uniform<Real>(ub) < (Real)A.ratio64[jb]) {
         c_real += 1;
         atomicAdd(&A.R[jb], w);
         h = c;
@@ -205,12 +213,12 @@ __global__ void __launch_bounds__(256) persistent_step_kernel(PArgs A) {
         due = 0;  // step (6): same direction and weight, a new path next iteration
       }
     }
-    A.px[i] = x[0];
-    if (DIM >= 2) A.py[i] = x[1];
-    if (DIM >= 3) A.pz[i] = x[2];
-    A.sx[i] = s[0];
-    if (DIM >= 2) A.sy[i] = s[1];
-    if (DIM >= 3) A.sz[i] = s[2];
+    px[i] = x[0];
+    if (DIM >= 2) py[i] = x[1];
+    if (DIM >= 3) pz[i] = x[2];
+    sx[i] = s[0];
+    if (DIM >= 2) sy[i] = s[1];
+    if (DIM >= 3) sz[i] = s[2];
     A.pw[i] = w;
     A.home[i] = h;
     A.due[i] = due;
@@ -224,6 +232,42 @@ __global__ void __launch_bounds__(256) persistent_step_kernel(PArgs A) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
     if ((threadIdx.x & 31) == 0 && v) atomicAdd(&A.counters[slots[q]], v);
+  }
+}
+
+// Power per particle re-emitted from each (band, home) this iteration: the home's power
+// (C_b T_emit V / tau_b for a cell, C_b v_b T_face A / 4 for a boundary face) over the
+// particles that ended there in the previous iteration (0 where none did).
+__global__ void persistent_home_power_kernel(const InstDesc* inst, int n_inst, int nb, const long long* home_off,
+                                             const long long* nband, const long long* nwall, const double* T,
+                                             const double* srcshift, const double* coef, const double* wcoef,
+                                             const double* wallTf, const unsigned* n_prev, double* home_w,
+                                             long long n_homes) {
+  for (long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x; j < n_homes;
+       j += (long long)gridDim.x * blockDim.x) {
+    int k = 0;
+    while (k + 1 < n_inst && home_off[k + 1] <= j) ++k;
+    const InstDesc& in = inst[k];
+    const long long nh = (home_off[k + 1] - home_off[k]) / nb;
+    const long long r = j - home_off[k];
+    const int b = (int)(r / nh);
+    const long long h = r - (long long)b * nh;
+    const unsigned n = n_prev[j];
+    double pw = 0.0;
+    if (n > 0) {
+      if (h < in.ncells) {
+        double te = T[in.cell_off + h];
+        if (srcshift) te += srcshift[in.cell_off + h];
+        // C_b V / tau_{b,c} = coef * N_b
+        pw = coef[in.bc_off + (long long)b * in.ncells + h] * (double)nband[(long long)k * nb + b] * te / (double)n;
+      } else {
+        const int bf = (int)(h - in.ncells);
+        int wl = 0;
+        while (wl + 1 < 2 * in.dim && bf >= in.wface_off[wl + 1]) ++wl;
+        pw = wcoef[((long long)k * nb + b) * 6 + wl] * (double)nwall[b] * wallTf[in.bface_off + bf] / (double)n;
+      }
+    }
+    home_w[j] = pw;
   }
 }
 
@@ -247,13 +291,9 @@ cudaError_t launch_persistent_step(const Ctx* c, const double* T, unsigned it, d
   a.v = c->d_v;
   a.wcoef = c->d_wcoef;
   a.wallTf = c->d_wallTf;
-  a.px = c->d_px;
-  a.py = c->d_px + c->pers_n;
-  a.pz = c->d_px + 2 * c->pers_n;
-  a.sx = c->d_px + 3 * c->pers_n;
-  a.sy = c->d_px + 4 * c->pers_n;
-  a.sz = c->d_px + 5 * c->pers_n;
-  a.pw = c->d_px + 6 * c->pers_n;
+  a.state = c->d_px;
+  a.pw = reinterpret_cast<double*>(c->d_px) + 6 * c->pers_n;  // after 6 arrays of FP64 or FP32
+  a.home_w = c->d_phome_w;
   a.band = c->d_pband;
   a.home = c->d_phome;
   a.due = c->d_pdue;
@@ -266,12 +306,24 @@ cudaError_t launch_persistent_step(const Ctx* c, const double* T, unsigned it, d
   a.seed = c->opt.seed;
   a.it = it;
   a.n_slots = c->pers_n;
+  {
+    const unsigned hb = (unsigned)std::min<long long>((c->pers_homes + 255) / 256 + 1, (long long)c->sm_count * 16);
+    persistent_home_power_kernel<<<hb, 256, 0, s>>>(c->d_inst, c->n_inst, c->nb, c->d_phome_off, c->d_pnband,
+                                                    c->d_pnwall, T, c->d_srcshift, c->d_coef, c->d_wcoef, c->d_wallTf,
+                                                    a.n_prev, c->d_phome_w, c->pers_homes);
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
   const long long want = (c->pers_n + 255) / 256;
   const unsigned blocks = (unsigned)std::min<long long>(std::max<long long>(want, 1), (long long)c->sm_count * 16);
-  switch (c->dim) {
-    case 1: persistent_step_kernel<1><<<blocks, 256, 0, s>>>(a); break;
-    case 2: persistent_step_kernel<2><<<blocks, 256, 0, s>>>(a); break;
-    default: persistent_step_kernel<3><<<blocks, 256, 0, s>>>(a); break;
+  const bool f32 = c->opt.precision == IUGKP_TRACK_FP32;
+  switch (c->dim * 2 + (f32 ? 1 : 0)) {
+    case 2: persistent_step_kernel<1, double><<<blocks, 256, 0, s>>>(a); break;
+    case 3: persistent_step_kernel<1, float><<<blocks, 256, 0, s>>>(a); break;
+    case 4: persistent_step_kernel<2, double><<<blocks, 256, 0, s>>>(a); break;
+    case 5: persistent_step_kernel<2, float><<<blocks, 256, 0, s>>>(a); break;
+    case 6: persistent_step_kernel<3, double><<<blocks, 256, 0, s>>>(a); break;
+    default: persistent_step_kernel<3, float><<<blocks, 256, 0, s>>>(a); break;
   }
   return cudaGetLastError();
 }
@@ -299,12 +351,12 @@ __global__ void persistent_init_kernel(const InstDesc* inst, int n_inst, int nb,
     for (int bb = 0; bb < nb; ++bb) thermal += nband[(long long)k * nb + bb] * in.ncells;
     if (r < thermal) {
       while (r >= nband[(long long)k * nb + b] * in.ncells) r -= nband[(long long)k * nb + b] * in.ncells, ++b;
-      h = (int)(r / nband[(long long)k * nb + b]);
+      h = (int)(r % in.ncells);
     } else {
       r -= thermal;
       const long long nbf = (home_off[k + 1] - home_off[k]) / nb - in.ncells;
       while (r >= nwall[b] * nbf) r -= nwall[b] * nbf, ++b;
-      h = in.ncells + (int)(r / nwall[b]);
+      h = in.ncells + (int)(r % nbf);
     }
     band[i] = b;
     home[i] = h;
