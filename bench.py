@@ -62,7 +62,7 @@ def run_profile(args):
     if args.profile == "persistent":
         # one cavity instance (Kn from --kn, default 1): population steps only
         wl = WL.cavity_sweep(NGRID, (args.kn if args.kn is not None else 1.0,), NPART)
-        s = make_solver(wl, seed=0, precision=0, tally=0, schedule=0)
+        s = make_solver(wl, seed=0, precision=0 if args.mode == "plain64" else 1, tally=0, schedule=0)
         s.persistent_reset()
         T = torch.full((s.total_cells,), 0.3, dtype=torch.float64, device="cuda")
         ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)

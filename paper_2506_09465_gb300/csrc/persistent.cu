@@ -61,8 +61,21 @@ struct PArgs {
   long long n_slots;
 };
 
+// Element i of a 3-vector with a runtime index, by selects on constant indices (the vectors
+// stay in registers instead of local memory).
+template <typename V>
+__device__ __forceinline__ V pick(const V (&v)[3], int i) {
+  return i == 0 ? v[0] : (i == 1 ? v[1] : v[2]);
+}
+template <typename V>
+__device__ __forceinline__ void put(V (&v)[3], int i, V x) {
+  v[0] = i == 0 ? x : v[0];
+  v[1] = i == 1 ? x : v[1];
+  v[2] = i == 2 ? x : v[2];
+}
+
 template <int DIM, typename Real>
-__global__ void __launch_bounds__(256) persistent_step_kernel(PArgs A) {
+__global__ void __launch_bounds__(256, 4) persistent_step_kernel(PArgs A) {
   Real* px = reinterpret_cast<Real*>(A.state);
   Real* py = px + A.n_slots;
   Real* pz = px + 2 * A.n_slots;
@@ -128,37 +141,37 @@ __global__ void __launch_bounds__(256) persistent_step_kernel(PArgs A) {
         const int a = wl >> 1, side = wl & 1, o1 = (a + 1) % 3, o2 = (a + 2) % 3;
         const int j = bf - in.wface_off[wl];
         const int no1 = in.n[o1];
-        int f[3];
-        f[a] = side ? in.n[a] : 0;
-        f[o1] = j % no1;
-        f[o2] = j / no1;
+        int f[3] = {0, 0, 0};
+        put(f, a, side ? in.n[a] : 0);
+        put(f, o1, j % no1);
+        put(f, o2, j / no1);
         Real u_n, u_phi = (Real)0.5;
         if (DIM == 1) {
           u_n = word_uniform<Real>(st.buf.x);
         } else if (DIM == 2) {
           const int t = (o1 < 2) ? o1 : o2;
-          x[t] = ((Real)f[t] + word_uniform<Real>(st.buf.x)) * (Real)in.h[t];
+          put(x, t, ((Real)pick(f, t) + word_uniform<Real>(st.buf.x)) * (Real)in.h[t]);
           u_n = word_uniform<Real>(st.buf.y);
           u_phi = word_uniform<Real>(st.buf.z);
         } else {
           const int t0 = o1 < o2 ? o1 : o2, t1 = o1 < o2 ? o2 : o1;
-          x[t0] = ((Real)f[t0] + word_uniform<Real>(st.buf.x)) * (Real)in.h[t0];
-          x[t1] = ((Real)f[t1] + word_uniform<Real>(st.buf.y)) * (Real)in.h[t1];
+          put(x, t0, ((Real)pick(f, t0) + word_uniform<Real>(st.buf.x)) * (Real)in.h[t0]);
+          put(x, t1, ((Real)pick(f, t1) + word_uniform<Real>(st.buf.y)) * (Real)in.h[t1]);
           u_n = word_uniform<Real>(st.buf.z);
           u_phi = word_uniform<Real>(st.buf.w);
         }
-        x[a] = (Real)f[a] * (Real)in.h[a];
+        put(x, a, (Real)pick(f, a) * (Real)in.h[a]);
         const Real mn = sqrt(u_n);
-        s[a] = side ? -mn : mn;
+        put(s, a, side ? -mn : mn);
         if (DIM >= 2) {
           const Real stn = sqrt((Real)1 - u_n);
           Real sp, cp;
           RealTraits<Real>::sincos2pi(u_phi, &sp, &cp);
-          s[o1] = stn * cp;
-          s[o2] = stn * sp;
+          put(s, o1, stn * cp);
+          put(s, o2, stn * sp);
         } else {
-          s[o1] = (Real)0;
-          s[o2] = (Real)0;
+          put(s, o1, (Real)0);
+          put(s, o2, (Real)0);
         }
         st.j = wall_uniforms(DIM);
       }
@@ -188,8 +201,8 @@ __global__ void __launch_bounds__(256) persistent_step_kernel(PArgs A) {
       atomicAdd(&A.wall[in.wall_off + wl], w);
       const int a = wl >> 1, o1 = (a + 1) % 3, o2 = (a + 2) % 3;
       int j1 = 0, j2 = 0;
-      if (o1 < DIM) j1 = min(max((int)floor((x[o1] + tw * s[o1]) / (Real)in.h[o1]), 0), in.n[o1] - 1);
-      if (o2 < DIM) j2 = min(max((int)floor((x[o2] + tw * s[o2]) / (Real)in.h[o2]), 0), in.n[o2] - 1);
+      if (o1 < DIM) j1 = min(max((int)floor((pick(x, o1) + tw * pick(s, o1)) / (Real)in.h[o1]), 0), in.n[o1] - 1);
+      if (o2 < DIM) j2 = min(max((int)floor((pick(x, o2) + tw * pick(s, o2)) / (Real)in.h[o2]), 0), in.n[o2] - 1);
       h = in.ncells + in.wface_off[wl] + j2 * in.n[o1] + j1;
       atomicAdd(&A.n_new[A.home_off[k] + (long long)b * nh + h], 1u);
     } else {
