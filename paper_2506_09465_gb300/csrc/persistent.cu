@@ -74,8 +74,17 @@ __device__ __forceinline__ void put(V (&v)[3], int i, V x) {
   v[2] = i == 2 ? x : v[2];
 }
 
+// Wall power is accumulated per block in shared memory and flushed once: every absorption
+// adding to one of 2 dim addresses per instance in global memory would serialise at the L2.
+constexpr int PERS_SHARED_WALLS = 384;
+
 template <int DIM, typename Real>
 __global__ void __launch_bounds__(256, 4) persistent_step_kernel(PArgs A) {
+  __shared__ double swall[PERS_SHARED_WALLS];
+  const int n_walls = 2 * DIM * A.n_inst;
+  const bool wall_shared = n_walls <= PERS_SHARED_WALLS;
+  for (int j = threadIdx.x; j < PERS_SHARED_WALLS; j += blockDim.x) swall[j] = 0.0;
+  __syncthreads();
   Real* px = reinterpret_cast<Real*>(A.state);
   Real* py = px + A.n_slots;
   Real* pz = px + 2 * A.n_slots;
@@ -83,8 +92,15 @@ __global__ void __launch_bounds__(256, 4) persistent_step_kernel(PArgs A) {
   Real* sy = px + 4 * A.n_slots;
   Real* sz = px + 5 * A.n_slots;
   unsigned c_flights = 0, c_cand = 0, c_real = 0, c_exit = 0;
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < A.n_slots;
-       i += (long long)gridDim.x * blockDim.x) {
+  const int lane = threadIdx.x & 31;
+  // every thread of a block runs the same number of passes, so warps are converged at the
+  // end of each pass (for the warp reduction of the wall tallies)
+  for (long long base = (long long)blockIdx.x * blockDim.x; base < A.n_slots;
+       base += (long long)gridDim.x * blockDim.x) {
+    const long long i = base + threadIdx.x;
+    int exit_key = -1;  // global wall index of this pass's absorption, if any
+    double exit_w = 0.0;
+    if (i < A.n_slots) {
     int k = 0;
     while (k + 1 < A.n_inst && A.slot_off[k + 1] <= i) ++k;
     const InstDesc& in = A.inst[k];
@@ -198,7 +214,8 @@ __global__ void __launch_bounds__(256, 4) persistent_step_kernel(PArgs A) {
     if (wl >= 0 && tw < ell) {
       // absorbed by the wall it reaches first; its home is the face it crossed
       c_exit += 1;
-      atomicAdd(&A.wall[in.wall_off + wl], w);
+      exit_key = in.wall_off + wl;
+      exit_w = w;
       const int a = wl >> 1, o1 = (a + 1) % 3, o2 = (a + 2) % 3;
       int j1 = 0, j2 = 0;
       if (o1 < DIM) j1 = min(max((int)floor((pick(x, o1) + tw * pick(s, o1)) / (Real)in.h[o1]), 0), in.n[o1] - 1);
@@ -236,7 +253,25 @@ __global__ void __launch_bounds__(256, 4) persistent_step_kernel(PArgs A) {
     A.home[i] = h;
     A.due[i] = due;
     (void)n2;
+    }
+    // wall tallies: the lanes that hit one wall are summed first, one atomic per wall
+    unsigned pending = __ballot_sync(0xffffffffu, exit_key >= 0);
+    while (pending) {
+      const int key = __shfl_sync(0xffffffffu, exit_key, __ffs(pending) - 1);
+      double v = exit_key == key ? exit_w : 0.0;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+      if (lane == 0) {
+        if (wall_shared) atomicAdd(&swall[key], v);
+        else atomicAdd(&A.wall[key], v);
+      }
+      pending &= ~__ballot_sync(0xffffffffu, exit_key == key);
+    }
   }
+  __syncthreads();
+  if (wall_shared)
+    for (int j = threadIdx.x; j < n_walls; j += blockDim.x)
+      if (swall[j] != 0.0) atomicAdd(&A.wall[j], swall[j]);
   unsigned long long vals[4] = {c_flights, c_cand, c_real, c_exit};
   const int slots[4] = {CNT_FLIGHTS, CNT_CANDIDATES, CNT_REAL, CNT_WALL_EXITS};
 #pragma unroll
