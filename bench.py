@@ -24,6 +24,7 @@ sys.path.insert(0, ROOT)
 
 METRIC = "cell-crossings/s and time-to-steady (res 1e-8) vs plain FP64 sweep, same GPU"
 KNS = (0.01, 0.1, 1.0, 10.0)
+SWEEP_DRAM_BYTES = 3.19e6  # ncu dram bytes per launch of the staged sweep on this workload
 NGRID = 128
 NPART = 1024
 
@@ -543,7 +544,8 @@ def run_ours(args):
             cpu = {"value": rate, "unit": "cell-crossings/s", "cores": 1, "kind": "oracle", "sample": sample}
         clocks = clk.summary()
         # Roofline of the dominant kernel (the sweep): ALU issue bound. Algorithmic
-        # lane-operations per event x events / kernel time.
+        # lane-operations per event of a cell-by-cell walk (10 per crossing, 50 per
+        # candidate, 200 per flight) x events / kernel time.
         OPS_CROSS, OPS_CAND, OPS_FLIGHT = 10, 50, 200
         sw_s = statistics.median(sweep_ms) / 1e3
         ops = (OPS_CROSS * sweep_counts[3] + OPS_CAND * sweep_counts[1] + OPS_FLIGHT * sweep_counts[0])
@@ -576,7 +578,10 @@ def run_ours(args):
             # plus three finalize passes (R, W, F) with compensated FP32 tallies
             "gpu_launches": args.steps * (11 + (3 if tuned.get("tally") == 2 else 0)),
             "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": peak_ops / 1e12,
-                         "unit": "Tops/s (FP32+INT32 lane ops)", "frac": achieved / peak_ops, "traffic": None,
+                         "unit": "Tops/s (FP32+INT32 lane ops)", "frac": achieved / peak_ops,
+                         # DRAM bytes (read + write) of one launch of this sweep kernel on this
+                         # workload, from one ncu capture of the kernel as it is
+                         "traffic": SWEEP_DRAM_BYTES,
                          "kernel": "sweep", "peak_source": "152 SMs x 128 lanes x 2.07 GHz (unit counts and clock)"},
             "cpu_baseline": cpu,
             "clocks": clocks,

@@ -24,7 +24,7 @@
 //   * the adjoint of one sweep (with draws fixed a sweep is a linear map, Sec. 2,
 //     Eq. "sum-g"), by re-tracing each particle and gathering at its real collision.
 //
-// Readings of the paper that this file fixes (each one is listed in the design doc):
+// Readings of the paper that this file fixes:
 //   * emission weights are powers (thermal C_b T V / tau_b, wall C_b v_b T_w A / 4),
 //     so that with constant tau, multiplying by tau gives the paper's w = W / N;
 //   * a particle keeps flying through its null collisions inside the same sweep, with
