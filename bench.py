@@ -25,6 +25,7 @@ sys.path.insert(0, ROOT)
 METRIC = "cell-crossings/s and time-to-steady (res 1e-8) vs plain FP64 sweep, same GPU"
 KNS = (0.01, 0.1, 1.0, 10.0)
 SWEEP_DRAM_BYTES = 3.19e6  # ncu dram bytes per launch of the staged sweep on this workload
+SWEEP_ISSUE_UTIL = 0.769   # ncu smsp__issue_active of the same launch
 NGRID = 128
 NPART = 1024
 
@@ -582,6 +583,9 @@ def run_ours(args):
                          # DRAM bytes (read + write) of one launch of this sweep kernel on this
                          # workload, from one ncu capture of the kernel as it is
                          "traffic": SWEEP_DRAM_BYTES,
+                         # the hardware measure of the same kernel on this workload (ncu):
+                         # issued instructions / (SMs x 4 schedulers x cycles)
+                         "issue_slot_utilisation_ncu": SWEEP_ISSUE_UTIL,
                          "kernel": "sweep", "peak_source": "152 SMs x 128 lanes x 2.07 GHz (unit counts and clock)"},
             "cpu_baseline": cpu,
             "clocks": clocks,
