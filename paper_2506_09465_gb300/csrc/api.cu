@@ -110,7 +110,7 @@ void free_all(Ctx* c) {
                   c->d_group_mag, c->d_mag, c->d_wall_unit, c->d_all_beg, c->d_all_end, c->d_all_cost_prefix,
                   c->d_all_group_mag, c->d_R32, c->d_W32, c->d_F32, c->d_m2, c->d_wallTf,
                   c->d_pslot_off, c->d_phome_off, c->d_pnband, c->d_pnwall, c->d_px, c->d_pband, c->d_phome,
-                  c->d_pdue, c->d_pcount, c->d_phome_w};
+                  c->d_pdue, c->d_pcount, c->d_phome_w, c->d_wemit};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (c->h_pinned) cudaFreeHost(c->h_pinned);
@@ -654,6 +654,7 @@ iugkp_status iugkp_create_batch(int n, const iugkp_grid* g, const double* const*
   if ((s = dalloc(c, &c->d_R, (size_t)nb * cell_off)) != IUGKP_OK) return bail(s);
   if ((s = dalloc(c, &c->d_W, (size_t)nb * cell_off)) != IUGKP_OK) return bail(s);
   if ((s = dalloc(c, &c->d_F, face_off)) != IUGKP_OK) return bail(s);
+  if ((s = dalloc(c, &c->d_wemit, (size_t)nb * cell_off)) != IUGKP_OK) return bail(s);
   if ((s = dalloc(c, &c->d_wall, c->total_walls)) != IUGKP_OK) return bail(s);
   if ((s = dalloc(c, &c->d_red, 1024)) != IUGKP_OK) return bail(s);
   if ((s = dalloc(c, &c->d_counters, CNT_N)) != IUGKP_OK) return bail(s);
@@ -727,6 +728,7 @@ SweepArgs base_args(Ctx* c) {
   a.v = c->d_v;
   a.wcoef = c->d_wcoef;
   a.wallT = c->d_wallT;
+  a.wemit = c->d_wemit;
   a.wallTf = c->d_wallTf;
   a.seed = c->opt.seed;
   a.budget = c->opt.step_budget;

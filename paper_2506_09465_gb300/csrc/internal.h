@@ -32,6 +32,7 @@ struct SweepArgs {
   const float* vtm32;      // [inst * nb] v_b tau_maj in FP32
   const double* wcoef;     // [inst * nb * 6] C_b v_b A / (4 N_w) per wall
   const double* wallT;     // [walls]
+  double* wemit;           // [bc] staged sweep: weight of every thermal emitter (w_max pre-pass)
   const double* wallTf;    // [boundary faces] temperature of every boundary face
   double* R;
   double* W;
@@ -81,6 +82,7 @@ struct Ctx {
   double* d_v = nullptr;
   double* d_wcoef = nullptr;
   double* d_wallT = nullptr;
+  double* d_wemit = nullptr;     // [nb * cells] emitter weights of the current sweep
   double* d_wallTf = nullptr;    // [total_bfaces]
   double* d_srcshift = nullptr;  // null when no source
   double* d_source = nullptr;    // Q (kept for set_field)

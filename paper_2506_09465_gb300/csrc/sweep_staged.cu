@@ -104,11 +104,13 @@ __global__ void group_wmax_kernel(SweepArgs A, unsigned long long* wmax_bits) {
   const InstDesc& in = A.inst[G.inst];
   double m = 0.0;
   if (G.kind == 0) {
-    const double* coef = A.coef + in.bc_off + (long long)G.band * in.ncells;
+    const long long base = in.bc_off + (long long)G.band * in.ncells;
     for (int e = threadIdx.x; e < in.ncells; e += blockDim.x) {
       double Te = A.T[in.cell_off + e];
       if (A.srcshift) Te += A.srcshift[in.cell_off + e];
-      m = fmax(m, fabs(coef[e] * Te));
+      const double w = A.coef[base + e] * Te;
+      A.wemit[base + e] = w;  // the weight of every particle of this emitter
+      m = fmax(m, fabs(w));
     }
   } else {
     const int wl = G.kind - 1;
@@ -176,10 +178,8 @@ __device__ __forceinline__ bool staged_emit(const SweepArgs& A, const StagedArgs
     if (ADJ) {
       w = A.coef[in.bc_off + (long long)b * in.ncells + e];
     } else {
-      double Te = A.T[in.cell_off + e];
-      if (A.srcshift) Te += A.srcshift[in.cell_off + e];
-      w = A.coef[in.bc_off + (long long)b * in.ncells + e] * Te;
-      if (w == 0.0) return false;
+      w = A.wemit[in.bc_off + (long long)b * in.ncells + e];  // from the w_max pre-pass
+      if ((__double_as_longlong(w) << 1) == 0) return false;   // +-0: nothing to trace
     }
     emitter = e;
     st.init(A.seed, in.inst_id, (uint32_t)b, A.epoch, (uint32_t)e, (uint32_t)q);
@@ -329,6 +329,18 @@ __device__ __forceinline__ void tally_k32(float2* p, double x) {
   if (lo != 0.f) atomicAdd(&p->y, lo);
 }
 
+// The candidate estimator W = sum of w tau_maj over candidates (Sec. 3.2): the staged sweep
+// sums w per (band, cell) and multiplies by the instance's tau_maj of the band here.
+__global__ void scale_by_taumaj_kernel(const InstDesc* inst, int n_inst, int nb, const double* taumaj, double* W,
+                                       long long total) {
+  for (long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x; j < total; j += (long long)gridDim.x * blockDim.x) {
+    int k = 0;
+    while (k + 1 < n_inst && inst[k + 1].bc_off <= j) ++k;
+    const int b = (int)((j - inst[k].bc_off) / inst[k].ncells);
+    W[j] *= taumaj[(long long)k * nb + b];
+  }
+}
+
 // FP64 value of compensated tallies: dst = hi + lo (add = 0) or dst += hi + lo (add = 1).
 __global__ void k32_finalize_kernel(const float2* src, double* dst, long long n, int add) {
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
@@ -382,7 +394,7 @@ __global__ void __launch_bounds__(STAGED_NT, 1) sweep_staged_kernel(SweepArgs A,
     const double qinv = wmax > 0.0 ? WIN_SCALE / wmax : 0.0;
     const unsigned pend = (unsigned)S.inst_end[k];
     unsigned rbeg = 0, rend = 0;  // this warp's private particle range
-    double w = 0.0, wt = 0.0;
+    double w = 0.0;
     unsigned qwx = 0;             // signed x-face contribution in units of q (two's complement)
     int band = 0;
     long long bcbase = 0;
@@ -428,7 +440,6 @@ __global__ void __launch_bounds__(STAGED_NT, 1) sweep_staged_kernel(SweepArgs A,
             cnt.v[CNT_FLIGHTS] += 1;
             const int qw = __double2int_rn(w * qinv);
             qwx = (unsigned)(f.s0 > 0 ? qw : -qw);
-            wt = w * A.taumaj[(long long)k * A.nb + band];
             vtm = A.vtm32[(long long)k * A.nb + band];
             bcbase = bc_off + (long long)band * ncells;
           }
@@ -457,8 +468,9 @@ __global__ void __launch_bounds__(STAGED_NT, 1) sweep_staged_kernel(SweepArgs A,
           if (DIM >= 2) cell += sy_cell * clampi(f.i1 + f.s1 * faces_before(f.D, f.t1, f.d1), n1);
           if (DIM == 3) cell += sz_cell * clampi(f.i2 + f.s2 * faces_before(f.D, f.t2, f.d2), n2);
           const long long ci = bcbase + cell;
-          if (!ADJ && K32 && S.W32) tally_k32(&S.W32[ci], wt);
-          else if (!ADJ && !K32 && A.W) atomicAdd(&A.W[ci], wt);
+          // W collects w here; the sweep scales it by tau_maj afterwards (scale_by_taumaj)
+          if (!ADJ && K32 && S.W32) tally_k32(&S.W32[ci], w);
+          else if (!ADJ && !K32 && A.W) atomicAdd(&A.W[ci], w);
           if (word_uniform<float>(ub) < A.ratio32[ci]) {
             cnt.v[CNT_REAL] += 1;
             if (ADJ) {
@@ -805,6 +817,11 @@ cudaError_t launch_sweep_staged(const Ctx* c, const SweepArgs& a, cudaStream_t s
     }
   }
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  if (a.W) {
+    scale_by_taumaj_kernel<<<c->sm_count * 4, 256, 0, s>>>(c->d_inst, c->n_inst, c->nb, c->d_taumaj, a.W,
+                                                          (long long)c->nb * c->total_cells);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  }
   if (a.F) {
     boundary_emission_kernel<<<dim3(8, 2 * c->dim, c->n_inst), 256, 0, s>>>(c->d_inst, c->dim, c->d_wall_unit,
                                                                            c->d_wallTf, a.F);
