@@ -40,6 +40,8 @@ struct PArgs {
   const double* srcshift;
   const double* coef;          // [bc] C_b V / (tau N_b)
   const double* ratio64;       // [bc] tau_maj / tau
+  const float* ratio32;        // [bc] tau_maj / tau in FP32
+  const float* vtm32;          // [inst * nb] v_b tau_maj in FP32
   const double* taumaj;        // [inst * nb]
   const double* v;             // [nb]
   const double* wcoef;         // [inst * nb * 6] C_b v_b A / (4 N_w)
@@ -73,6 +75,48 @@ __device__ __forceinline__ void put(V (&v)[3], int i, V x) {
   v[1] = i == 1 ? x : v[1];
   v[2] = i == 2 ? x : v[2];
 }
+
+// Tracking-precision values without FP64-pipe conversions in the FP32 variant: the FP32
+// cell sizes of the descriptor, integers below 2^23 turned into floats by placing them in
+// the mantissa of 2^23, floor of a float in (-2^23, 2^23) by a round-down add of 2^23 (the
+// FP32 variant's conversions otherwise issue on the slow FP64 pipe).
+template <typename Real>
+__device__ __forceinline__ Real cell_h(const InstDesc& in, int a);
+template <>
+__device__ __forceinline__ double cell_h<double>(const InstDesc& in, int a) { return in.h[a]; }
+template <>
+__device__ __forceinline__ float cell_h<float>(const InstDesc& in, int a) { return in.hf[a]; }
+
+template <typename Real>
+__device__ __forceinline__ Real int_to_real(int i) { return (Real)i; }
+template <>
+__device__ __forceinline__ float int_to_real<float>(int i) {
+  return __int_as_float(0x4B000000 | i) - 8388608.0f;  // exact for 0 <= i < 2^23
+}
+
+// max(floor(y), 0)
+template <typename Real>
+__device__ __forceinline__ int floor_nonneg(Real y) { return max((int)floor(y), 0); }
+template <>
+__device__ __forceinline__ int floor_nonneg<float>(float y) {
+  return max(__float_as_int(__fadd_rd(y, 8388608.0f)) - 0x4B000000, 0);
+}
+
+template <typename Real>
+__device__ __forceinline__ Real mean_path(const PArgs& A, int k, int b, double tm);
+template <>
+__device__ __forceinline__ double mean_path<double>(const PArgs& A, int, int b, double tm) { return A.v[b] * tm; }
+template <>
+__device__ __forceinline__ float mean_path<float>(const PArgs& A, int k, int b, double) {
+  return A.vtm32[(long long)k * A.nb + b];
+}
+
+template <typename Real>
+__device__ __forceinline__ Real accept_ratio(const PArgs& A, long long jb);
+template <>
+__device__ __forceinline__ double accept_ratio<double>(const PArgs& A, long long jb) { return A.ratio64[jb]; }
+template <>
+__device__ __forceinline__ float accept_ratio<float>(const PArgs& A, long long jb) { return A.ratio32[jb]; }
 
 // Wall power is accumulated per block in shared memory and flushed once: every absorption
 // adding to one of 2 dim addresses per instance in global memory would serialise at the L2.
@@ -121,20 +165,20 @@ __global__ void __launch_bounds__(256, 4) persistent_step_kernel(PArgs A) {
       if (h < in.ncells) {
         // re-emission in the cell of the real collision (Sec. 3.2 step (2))
         const int ci[3] = {h % n0, (h / n0) % n1, h / (n0 * n1)};
-        const Real hx = (Real)in.h[0], hy = (Real)in.h[1], hz = (Real)in.h[2];
+        const Real hx = cell_h<Real>(in, 0), hy = cell_h<Real>(in, 1), hz = cell_h<Real>(in, 2);
         Real u_mu, u_phi = (Real)0.5;
         if (DIM == 1) {
-          x[0] = ((Real)ci[0] + word_uniform<Real>(st.buf.x)) * hx;
+          x[0] = (int_to_real<Real>(ci[0]) + word_uniform<Real>(st.buf.x)) * hx;
           u_mu = word_uniform<Real>(st.buf.y);
         } else if (DIM == 2) {
-          x[0] = ((Real)ci[0] + word_uniform<Real>(st.buf.x)) * hx;
-          x[1] = ((Real)ci[1] + word_uniform<Real>(st.buf.y)) * hy;
+          x[0] = (int_to_real<Real>(ci[0]) + word_uniform<Real>(st.buf.x)) * hx;
+          x[1] = (int_to_real<Real>(ci[1]) + word_uniform<Real>(st.buf.y)) * hy;
           u_mu = word_uniform<Real>(st.buf.z);
           u_phi = word_uniform<Real>(st.buf.w);
         } else {
-          x[0] = ((Real)ci[0] + word_uniform<Real>(st.buf.x)) * hx;
-          x[1] = ((Real)ci[1] + word_uniform<Real>(st.buf.y)) * hy;
-          x[2] = ((Real)ci[2] + word_uniform<Real>(st.buf.z)) * hz;
+          x[0] = (int_to_real<Real>(ci[0]) + word_uniform<Real>(st.buf.x)) * hx;
+          x[1] = (int_to_real<Real>(ci[1]) + word_uniform<Real>(st.buf.y)) * hy;
+          x[2] = (int_to_real<Real>(ci[2]) + word_uniform<Real>(st.buf.z)) * hz;
           u_mu = word_uniform<Real>(st.buf.w);
           st.load_block(1);
           u_phi = word_uniform<Real>(st.buf.x);
@@ -166,17 +210,17 @@ __global__ void __launch_bounds__(256, 4) persistent_step_kernel(PArgs A) {
           u_n = word_uniform<Real>(st.buf.x);
         } else if (DIM == 2) {
           const int t = (o1 < 2) ? o1 : o2;
-          put(x, t, ((Real)pick(f, t) + word_uniform<Real>(st.buf.x)) * (Real)in.h[t]);
+          put(x, t, (int_to_real<Real>(pick(f, t)) + word_uniform<Real>(st.buf.x)) * cell_h<Real>(in, t));
           u_n = word_uniform<Real>(st.buf.y);
           u_phi = word_uniform<Real>(st.buf.z);
         } else {
           const int t0 = o1 < o2 ? o1 : o2, t1 = o1 < o2 ? o2 : o1;
-          put(x, t0, ((Real)pick(f, t0) + word_uniform<Real>(st.buf.x)) * (Real)in.h[t0]);
-          put(x, t1, ((Real)pick(f, t1) + word_uniform<Real>(st.buf.y)) * (Real)in.h[t1]);
+          put(x, t0, (int_to_real<Real>(pick(f, t0)) + word_uniform<Real>(st.buf.x)) * cell_h<Real>(in, t0));
+          put(x, t1, (int_to_real<Real>(pick(f, t1)) + word_uniform<Real>(st.buf.y)) * cell_h<Real>(in, t1));
           u_n = word_uniform<Real>(st.buf.z);
           u_phi = word_uniform<Real>(st.buf.w);
         }
-        put(x, a, (Real)pick(f, a) * (Real)in.h[a]);
+        put(x, a, int_to_real<Real>(pick(f, a)) * cell_h<Real>(in, a));
         const Real mn = sqrt(u_n);
         put(s, a, side ? -mn : mn);
         if (DIM >= 2) {
@@ -197,13 +241,13 @@ __global__ void __launch_bounds__(256, 4) persistent_step_kernel(PArgs A) {
     uint32_t ua, ub;
     st.next_pair(ua, ub);
     const double tm = A.taumaj[(long long)k * A.nb + b];
-    const Real ell = -RealTraits<Real>::log_(word_uniform<Real>(ua)) * (Real)(A.v[b] * tm);
+    const Real ell = -RealTraits<Real>::log_(word_uniform<Real>(ua)) * mean_path<Real>(A, k, b, tm);
     Real tw = RealTraits<Real>::inf();
     int wl = -1;
 #pragma unroll
     for (int a = 0; a < DIM; ++a) {
       if (s[a] == (Real)0) continue;
-      const Real L = (Real)(in.h[a] * in.n[a]);
+      const Real L = cell_h<Real>(in, a) * int_to_real<Real>(in.n[a]);
       const Real t = s[a] > (Real)0 ? (L - x[a]) / s[a] : -x[a] / s[a];
       if (t < tw) {
         tw = t;
@@ -218,8 +262,8 @@ __global__ void __launch_bounds__(256, 4) persistent_step_kernel(PArgs A) {
       exit_w = w;
       const int a = wl >> 1, o1 = (a + 1) % 3, o2 = (a + 2) % 3;
       int j1 = 0, j2 = 0;
-      if (o1 < DIM) j1 = min(max((int)floor((pick(x, o1) + tw * pick(s, o1)) / (Real)in.h[o1]), 0), in.n[o1] - 1);
-      if (o2 < DIM) j2 = min(max((int)floor((pick(x, o2) + tw * pick(s, o2)) / (Real)in.h[o2]), 0), in.n[o2] - 1);
+      if (o1 < DIM) j1 = min(floor_nonneg<Real>((pick(x, o1) + tw * pick(s, o1)) / cell_h<Real>(in, o1)), in.n[o1] - 1);
+      if (o2 < DIM) j2 = min(floor_nonneg<Real>((pick(x, o2) + tw * pick(s, o2)) / cell_h<Real>(in, o2)), in.n[o2] - 1);
       h = in.ncells + in.wface_off[wl] + j2 * in.n[o1] + j1;
       atomicAdd(&A.n_new[A.home_off[k] + (long long)b * nh + h], 1u);
     } else {
@@ -227,14 +271,14 @@ __global__ void __launch_bounds__(256, 4) persistent_step_kernel(PArgs A) {
 #pragma unroll
       for (int a = 0; a < DIM; ++a) {
         x[a] += ell * s[a];
-        ci[a] = min(max((int)floor(x[a] / (Real)in.h[a]), 0), in.n[a] - 1);
+        ci[a] = min(floor_nonneg<Real>(x[a] / cell_h<Real>(in, a)), in.n[a] - 1);
       }
       const int c = ci[0] + n0 * (ci[1] + n1 * ci[2]);
       // candidate (steps (4)-(5)): W from every candidate, R and the count from real ones
       c_cand += 1;
       const long long jb = in.bc_off + (long long)b * in.ncells + c;
       atomicAdd(&A.W[jb], w * tm);
-      if (word_uniform<Real>(ub) < (Real)A.ratio64[jb]) {
+      if (word_uniform<Real>(ub) < accept_ratio<Real>(A, jb)) {
         c_real += 1;
         atomicAdd(&A.R[jb], w);
         h = c;
@@ -335,6 +379,8 @@ cudaError_t launch_persistent_step(const Ctx* c, const double* T, unsigned it, d
   a.srcshift = c->d_srcshift;
   a.coef = c->d_coef;
   a.ratio64 = c->d_ratio64;
+  a.ratio32 = c->d_ratio32;
+  a.vtm32 = c->d_vtm32;
   a.taumaj = c->d_taumaj;
   a.v = c->d_v;
   a.wcoef = c->d_wcoef;
