@@ -110,7 +110,7 @@ typedef struct {
 
 /* Fills *o with defaults: FP32 tracking, staged tallies, frozen draws, Newton on,
  * persistent schedule, 1024 particles per cell and per wall face, seed 0,
- * cg_rtol 1e-4 (the correction is an inexact Newton step: its tolerance changes the
+ * cg_rtol 1e-3 (the correction is an inexact Newton step: its tolerance changes the
  * iteration count, not the fixed point), cg_maxit 5000, step budget 2^24. */
 void iugkp_default_options(iugkp_options *o);
 

@@ -275,7 +275,7 @@ void iugkp_default_options(iugkp_options* o) {
   o->seed = 0;
   o->epoch0 = 0;
   o->instance_base = 0;
-  o->cg_rtol = 1e-4;
+  o->cg_rtol = 1e-3;
   o->cg_maxit = 5000;
   o->step_budget = 1ll << 24;
   o->block_threads = 0;
