@@ -110,7 +110,7 @@ void free_all(Ctx* c) {
                   c->d_group_mag, c->d_mag, c->d_wall_unit, c->d_all_beg, c->d_all_end, c->d_all_cost_prefix,
                   c->d_all_group_mag, c->d_R32, c->d_W32, c->d_F32, c->d_m2, c->d_wallTf,
                   c->d_pslot_off, c->d_phome_off, c->d_pnband, c->d_pnwall, c->d_px, c->d_pband, c->d_phome,
-                  c->d_pdue, c->d_pcount, c->d_phome_w, c->d_wemit};
+                  c->d_pdue, c->d_pcount, c->d_phome_w, c->d_wemit, c->d_DY, c->d_EY, c->d_GX, c->d_Fd};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (c->h_pinned) cudaFreeHost(c->h_pinned);
@@ -235,12 +235,19 @@ iugkp_status rebuild_forward_groups(Ctx* c) {
   double tot = 0.0;
   staged_tables(c, c->h_groups_fwd, beg, end, prefix, tot, gmag);
   c->cost_total = tot;
-  // x-face window: all x-faces when they fit, else a centred run of them (the rest take
-  // global atomics)
+  // Shared-memory face window. 2D instances whose faces all fit take every face (two-group
+  // tallies); otherwise the window holds all x-faces when they fit, else a centred run of
+  // them (the rest take global atomics).
   std::vector<int2> window(c->n_inst);
+  c->any_two_group = false;
   for (int k = 0; k < c->n_inst; ++k) {
     const InstDesc& in = c->h_inst[k];
     const long long X = (long long)(in.n[0] + 1) * in.n[1] * in.n[2];
+    if (c->dim == 2 && in.nfaces <= c->staged_cap) {
+      window[k] = make_int2(0, (int)in.nfaces);
+      c->any_two_group = true;
+      continue;
+    }
     const long long len = std::min<long long>(X, c->staged_cap);
     window[k] = make_int2((int)((X - len) / 2), (int)len);
   }
@@ -614,7 +621,8 @@ iugkp_status iugkp_create_batch(int n, const iugkp_grid* g, const double* const*
   if ((s = set_source(c, Qv, m)) != IUGKP_OK) return bail(s);
   {
     long long maxX = 0;
-    for (const InstDesc& in : c->h_inst) maxX = std::max(maxX, (long long)(in.n[0] + 1) * in.n[1] * in.n[2]);
+    for (const InstDesc& in : c->h_inst)
+      maxX = std::max(maxX, c->dim == 2 ? in.nfaces : (long long)(in.n[0] + 1) * in.n[1] * in.n[2]);
     const long long budget = ((long long)c->smem_optin - 4096) / (long long)sizeof(unsigned);
     c->staged_cap = (int)std::max<long long>(1, std::min(maxX, budget));
   }
@@ -655,6 +663,12 @@ iugkp_status iugkp_create_batch(int n, const iugkp_grid* g, const double* const*
   if ((s = dalloc(c, &c->d_W, (size_t)nb * cell_off)) != IUGKP_OK) return bail(s);
   if ((s = dalloc(c, &c->d_F, face_off)) != IUGKP_OK) return bail(s);
   if ((s = dalloc(c, &c->d_wemit, (size_t)nb * cell_off)) != IUGKP_OK) return bail(s);
+  if (c->dim == 2) {
+    if ((s = dalloc(c, &c->d_DY, cell_off)) != IUGKP_OK) return bail(s);
+    if ((s = dalloc(c, &c->d_EY, (size_t)c->total_bfaces)) != IUGKP_OK) return bail(s);
+    if ((s = dalloc(c, &c->d_GX, (size_t)c->total_bfaces)) != IUGKP_OK) return bail(s);
+    if ((s = dalloc(c, &c->d_Fd, face_off)) != IUGKP_OK) return bail(s);
+  }
   if ((s = dalloc(c, &c->d_wall, c->total_walls)) != IUGKP_OK) return bail(s);
   if ((s = dalloc(c, &c->d_red, 1024)) != IUGKP_OK) return bail(s);
   if ((s = dalloc(c, &c->d_counters, CNT_N)) != IUGKP_OK) return bail(s);

@@ -83,6 +83,12 @@ struct Ctx {
   double* d_wcoef = nullptr;
   double* d_wallT = nullptr;
   double* d_wemit = nullptr;     // [nb * cells] emitter weights of the current sweep
+  // two-group face tallies of the staged sweep (2D): group balances and derived faces
+  double* d_DY = nullptr;        // [cells]
+  double* d_EY = nullptr;        // [total_bfaces]
+  double* d_GX = nullptr;        // [total_bfaces]
+  double* d_Fd = nullptr;        // [total_faces] faces derived from the group balances
+  bool any_two_group = false;    // some instance of the context uses the two-group tallies
   double* d_wallTf = nullptr;    // [total_bfaces]
   double* d_srcshift = nullptr;  // null when no source
   double* d_source = nullptr;    // Q (kept for set_field)

@@ -32,6 +32,15 @@ struct StagedArgs {
   float2* R32;                    // [nb * total_cells]
   float2* W32;                    // [nb * total_cells] or null
   float2* F32;                    // [total_faces] face tallies that miss the window, or null
+  // Two-group face tallies (2D instances whose faces all fit the window): a particle whose
+  // path per cell along x is at least that along y (d_x >= d_y) is in the x-group and
+  // tallies the faces normal to x it crosses; the others (y-group) tally the faces normal
+  // to y. The untallied faces of each group follow from that group's own power balance.
+  double* DY;                     // [total_cells] y-group: absorbed minus emitted power per cell
+  double* EY;                     // [total_bfaces] y-group wall emission per boundary face (signed
+                                  // flux: + on the low walls, - on the high walls)
+  double* GX;                     // [total_bfaces] exits of the x-group through the low y-wall and
+                                  // of the y-group through the low x-wall (signed flux)
 };
 
 }  // namespace iugkp

@@ -149,7 +149,7 @@ struct EmitCache {
 template <int DIM, bool ADJ>
 __device__ __forceinline__ bool staged_emit(const SweepArgs& A, const StagedArgs& S, unsigned pid, bool useF,
                                             double& w, int& band, PW& f, Stream& st, uint32_t& ub, EmitCache& ec,
-                                            const InstDesc& in, int k, int& emitter) {
+                                            const InstDesc& in, int k, int& emitter, bool two) {
   if (pid < ec.g_first || pid >= ec.g_end) {
     const int gi = find_group(A.groups, A.n_groups, (long long)pid);
     const Group G = A.groups[gi];
@@ -299,6 +299,15 @@ __device__ __forceinline__ bool staged_emit(const SweepArgs& A, const StagedArgs
     axis_init(sz, xi2, in.hf[2], f.t2, f.d2, f.s2);
     f.tex = fminf(f.tex, axis_exit(f.i2, f.s2, n2, f.t2, f.d2));
   }
+  if (!ADJ && DIM == 2 && two && f.d0 < f.d1) {
+    // y-group: its emission enters its own power balance (cell) or boundary flux (face)
+    if (kind == 0) {
+      atomicAdd(&S.DY[in.cell_off + e], -w);
+    } else {
+      const int wl = kind - 1;
+      atomicAdd(&S.EY[in.bface_off + in.wface_off[wl] + e], (wl & 1) ? -w : w);
+    }
+  }
   uint32_t ua;
   st.next_pair(ua, ub);
   f.D = -__logf(word_uniform<float>(ua)) * A.vtm32[(long long)k * A.nb + b];
@@ -388,6 +397,8 @@ __global__ void __launch_bounds__(STAGED_NT, 1) sweep_staged_kernel(SweepArgs A,
     const int wbase = wd.x;
     const unsigned wlen = (unsigned)wd.y;
     const bool wfull = wbase == 0 && (long long)wlen == (long long)(n0 + 1) * n1 * n2;
+    // 2D instance whose faces all fit the window: two-group tallies (see StagedArgs)
+    const bool two = DIM == 2 && useF && wbase == 0 && (long long)wlen == in.nfaces;
     for (unsigned i = threadIdx.x; i < wlen; i += STAGED_NT) win[i] = WIN_BIAS;
     __syncthreads();
     const double wmax = S.wmax[k];
@@ -430,7 +441,7 @@ __global__ void __launch_bounds__(STAGED_NT, 1) sweep_staged_kernel(SweepArgs A,
         const unsigned rank = __popc(dead & lt_mask);
         const unsigned take = min((unsigned)__popc(dead), rend - rbeg);
         if (!alive && rank < take) {
-          alive = staged_emit<DIM, ADJ>(A, S, rbeg + rank, useF, w, band, f, st, ub, ec, in, k, emitter);
+          alive = staged_emit<DIM, ADJ>(A, S, rbeg + rank, useF, w, band, f, st, ub, ec, in, k, emitter, two);
           if (ADJ && alive && emitter < 0 && emitter != acc_slot) {
             if (acc != 0.0) atomicAdd(&A.adj_wall[in.wall_off + (-1 - acc_slot)], acc);
             acc = 0.0;
@@ -439,7 +450,8 @@ __global__ void __launch_bounds__(STAGED_NT, 1) sweep_staged_kernel(SweepArgs A,
           if (alive) {
             cnt.v[CNT_FLIGHTS] += 1;
             const int qw = __double2int_rn(w * qinv);
-            qwx = (unsigned)(f.s0 > 0 ? qw : -qw);
+            // signed along the axis whose faces the particle tallies
+            qwx = (unsigned)(((two && f.d0 < f.d1) ? f.s1 : f.s0) > 0 ? qw : -qw);
             vtm = A.vtm32[(long long)k * A.nb + band];
             bcbase = bc_off + (long long)band * ncells;
           }
@@ -483,6 +495,7 @@ __global__ void __launch_bounds__(STAGED_NT, 1) sweep_staged_kernel(SweepArgs A,
             } else {
               atomicAdd(&A.R[ci], w);
             }
+            if (!ADJ && two && f.d0 < f.d1) atomicAdd(&S.DY[in.cell_off + cell], w);
             ended = true;
             break;
           }
@@ -513,7 +526,51 @@ __global__ void __launch_bounds__(STAGED_NT, 1) sweep_staged_kernel(SweepArgs A,
             c2 = ex == 2 ? m2 - 1 : min(faces_before(L, f.t2, f.d2), m2 - 1);
           }
           cnt.v[CNT_CROSSINGS] += c0 + c1 + c2;
-          if (useF) {
+          if (DIM == 2 && (two || wfull)) {
+            // Face items k = 0 .. kend-1 along the tallied axis p (the other axis: q). Item k
+            // is the face index a0 + k sp + sq min(ceil(u0 + k r), lim): the k-th face normal
+            // to p, in the row (or column) given by the faces normal to q crossed before it,
+            // ceil(u0 + k r) with u0 = (t_p - t_q) / d_q and r = d_p / d_q, at most lim.
+            const bool yg = two && f.d0 < f.d1;
+            int a0, sp, sq, lim;
+            float u0, r;
+            if (!yg) {
+              // exit through the low y-wall: the one face normal to y this group tallies
+              if (ex == 1 && f.s1 < 0) {
+                const int col = f.i0 + f.s0 * c0;
+                if (two) atomicAdd(&S.GX[in.bface_off + in.wface_off[2] + col], -w);
+                else if (K32) tally_k32(&S.F32[face_off + fax1 + col], -w);
+                else atomicAdd(&A.F[face_off + fax1 + col], -w);
+              }
+              kend = c0 + (ex == 0 ? 1 : 0);
+              const bool flat = !(f.d1 < INFINITY);
+              u0 = flat ? -1.f : __fdividef(f.t0 - f.t1, f.d1);
+              r = flat ? 0.f : __fdividef(f.d0, f.d1);
+              lim = m1 - 1;
+              a0 = (f.s0 > 0 ? f.i0 + 1 : f.i0) + sy_xf * f.i1;
+              sp = f.s0;
+              sq = f.s1 * sy_xf;
+            } else {
+              // exit through the low x-wall: the one face normal to x this group tallies
+              if (ex == 0 && f.s0 < 0) atomicAdd(&S.GX[in.bface_off + in.wface_off[0] + (f.i1 + f.s1 * c1)], -w);
+              kend = c1 + (ex == 1 ? 1 : 0);
+              u0 = __fdividef(f.t1 - f.t0, f.d0);
+              r = __fdividef(f.d1, f.d0);
+              lim = m0 - 1;
+              a0 = (int)fax1 + f.i0 + n0 * (f.s1 > 0 ? f.i1 + 1 : f.i1);
+              sp = f.s1 * n0;
+              sq = f.s0;
+            }
+            f.i0 = a0;
+            f.s0 = sp;
+            f.s1 = sq;
+            f.i2 = lim;
+            f.D = u0;
+            f.tex = r;
+            kcur = 0;
+            tally = kend > 0;
+            alive = tally;
+          } else if (useF) {
             // faces normal to the last axis: only the low boundary is tallied (the rest
             // follow from conservation)
             if (DIM == 2 && ex == 1 && f.s1 < 0) {
@@ -559,14 +616,14 @@ __global__ void __launch_bounds__(STAGED_NT, 1) sweep_staged_kernel(SweepArgs A,
           const int carry = ((int)qwx >> 31) + (old + qwx < old ? 1 : 0);
           if (carry) atomicAdd(&A.F[face_off + xface], (double)carry * S.wmax[k] * WIN_CARRY);
         };
-        if (DIM == 2 && wfull) {
-          // every x-face of the instance is in the window; rows need only the upper bound
-          // f.i2 = faces before the y-wall (the lower bound holds by construction)
+        if (DIM == 2 && (two || wfull)) {
+          // every face of the tallied axis is in the window at its instance index; the count
+          // along the other axis needs only the upper bound (the lower one holds by
+          // construction)
 #pragma unroll 1
           for (; kcur < kstop; ++kcur, fk += 1.f) {
-            const int row = f.i1 + f.s1 * min(ceil_count(fmaf(fk, f.tex, f.D)), f.i2);
-            const int xface = (f.s0 > 0 ? f.i0 + 1 + kcur : f.i0 - kcur) + sy_xf * row;
-            window_add(xface, (unsigned)xface);
+            const int face = f.i0 + kcur * f.s0 + f.s1 * min(ceil_count(fmaf(fk, f.tex, f.D)), f.i2);
+            window_add(face, (unsigned)face);
           }
         } else {
 #pragma unroll 1
@@ -648,14 +705,21 @@ __device__ __forceinline__ double column_step(const InstDesc& in, int nb, const 
 // segment's running values.
 constexpr int DERIVE_SEG = 8;
 
+// A 2D instance whose faces all sit in the staged window uses the two-group tallies.
+__device__ __forceinline__ bool two_group(const InstDesc& in, const int2* window, int k) {
+  return in.dim == 2 && window[k].x == 0 && (long long)window[k].y == in.nfaces;
+}
+
 template <int DIM>
 __global__ void __launch_bounds__(32 * DERIVE_SEG) derive_last_axis_kernel(const InstDesc* inst, int n_inst, int nb,
-                                                                         const double* T, const double* srcshift,
-                                                                         const double* Vm, const double* R, double* F) {
+                                                                         const int2* window, const double* T,
+                                                                         const double* srcshift, const double* Vm,
+                                                                         const double* R, double* F) {
   __shared__ double segsum[DERIVE_SEG][32];
   const int k = blockIdx.y;
   if (k >= n_inst) return;
   const InstDesc& in = inst[k];
+  if (two_group(in, window, k)) return;
   const int n0 = in.n[0], n1 = in.n[1], n2 = in.n[2];
   const int nlast = DIM == 2 ? n1 : n2;
   const int ncol = in.ncells / nlast;
@@ -714,18 +778,134 @@ __device__ __forceinline__ int wall_faces(const InstDesc& in, int a) {
 // Power entering through every boundary face from its wall's emission (N_w particles of
 // weight C_b v_b A T_w / (4 N_w) per face and band), except on the high side of the
 // derived axis (that axis is rebuilt from conservation). Grid: (faces, walls, instances).
-__global__ void boundary_emission_kernel(const InstDesc* inst, int dim, const double* wall_unit, const double* wallTf,
-                                         double* F) {
+__global__ void boundary_emission_kernel(const InstDesc* inst, int dim, const int2* window, const double* wall_unit,
+                                         const double* wallTf, double* F) {
   const int k = blockIdx.z, wl = blockIdx.y;
   const int a = wl >> 1, side = wl & 1;
   if (dim >= 2 && a == dim - 1 && side == 1) return;
   const InstDesc& in = inst[k];
+  if (two_group(in, window, k)) return;  // added with the group balances
   const double u = wall_unit[k * 6 + wl];
   const double* tf = wallTf + in.bface_off + in.wface_off[wl];
   const int nf = wall_faces(in, a);
   for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < nf; j += gridDim.x * blockDim.x) {
     const double e = u * tf[j];
     if (e != 0.0) F[in.face_off + wall_face(in, a, side, j)] += side ? -e : e;
+  }
+}
+
+// Two-group instances (2D): the faces each group did not tally follow from that group's
+// power balance in every cell. x-group, column i, faces normal to y from the bottom up:
+//   G[j+1] = G[j] + (X[i,j] - X[i+1,j]) - ((R - S)_c - D_y,c),
+// starting from the x-group's net flux through the bottom face (its exits there plus its
+// share of the wall's emission, the whole emission minus the y-group's); X are the x-group's
+// tallied faces plus its share of the emission on the x-walls. y-group, row j, faces
+// normal to x from the left:
+//   H[i+1] = H[i] + (Y[i,j] - Y[i,j+1]) - D_y,c,
+// starting from its exits through the left wall and its emission there; Y are its tallied
+// faces plus its emission on the y-walls. One warp per line, prefix sums over chunks of 32
+// cells in a fixed order; results go to Fd (F is only read).
+__global__ void __launch_bounds__(256) derive_two_group_kernel(const InstDesc* inst, int nb, const int2* window,
+                                                               const double* T, const double* srcshift,
+                                                               const double* Vm, const double* R,
+                                                               const double* wall_unit, const double* wallTf,
+                                                               const double* DY, const double* EY, const double* GX,
+                                                               const double* F, double* Fd) {
+  const int k = blockIdx.y;
+  const InstDesc& in = inst[k];
+  if (!two_group(in, window, k)) return;
+  const int n0 = in.n[0], n1 = in.n[1];
+  const int line = blockIdx.x * 8 + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+  if (line >= n0 + n1) return;
+  const double* Fi = F + in.face_off;
+  double* Fo = Fd + in.face_off;
+  const long long fax1 = in.fax_off[1];
+  const double* ey = EY + in.bface_off;
+  const double* gx = GX + in.bface_off;
+  const double* tf = wallTf + in.bface_off;
+  const double* dy = DY + in.cell_off;
+  // signed flux of the whole emission of wall wl through its face j
+  auto etot = [&](int wl, int j) {
+    const double e = wall_unit[k * 6 + wl] * tf[in.wface_off[wl] + j];
+    return (wl & 1) ? -e : e;
+  };
+  if (line < n0) {
+    const int i = line;
+    double acc = gx[in.wface_off[2] + i] + etot(2, i) - ey[in.wface_off[2] + i];
+    if (lane == 0) Fo[fax1 + i] = acc;
+    for (int j0 = 0; j0 < n1; j0 += 32) {
+      const int j = j0 + lane;
+      double v = 0.0;
+      if (j < n1) {
+        const long long c = i + (long long)n0 * j;
+        const long long fl = c + j;  // x-face (i, j)
+        double left = Fi[fl], right = Fi[fl + 1];
+        if (i == 0) left += etot(0, j) - ey[in.wface_off[0] + j];
+        if (i == n0 - 1) right += etot(1, j) - ey[in.wface_off[1] + j];
+        double rr = 0.0;
+        for (int b = 0; b < nb; ++b) rr += R[in.bc_off + (long long)b * in.ncells + c];
+        double te = T[in.cell_off + c];
+        if (srcshift) te += srcshift[in.cell_off + c];
+        v = (left - right) - (rr - Vm[in.cell_off + c] * te - dy[c]);
+      }
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const double t = __shfl_up_sync(0xffffffffu, v, o);
+        if (lane >= o) v += t;
+      }
+      if (j < n1) Fo[fax1 + i + (long long)n0 * (j + 1)] = acc + v;
+      acc += __shfl_sync(0xffffffffu, v, 31);
+    }
+  } else {
+    const int j = line - n0;
+    double acc = gx[in.wface_off[0] + j] + ey[in.wface_off[0] + j];
+    if (lane == 0) Fo[(long long)(n0 + 1) * j] = acc;
+    for (int ib = 0; ib < n0; ib += 32) {
+      const int i = ib + lane;
+      double v = 0.0;
+      if (i < n0) {
+        const long long c = i + (long long)n0 * j;
+        double bot = Fi[fax1 + c], top = Fi[fax1 + c + n0];
+        if (j == 0) bot += ey[in.wface_off[2] + i];
+        if (j == n1 - 1) top += ey[in.wface_off[3] + i];
+        v = (bot - top) - dy[c];
+      }
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const double t = __shfl_up_sync(0xffffffffu, v, o);
+        if (lane >= o) v += t;
+      }
+      if (i < n0) Fo[(long long)(n0 + 1) * j + i + 1] = acc + v;
+      acc += __shfl_sync(0xffffffffu, v, 31);
+    }
+  }
+}
+
+// Two-group instances: every face = its tallied group's sum + the other group's derived
+// flux + the tallied group's share of the wall emission on boundary faces.
+__global__ void assemble_two_group_kernel(const InstDesc* inst, const int2* window, const double* wall_unit,
+                                          const double* wallTf, const double* EY, const double* Fd, double* F) {
+  const int k = blockIdx.y;
+  const InstDesc& in = inst[k];
+  if (!two_group(in, window, k)) return;
+  const int n0 = in.n[0], n1 = in.n[1];
+  const long long X = in.fax_off[1];
+  const double* ey = EY + in.bface_off;
+  const double* tf = wallTf + in.bface_off;
+  for (long long f = blockIdx.x * (long long)blockDim.x + threadIdx.x; f < in.nfaces;
+       f += (long long)gridDim.x * blockDim.x) {
+    double add = Fd[in.face_off + f];
+    if (f < X) {
+      const int i = (int)(f % (n0 + 1)), j = (int)(f / (n0 + 1));
+      if (i == 0) add += wall_unit[k * 6 + 0] * tf[in.wface_off[0] + j] - ey[in.wface_off[0] + j];
+      if (i == n0) add += -wall_unit[k * 6 + 1] * tf[in.wface_off[1] + j] - ey[in.wface_off[1] + j];
+    } else {
+      const long long g = f - X;
+      const int i = (int)(g % n0), jf = (int)(g / n0);
+      if (jf == 0) add += ey[in.wface_off[2] + i];
+      if (jf == n1) add += ey[in.wface_off[3] + i];
+    }
+    F[in.face_off + f] += add;
   }
 }
 
@@ -789,6 +969,15 @@ cudaError_t launch_sweep_staged(const Ctx* c, const SweepArgs& a, cudaStream_t s
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   const size_t smem = (size_t)c->staged_cap * sizeof(unsigned);
   const int blocks = c->sm_count * c->staged_blocks_per_sm;
+  const bool two = a.F && c->dim == 2 && c->any_two_group;
+  S.DY = c->d_DY;
+  S.EY = c->d_EY;
+  S.GX = c->d_GX;
+  if (two) {
+    if ((e = cudaMemsetAsync(c->d_DY, 0, (size_t)c->total_cells * sizeof(double), s)) != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(c->d_EY, 0, (size_t)c->total_bfaces * sizeof(double), s)) != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(c->d_GX, 0, (size_t)c->total_bfaces * sizeof(double), s)) != cudaSuccess) return e;
+  }
   const bool k32 = c->opt.tally == IUGKP_TALLY_STAGED_K32;
   S.R32 = k32 ? c->d_R32 : nullptr;
   S.W32 = k32 && a.W ? c->d_W32 : nullptr;
@@ -823,8 +1012,8 @@ cudaError_t launch_sweep_staged(const Ctx* c, const SweepArgs& a, cudaStream_t s
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
   if (a.F) {
-    boundary_emission_kernel<<<dim3(8, 2 * c->dim, c->n_inst), 256, 0, s>>>(c->d_inst, c->dim, c->d_wall_unit,
-                                                                           c->d_wallTf, a.F);
+    boundary_emission_kernel<<<dim3(8, 2 * c->dim, c->n_inst), 256, 0, s>>>(c->d_inst, c->dim, c->d_window,
+                                                                           c->d_wall_unit, c->d_wallTf, a.F);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
   if (a.F && c->dim >= 2) {
@@ -833,13 +1022,27 @@ cudaError_t launch_sweep_staged(const Ctx* c, const SweepArgs& a, cudaStream_t s
     for (const InstDesc& in : c->h_inst) maxcol = std::max<long long>(maxcol, in.ncells / (c->dim == 2 ? in.n[1] : in.n[2]));
     dim3 grid((unsigned)std::min<long long>((maxcol + 31) / 32, 4096), (unsigned)c->n_inst);
     if (c->dim == 2)
-      derive_last_axis_kernel<2><<<grid, 32 * DERIVE_SEG, 0, s>>>(c->d_inst, c->n_inst, c->nb, a.T, a.srcshift,
-                                                                  c->d_Vm, a.R, a.F);
+      derive_last_axis_kernel<2><<<grid, 32 * DERIVE_SEG, 0, s>>>(c->d_inst, c->n_inst, c->nb, c->d_window, a.T,
+                                                                  a.srcshift, c->d_Vm, a.R, a.F);
     else
-      derive_last_axis_kernel<3><<<grid, 32 * DERIVE_SEG, 0, s>>>(c->d_inst, c->n_inst, c->nb, a.T, a.srcshift,
-                                                                  c->d_Vm, a.R, a.F);
+      derive_last_axis_kernel<3><<<grid, 32 * DERIVE_SEG, 0, s>>>(c->d_inst, c->n_inst, c->nb, c->d_window, a.T,
+                                                                  a.srcshift, c->d_Vm, a.R, a.F);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
+  }
+  if (two) {
+    long long lines = 0, faces = 0;
+    for (const InstDesc& in : c->h_inst) {
+      lines = std::max<long long>(lines, in.n[0] + in.n[1]);
+      faces = std::max<long long>(faces, in.nfaces);
+    }
+    derive_two_group_kernel<<<dim3((unsigned)((lines + 7) / 8), (unsigned)c->n_inst), 256, 0, s>>>(
+        c->d_inst, c->nb, c->d_window, a.T, a.srcshift, c->d_Vm, a.R, c->d_wall_unit, c->d_wallTf, c->d_DY, c->d_EY,
+        c->d_GX, a.F, c->d_Fd);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    assemble_two_group_kernel<<<dim3((unsigned)std::min<long long>((faces + 255) / 256, 1024), (unsigned)c->n_inst), 256,
+                                0, s>>>(c->d_inst, c->d_window, c->d_wall_unit, c->d_wallTf, c->d_EY, c->d_Fd, a.F);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
   if (a.F && a.wall) {
     wall_absorbed_kernel<<<dim3(2 * c->dim, c->n_inst), 256, 0, s>>>(c->d_inst, c->d_wall_unit, c->d_wallTf, a.F,
@@ -870,6 +1073,7 @@ cudaError_t launch_adjoint_staged(const Ctx* c, const SweepArgs& a, cudaStream_t
                                   cudaMemcpyDeviceToDevice, s);
   if (e != cudaSuccess) return e;
   S.R32 = S.W32 = S.F32 = nullptr;
+  S.DY = S.EY = S.GX = nullptr;
   const int blocks = c->sm_count * c->adj_blocks_per_sm;
   switch (c->dim) {
     case 1: sweep_staged_kernel<1, true, false><<<blocks, STAGED_NT, 0, s>>>(a, S); break;

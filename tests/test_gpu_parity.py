@@ -361,3 +361,40 @@ def test_adjoint_gradient_exact_for_frozen_map():
     (g * T).sum().backward()
     assert torch.allclose(Qr.grad, gs, rtol=1e-9, atol=1e-12)
     assert torch.allclose(Twr.grad, gw, rtol=1e-9, atol=1e-12)
+
+
+def test_two_group_face_tallies_match_plain_fp64_faces():
+    # 2D instances whose faces all fit the shared-memory window split the particles by the
+    # axis they cross less often: each group tallies only those faces and the rest follow
+    # from the group's own power balance. Against the plain FP64 sweep of the same particles
+    # (every face tallied by FP64 atomics), on every face kind (interior, each wall) with
+    # hot, cold and negative wall temperatures: a difference is a particle whose FP32 walk
+    # ended within rounding of a face (a tie), so every face, cell and wall differs by at
+    # most a few particle weights, and only a small fraction differs at all.
+    n, N, tau = 96, 256, 0.5
+    inst = WL.cavity(n, tau).instances[0]
+    inst.wall_T = np.array([0.4, -0.3, 0.8, 1.0])
+    rng = np.random.default_rng(21)
+    T = rng.uniform(-0.2, 1.0, inst.ncells)
+    h = 1.0 / n
+    wmax = max(np.abs(T).max() * h * h / tau / N, np.abs(inst.wall_T).max() * h / 4.0 / N)
+    out = []
+    for prec, tally, sched in ((0, 0, 0), (1, 1, 1), (1, 2, 1)):
+        s = gpu_solver(inst, [1.0], [1.0], N, N, precision=prec, tally=tally, schedule=sched, seed=12)
+        out.append(s.sweep(cuda_T(T), 0))
+    ref = {key: out[0][key].cpu().numpy() for key in ("R", "W", "F", "wall")}
+    nx = (n + 1) * n
+    kinds = {"x low wall": np.s_[0:nx:n + 1], "x high wall": np.s_[n:nx:n + 1], "y low wall": np.s_[nx:nx + n],
+             "y high wall": np.s_[nx + n * n:], "all": np.s_[:]}
+    for g in out[1:]:
+        c_g, c_0 = (np.array(x["counters"].cpu().tolist(), dtype=float) for x in (g, out[0]))
+        assert c_g[0] == c_0[0] and np.all(np.abs(c_g - c_0) <= 1e-4 * c_0 + 5)
+        for key, bound in (("R", 4 * wmax), ("W", 4 * wmax * tau), ("F", 4 * wmax), ("wall", 20 * wmax)):
+            d = np.abs(g[key].cpu().numpy() - ref[key])
+            assert d.max() <= bound, (key, d.max() / wmax)
+            if key in ("R", "F"):
+                assert np.mean(d > 0.01 * wmax) < 0.02, (key, np.mean(d > 0.01 * wmax))
+        F = g["F"].cpu().numpy()
+        for name, sl in kinds.items():
+            assert np.abs(F[sl] - ref["F"][sl]).max() <= 4 * wmax, name
+            assert np.abs(ref["F"][sl]).max() > 50 * wmax, name  # the faces carry real flux
