@@ -80,6 +80,9 @@ __device__ __forceinline__ int ceil_count(float u) {
   return __float_as_int(__fadd_ru(fmaxf(u, 0.f), 8388608.f)) - 0x4B000000;
 }
 
+// i as a float for 0 <= i < 2^23, placed in the mantissa of 2^23 (no conversion instruction).
+__device__ __forceinline__ float small_int_float(int i) { return __int_as_float(0x4B000000 | i) - 8388608.f; }
+
 // Faces normal to one axis reached before path length L: #{k >= 0 : t + k d < L}.
 __device__ __forceinline__ int faces_before(float L, float t, float d) {
   return L > t ? ceil_count(__fdividef(L - t, d)) : 0;
@@ -89,7 +92,7 @@ __device__ __forceinline__ int faces_before(float L, float t, float d) {
 __device__ __forceinline__ int faces_to_wall(int i, int s, int n) { return s > 0 ? n - i : i + 1; }
 __device__ __forceinline__ float axis_exit(int i, int s, int n, float t, float d) {
   const int m = faces_to_wall(i, s, n);
-  return m > 1 ? fmaf((float)(m - 1), d, t) : t;
+  return m > 1 ? fmaf(small_int_float(m - 1), d, t) : t;
 }
 
 __device__ __forceinline__ int clampi(int v, int n) { return min(max(v, 0), n - 1); }
@@ -362,6 +365,7 @@ __global__ void k32_finalize_kernel(const float2* src, double* dst, long long n,
 template <int DIM, bool ADJ, bool K32>
 __global__ void __launch_bounds__(STAGED_NT, 1) sweep_staged_kernel(SweepArgs A, StagedArgs S) {
   extern __shared__ unsigned win[];
+  __shared__ int s_owner[STAGED_NT / 32][32];  // cooperative tallies: item position -> lane
   __shared__ int s_inst;
   LCounts cnt;
 #pragma unroll
@@ -449,7 +453,8 @@ __global__ void __launch_bounds__(STAGED_NT, 1) sweep_staged_kernel(SweepArgs A,
           }
           if (alive) {
             cnt.v[CNT_FLIGHTS] += 1;
-            const int qw = __double2int_rn(w * qinv);
+            // round(w / q) as the low word of w qinv + 1.5 2^52 (one FMA, |w qinv| <= 2^26)
+            const int qw = __double2loint(fma(w, qinv, 0x1.8p52));
             // signed along the axis whose faces the particle tallies
             qwx = (unsigned)(((two && f.d0 < f.d1) ? f.s1 : f.s0) > 0 ? qw : -qw);
             vtm = A.vtm32[(long long)k * A.nb + band];
@@ -466,6 +471,7 @@ __global__ void __launch_bounds__(STAGED_NT, 1) sweep_staged_kernel(SweepArgs A,
       // of the straight segment; its cell follows from the faces before D on each axis.
       // W tally, then acceptance with probability tau_maj / tau(x); a rejected candidate
       // draws the next flight length and the particle goes on in the same direction ----
+      int nitem = 0;  // cooperative tallies: face items of the lane's particle ended in this pass
       if (alive && !tally) {
         bool ended = false, wall_exit = false;
 #pragma unroll 1
@@ -567,9 +573,8 @@ __global__ void __launch_bounds__(STAGED_NT, 1) sweep_staged_kernel(SweepArgs A,
             f.i2 = lim;
             f.D = u0;
             f.tex = r;
-            kcur = 0;
-            tally = kend > 0;
-            alive = tally;
+            nitem = kend;  // tallied below by the whole warp
+            alive = false;
           } else if (useF) {
             // faces normal to the last axis: only the low boundary is tallied (the rest
             // follow from conservation)
@@ -587,7 +592,7 @@ __global__ void __launch_bounds__(STAGED_NT, 1) sweep_staged_kernel(SweepArgs A,
             kcur = 0;
             kend = c0 + (ex == 0 ? 1 : 0);
             if (DIM == 3) {
-              f.tex = (float)kend;  // first y-face item
+              f.tex = small_int_float(kend);  // first y-face item
               kend += c1 + (ex == 1 ? 1 : 0);
             } else if (DIM == 2) {
               // rows of the x-face crossings, incrementally: faces normal to y before the
@@ -604,10 +609,53 @@ __global__ void __launch_bounds__(STAGED_NT, 1) sweep_staged_kernel(SweepArgs A,
           }
         }
       }
+      // ---- 2D, every tallied face in the window: the warp tallies the face items of the
+      // particles that ended in this pass together, 32 items per round. Lane j of a round
+      // takes item base + j of the concatenated item lists; its owner (the lane whose list
+      // holds it) comes from the positions where lists begin within the round, and the
+      // owner's parameters by shuffles ----
+      if (DIM == 2 && (two || wfull)) {
+        int incl = nitem;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+          const int t = __shfl_up_sync(0xffffffffu, incl, o);
+          if (lane >= o) incl += t;
+        }
+        const int total = __shfl_sync(0xffffffffu, incl, 31);
+        const int first = incl - nitem;
+        int* own = s_owner[threadIdx.x >> 5];
+#pragma unroll 1
+        for (int base = 0; base < total; base += 32) {
+          const bool hit = nitem > 0 && first < base + 32 && incl > base;
+          const int p = max(first - base, 0);
+          const unsigned heads = __reduce_or_sync(0xffffffffu, hit ? 1u << p : 0u);
+          if (hit) own[p] = lane;
+          __syncwarp();
+          // the last list head at or before this lane's position (position 0 always is one)
+          const int owner = own[31 - __clz(heads & (0xffffffffu >> (31 - lane)))];
+          __syncwarp();
+          const int o_a0 = __shfl_sync(0xffffffffu, f.i0, owner);
+          const int o_sp = __shfl_sync(0xffffffffu, f.s0, owner);
+          const int o_sq = __shfl_sync(0xffffffffu, f.s1, owner);
+          const int o_lim = __shfl_sync(0xffffffffu, f.i2, owner);
+          const int o_first = __shfl_sync(0xffffffffu, first, owner);
+          const float o_u0 = __shfl_sync(0xffffffffu, f.D, owner);
+          const float o_r = __shfl_sync(0xffffffffu, f.tex, owner);
+          const unsigned o_q = __shfl_sync(0xffffffffu, qwx, owner);
+          const int g = base + lane;
+          if (g < total) {
+            const int kk = g - o_first;
+            const int face = o_a0 + kk * o_sp + o_sq * min(ceil_count(fmaf(small_int_float(kk), o_r, o_u0)), o_lim);
+            const unsigned old = atomicAdd(&win[face], o_q);
+            const int carry = ((int)o_q >> 31) + (old + o_q < old ? 1 : 0);
+            if (carry) atomicAdd(&A.F[face_off + face], (double)carry * S.wmax[k] * WIN_CARRY);
+          }
+        }
+      }
       // ---- face tallies of ended particles: up to walk_k per lane ----
       if (tally) {
         const int kstop = min(kend, kcur + S.walk_k);
-        float fk = (float)kcur;  // the item index in FP32, advanced without conversions
+        float fk = small_int_float(kcur);  // the item index in FP32, advanced without conversions
         // 64-bit sums kept as 32-bit low words in the window plus carries added to the FP64
         // face: the old word tells whether an addition wrapped (rare: words start at 2^31
         // and one contribution is at most 2^26)
