@@ -623,9 +623,9 @@ iugkp_status iugkp_create_batch(int n, const iugkp_grid* g, const double* const*
     long long maxX = 0;
     for (const InstDesc& in : c->h_inst)
       maxX = std::max(maxX, c->dim == 2 ? in.nfaces : (long long)(in.n[0] + 1) * in.n[1] * in.n[2]);
-    // static shared memory of the staged kernel (owner table of the cooperative tallies and a
-    // few words) stays below 8 KB
-    const long long budget = ((long long)c->smem_optin - 8192) / (long long)sizeof(unsigned);
+    // static shared memory of the staged kernel (the cooperative tallies' parameter table and
+    // list starts, 36.2 KB, and a few words) stays below 37 KB
+    const long long budget = ((long long)c->smem_optin - 37 * 1024) / (long long)sizeof(unsigned);
     c->staged_cap = (int)std::max<long long>(1, std::min(maxX, budget));
   }
   if ((s = rebuild_forward_groups(c)) != IUGKP_OK) return bail(s);

@@ -365,7 +365,9 @@ __global__ void k32_finalize_kernel(const float2* src, double* dst, long long n,
 template <int DIM, bool ADJ, bool K32>
 __global__ void __launch_bounds__(STAGED_NT, 1) sweep_staged_kernel(SweepArgs A, StagedArgs S) {
   extern __shared__ unsigned win[];
-  __shared__ int s_owner[STAGED_NT / 32][32];  // cooperative tallies: item position -> lane
+  // cooperative tallies: per warp, each lane's particle parameters and the item list starts
+  __shared__ int4 s_par[STAGED_NT / 32][64];
+  __shared__ int s_lst[STAGED_NT / 32][33];
   __shared__ int s_inst;
   LCounts cnt;
 #pragma unroll
@@ -610,10 +612,10 @@ __global__ void __launch_bounds__(STAGED_NT, 1) sweep_staged_kernel(SweepArgs A,
         }
       }
       // ---- 2D, every tallied face in the window: the warp tallies the face items of the
-      // particles that ended in this pass together, 32 items per round. Lane j of a round
-      // takes item base + j of the concatenated item lists; its owner (the lane whose list
-      // holds it) comes from the positions where lists begin within the round, and the
-      // owner's parameters by shuffles ----
+      // particles that ended in this pass together. The items are concatenated in lane
+      // order and cut into 32 equal contiguous chunks, one per lane; a lane finds the
+      // particle holding its first item by binary search over the list starts and reads
+      // each particle's parameters from shared memory when its chunk enters that list ----
       if (DIM == 2 && (two || wfull)) {
         int incl = nitem;
 #pragma unroll
@@ -622,34 +624,49 @@ __global__ void __launch_bounds__(STAGED_NT, 1) sweep_staged_kernel(SweepArgs A,
           if (lane >= o) incl += t;
         }
         const int total = __shfl_sync(0xffffffffu, incl, 31);
-        const int first = incl - nitem;
-        int* own = s_owner[threadIdx.x >> 5];
-#pragma unroll 1
-        for (int base = 0; base < total; base += 32) {
-          const bool hit = nitem > 0 && first < base + 32 && incl > base;
-          const int p = max(first - base, 0);
-          const unsigned heads = __reduce_or_sync(0xffffffffu, hit ? 1u << p : 0u);
-          if (hit) own[p] = lane;
-          __syncwarp();
-          // the last list head at or before this lane's position (position 0 always is one)
-          const int owner = own[31 - __clz(heads & (0xffffffffu >> (31 - lane)))];
-          __syncwarp();
-          const int o_a0 = __shfl_sync(0xffffffffu, f.i0, owner);
-          const int o_sp = __shfl_sync(0xffffffffu, f.s0, owner);
-          const int o_sq = __shfl_sync(0xffffffffu, f.s1, owner);
-          const int o_lim = __shfl_sync(0xffffffffu, f.i2, owner);
-          const int o_first = __shfl_sync(0xffffffffu, first, owner);
-          const float o_u0 = __shfl_sync(0xffffffffu, f.D, owner);
-          const float o_r = __shfl_sync(0xffffffffu, f.tex, owner);
-          const unsigned o_q = __shfl_sync(0xffffffffu, qwx, owner);
-          const int g = base + lane;
-          if (g < total) {
-            const int kk = g - o_first;
-            const int face = o_a0 + kk * o_sp + o_sq * min(ceil_count(fmaf(small_int_float(kk), o_r, o_u0)), o_lim);
-            const unsigned old = atomicAdd(&win[face], o_q);
-            const int carry = ((int)o_q >> 31) + (old + o_q < old ? 1 : 0);
-            if (carry) atomicAdd(&A.F[face_off + face], (double)carry * S.wmax[k] * WIN_CARRY);
+        if (total > 0) {
+          const int first = incl - nitem;
+          int4* par = s_par[threadIdx.x >> 5];
+          int* lst = s_lst[threadIdx.x >> 5];
+          lst[lane] = first;
+          if (lane == 31) lst[32] = total;
+          if (nitem > 0) {
+            par[2 * lane] = make_int4(f.i0, f.s0, f.s1, f.i2);
+            par[2 * lane + 1] = make_int4(__float_as_int(f.D), __float_as_int(f.tex), (int)qwx, first);
           }
+          __syncwarp();
+          const int c0 = (lane * total) >> 5, c1 = ((lane + 1) * total) >> 5;
+          if (c0 < c1) {
+            // the last list starting at or before c0 (it holds c0: empty lists start where
+            // the next one does)
+            int l = 0;
+#pragma unroll
+            for (int st = 16; st > 0; st >>= 1)
+              if (lst[l + st] <= c0) l += st;
+            int lend = lst[l + 1];
+            int4 pa = par[2 * l], pb = par[2 * l + 1];
+#pragma unroll 1
+            for (int kk = c0; kk < c1; ++kk) {
+              if (kk >= lend) {
+                do {
+                  ++l;
+                  lend = lst[l + 1];
+                } while (lend <= kk);
+                pa = par[2 * l];
+                pb = par[2 * l + 1];
+              }
+              // item kl of the particle: a0 + kl sp + sq min(ceil(u0 + kl r), lim)
+              const int kl = kk - pb.w;
+              const int face =
+                  pa.x + kl * pa.y +
+                  pa.z * min(ceil_count(fmaf(small_int_float(kl), __int_as_float(pb.y), __int_as_float(pb.x))), pa.w);
+              const unsigned q = (unsigned)pb.z;
+              const unsigned old = atomicAdd(&win[face], q);
+              const int carry = ((int)q >> 31) + (old + q < old ? 1 : 0);
+              if (carry) atomicAdd(&A.F[face_off + face], (double)carry * S.wmax[k] * WIN_CARRY);
+            }
+          }
+          __syncwarp();
         }
       }
       // ---- face tallies of ended particles: up to walk_k per lane ----
