@@ -662,8 +662,11 @@ __global__ void __launch_bounds__(STAGED_NT, 1) sweep_staged_kernel(SweepArgs A,
                   pa.z * min(ceil_count(fmaf(small_int_float(kl), __int_as_float(pb.y), __int_as_float(pb.x))), pa.w);
               const unsigned q = (unsigned)pb.z;
               const unsigned old = atomicAdd(&win[face], q);
-              const int carry = ((int)q >> 31) + (old + q < old ? 1 : 0);
-              if (carry) atomicAdd(&A.F[face_off + face], (double)carry * S.wmax[k] * WIN_CARRY);
+              // |q| <= 2^26, so the word can wrap only from within 2^26 of 0 / 2^32
+              if (old + 0x04000000u < 0x08000000u) {
+                const int carry = ((int)q >> 31) + (old + q < old ? 1 : 0);
+                if (carry) atomicAdd(&A.F[face_off + face], (double)carry * S.wmax[k] * WIN_CARRY);
+              }
             }
           }
           __syncwarp();
@@ -678,8 +681,10 @@ __global__ void __launch_bounds__(STAGED_NT, 1) sweep_staged_kernel(SweepArgs A,
         // and one contribution is at most 2^26)
         auto window_add = [&](int xface, unsigned rel) {
           const unsigned old = atomicAdd(&win[rel], qwx);
-          const int carry = ((int)qwx >> 31) + (old + qwx < old ? 1 : 0);
-          if (carry) atomicAdd(&A.F[face_off + xface], (double)carry * S.wmax[k] * WIN_CARRY);
+          if (old + 0x04000000u < 0x08000000u) {  // a wrap starts within 2^26 of 0 / 2^32
+            const int carry = ((int)qwx >> 31) + (old + qwx < old ? 1 : 0);
+            if (carry) atomicAdd(&A.F[face_off + xface], (double)carry * S.wmax[k] * WIN_CARRY);
+          }
         };
         if (DIM == 2 && (two || wfull)) {
           // every face of the tallied axis is in the window at its instance index; the count
