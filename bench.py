@@ -24,8 +24,8 @@ sys.path.insert(0, ROOT)
 
 METRIC = "cell-crossings/s and time-to-steady (res 1e-8) vs plain FP64 sweep, same GPU"
 KNS = (0.01, 0.1, 1.0, 10.0)
-SWEEP_DRAM_BYTES = 2.41e6  # ncu dram bytes per launch of the staged sweep on this workload
-SWEEP_ISSUE_UTIL = 0.767   # ncu smsp__issue_active of the same launch
+SWEEP_DRAM_BYTES = 3.80e6  # ncu dram bytes per launch of the staged sweep on this workload
+SWEEP_ISSUE_UTIL = 0.774   # ncu smsp__issue_active of the same launch
 NGRID = 128
 NPART = 1024
 
@@ -501,7 +501,7 @@ def run_ours(args):
             # Plain FP64: FP64 walk, global FP64 atomics, one thread per particle, one
             # instance at a time, no CUDA graph (same iteration, Newton and CG tolerance).
             # instance j draws with id j, as in the batch, so the two steady states share draws
-            ptot_cross, ptot_ms, psteady, piters, worst = 0, 0.0, 0.0, [], 0.0
+            ptot_cross, ptot_ms, psteady, piters, worst, mean_sum = 0, 0.0, 0.0, [], 0.0, 0.0
             for j, kn in enumerate(KNS):
                 w1 = WL.cavity(NGRID, kn, NPART)
                 sp1 = make_solver(w1, seed=0, instance_base=j, precision=0, tally=0, schedule=0, use_graphs=0)
@@ -530,12 +530,18 @@ def run_ours(args):
                     piters.append(its)
                     n1 = sp1.total_cells
                     # wall span is 1: the difference is in units of the span
-                    worst = max(worst, float((Ts[j * n1:(j + 1) * n1] - Tp).abs().max()))
+                    dT = (Ts[j * n1:(j + 1) * n1] - Tp).abs()
+                    worst = max(worst, float(dT.max()))
+                    mean_sum += float(dT.mean()) / len(KNS)
                 del sp1
             plain = {"sweep_crossings_per_s": ptot_cross / (ptot_ms / 1e3),
                      "steady_s_sequential": psteady if not args.no_steady else None, "steady_iters": piters}
             if not args.no_steady:
+                # FP32 and FP64 walks part at ties (a particle ending within rounding of a
+                # face): a moved wall particle outweighs the ~70 real collisions per cell at
+                # Kn = 10, so single cells differ by much more than the mean
                 steady["fast_vs_fp64_max_abs_diff_of_span"] = worst
+                steady["fast_vs_fp64_mean_abs_diff_of_span"] = mean_sum
         others = None
         if not args.no_configs:
             others = other_config_sweeps(WL, make_solver)
