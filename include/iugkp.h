@@ -98,7 +98,12 @@ typedef struct {
   int blocks_per_sm;                  /* persistent blocks per SM (0 = auto) */
   int refill_lanes;                   /* staged sweep: a warp refills its idle lanes once at
                                          least this many (1..32) are idle; 0 = chosen per
-                                         instance from the expected events per particle */
+                                         instance from the expected events per particle.
+                                         0 or 32 in 2D when every instance's tallied faces
+                                         fit the shared-memory window: pass-synchronous
+                                         schedule (each pass of a warp emits up to 32
+                                         particles, follows each to its end, then tallies
+                                         their faces together) */
   int use_graphs;                     /* 1: iugkp_solve_steady with frozen draws replays a
                                          CUDA graph of two iterations (one host readback per
                                          two iterations); 0: plain launches */

@@ -746,6 +746,207 @@ __global__ void __launch_bounds__(STAGED_NT, 1) sweep_staged_kernel(SweepArgs A,
   flush_lcounts(cnt, A.counters);
 }
 
+// 2D instances whose tallied faces all sit in the window, pass by pass: every pass of a warp
+// emits up to 32 particles (one per lane), follows each to its end (real collision or
+// wall), and tallies the face items of all of them together (the cooperative tallies of
+// sweep_staged_kernel). A particle's state lives only inside its pass, so the tally loop
+// runs with the per-particle registers free. Same particles, draws and tallies as
+// sweep_staged_kernel; chosen when the candidates per flight are few (each lane waits for
+// the longest flight of its pass).
+template <bool K32>
+__global__ void __launch_bounds__(STAGED_NT, 1) sweep_sync_kernel(SweepArgs A, StagedArgs S) {
+  extern __shared__ unsigned win[];
+  __shared__ int4 s_par[STAGED_NT / 32][64];
+  __shared__ int s_lst[STAGED_NT / 32][33];
+  __shared__ int s_inst;
+  LCounts cnt;
+#pragma unroll
+  for (int k = 0; k < CNT_N; ++k) cnt.v[k] = 0;
+  const int lane = threadIdx.x & 31;
+  const int n_inst = S.n_inst;
+  int start = 0;
+  {
+    const double pos = (blockIdx.x + 0.5) / gridDim.x * S.cost_total;
+    while (start + 1 < n_inst && S.cost_prefix[start + 1] <= pos) ++start;
+  }
+  int4* par = s_par[threadIdx.x >> 5];
+  int* lst = s_lst[threadIdx.x >> 5];
+  for (int visit = 0; visit < n_inst; ++visit) {
+    const int k = (start + visit) % n_inst;
+    if (threadIdx.x == 0) s_inst = (*(volatile unsigned long long*)&S.inst_next[k] < (unsigned long long)S.inst_end[k]) ? k : -1;
+    __syncthreads();
+    if (s_inst < 0) {
+      __syncthreads();
+      continue;
+    }
+    const InstDesc& in = A.inst[k];
+    const int n0 = in.n[0], n1 = in.n[1];
+    const long long face_off = in.face_off, fax1 = in.fax_off[1];
+    const int sy_xf = n0 + 1;
+    const unsigned wlen = (unsigned)S.window[k].y;
+    const bool two = (long long)wlen == in.nfaces;  // else the window holds every x-face
+    for (unsigned i = threadIdx.x; i < wlen; i += STAGED_NT) win[i] = WIN_BIAS;
+    __syncthreads();
+    const double qinv = S.wmax[k] > 0.0 ? WIN_SCALE / S.wmax[k] : 0.0;
+    const unsigned pend = (unsigned)S.inst_end[k];
+    unsigned rbeg = 0, rend = 0;  // this warp's private particle range
+    EmitCache ec;
+    ec.g_first = 1;
+    ec.g_end = 0;  // empty: forces a lookup on the first emission
+    ec.e = -1;
+    for (;;) {
+      if (rbeg == rend) {  // private range used up: take the next one of the instance
+        unsigned long long got = 0;
+        if (lane == 0) got = atomicAdd(&S.inst_next[k], (unsigned long long)S.warp_grab);
+        got = __shfl_sync(0xffffffffu, got, 0);
+        if (got >= pend) break;
+        rbeg = (unsigned)got;
+        rend = (unsigned)min(got + (unsigned long long)S.warp_grab, (unsigned long long)pend);
+      }
+      const unsigned take = min(32u, rend - rbeg);
+      int nitem = 0;
+      if ((unsigned)lane < take) {
+        double w;
+        int band, emitter;
+        PW f;
+        Stream st;
+        uint32_t ub;
+        if (staged_emit<2, false>(A, S, rbeg + lane, true, w, band, f, st, ub, ec, in, k, emitter, two)) {
+          cnt.v[CNT_FLIGHTS] += 1;
+          const int qw = __double2loint(fma(w, qinv, 0x1.8p52));
+          const bool yg = two && f.d0 < f.d1;
+          const unsigned qwx = (unsigned)((yg ? f.s1 : f.s0) > 0 ? qw : -qw);
+          const float vtm = A.vtm32[(long long)k * A.nb + band];
+          const long long bcbase = in.bc_off + (long long)band * in.ncells;
+          // candidates (Sec. 3.2) until the particle collides for real or reaches a wall
+          bool wall_exit = false;
+#pragma unroll 1
+          for (;;) {
+            if (f.tex < f.D) {
+              cnt.v[CNT_WALL_EXITS] += 1;
+              wall_exit = true;
+              break;
+            }
+            cnt.v[CNT_CANDIDATES] += 1;
+            const int cell = clampi(f.i0 + f.s0 * faces_before(f.D, f.t0, f.d0), n0) +
+                             n0 * clampi(f.i1 + f.s1 * faces_before(f.D, f.t1, f.d1), n1);
+            const long long ci = bcbase + cell;
+            if (K32 && S.W32) tally_k32(&S.W32[ci], w);
+            else if (!K32 && A.W) atomicAdd(&A.W[ci], w);
+            if (word_uniform<float>(ub) < A.ratio32[ci]) {
+              cnt.v[CNT_REAL] += 1;
+              if (K32) tally_k32(&S.R32[ci], w);
+              else atomicAdd(&A.R[ci], w);
+              if (yg) atomicAdd(&S.DY[in.cell_off + cell], w);
+              break;
+            }
+            uint32_t ua;
+            st.next_pair(ua, ub);
+            f.D += -__logf(word_uniform<float>(ua)) * vtm;
+          }
+          // faces crossed before the end per axis (the exit axis's count is known)
+          const float L = wall_exit ? f.tex : f.D;
+          int ex = -1;
+          if (wall_exit) ex = axis_exit(f.i0, f.s0, n0, f.t0, f.d0) <= axis_exit(f.i1, f.s1, n1, f.t1, f.d1) ? 0 : 1;
+          const int m0 = faces_to_wall(f.i0, f.s0, n0), m1 = faces_to_wall(f.i1, f.s1, n1);
+          const int c0 = ex == 0 ? m0 - 1 : min(faces_before(L, f.t0, f.d0), m0 - 1);
+          const int c1 = ex == 1 ? m1 - 1 : min(faces_before(L, f.t1, f.d1), m1 - 1);
+          cnt.v[CNT_CROSSINGS] += c0 + c1;
+          // face items along the tallied axis p: a0 + k sp + sq min(ceil(u0 + k r), lim)
+          int a0, sp, sq, lim;
+          float u0, r;
+          if (!yg) {
+            if (ex == 1 && f.s1 < 0) {
+              const int col = f.i0 + f.s0 * c0;
+              if (two) atomicAdd(&S.GX[in.bface_off + in.wface_off[2] + col], -w);
+              else if (K32) tally_k32(&S.F32[face_off + fax1 + col], -w);
+              else atomicAdd(&A.F[face_off + fax1 + col], -w);
+            }
+            nitem = c0 + (ex == 0 ? 1 : 0);
+            const bool flat = !(f.d1 < INFINITY);
+            u0 = flat ? -1.f : __fdividef(f.t0 - f.t1, f.d1);
+            r = flat ? 0.f : __fdividef(f.d0, f.d1);
+            lim = m1 - 1;
+            a0 = (f.s0 > 0 ? f.i0 + 1 : f.i0) + sy_xf * f.i1;
+            sp = f.s0;
+            sq = f.s1 * sy_xf;
+          } else {
+            if (ex == 0 && f.s0 < 0) atomicAdd(&S.GX[in.bface_off + in.wface_off[0] + (f.i1 + f.s1 * c1)], -w);
+            nitem = c1 + (ex == 1 ? 1 : 0);
+            u0 = __fdividef(f.t1 - f.t0, f.d0);
+            r = __fdividef(f.d1, f.d0);
+            lim = m0 - 1;
+            a0 = (int)fax1 + f.i0 + n0 * (f.s1 > 0 ? f.i1 + 1 : f.i1);
+            sp = f.s1 * n0;
+            sq = f.s0;
+          }
+          par[2 * lane] = make_int4(a0, sp, sq, lim);
+          par[2 * lane + 1] = make_int4(__float_as_int(u0), __float_as_int(r), (int)qwx, 0);
+        }
+      }
+      rbeg += take;
+      // ---- the pass's face items, cut into 32 equal contiguous chunks (one per lane) ----
+      int incl = nitem;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int t = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += t;
+      }
+      const int total = __shfl_sync(0xffffffffu, incl, 31);
+      if (total > 0) {
+        const int first = incl - nitem;
+        lst[lane] = first;
+        if (lane == 31) lst[32] = total;
+        if (nitem > 0) par[2 * lane + 1].w = first;
+        __syncwarp();
+        const int c0 = (lane * total) >> 5, c1 = ((lane + 1) * total) >> 5;
+        if (c0 < c1) {
+          int l = 0;
+#pragma unroll
+          for (int st = 16; st > 0; st >>= 1)
+            if (lst[l + st] <= c0) l += st;
+          int lend = lst[l + 1];
+          int4 pa = par[2 * l], pb = par[2 * l + 1];
+#pragma unroll 1
+          for (int kk = c0; kk < c1; ++kk) {
+            if (kk >= lend) {
+              do {
+                ++l;
+                lend = lst[l + 1];
+              } while (lend <= kk);
+              pa = par[2 * l];
+              pb = par[2 * l + 1];
+            }
+            const int kl = kk - pb.w;
+            const int face =
+                pa.x + kl * pa.y +
+                pa.z * min(ceil_count(fmaf(small_int_float(kl), __int_as_float(pb.y), __int_as_float(pb.x))), pa.w);
+            const unsigned q = (unsigned)pb.z;
+            const unsigned old = atomicAdd(&win[face], q);
+            // |q| <= 2^26, so the word can wrap only from within 2^26 of 0 / 2^32
+            if (old + 0x04000000u < 0x08000000u) {
+              const int carry = ((int)q >> 31) + (old + q < old ? 1 : 0);
+              if (carry) atomicAdd(&A.F[face_off + face], (double)carry * S.wmax[k] * WIN_CARRY);
+            }
+          }
+        }
+        __syncwarp();
+      }
+    }
+    __syncthreads();
+    {
+      const double qs = S.wmax[k] / WIN_SCALE;
+      double* Fx = A.F + face_off;
+      for (unsigned i = threadIdx.x; i < wlen; i += STAGED_NT) {
+        const int v = (int)(win[i] - WIN_BIAS);
+        if (v) atomicAdd(&Fx[i], (double)v * qs);
+      }
+    }
+    __syncthreads();
+  }
+  flush_lcounts(cnt, A.counters);
+}
+
 // Faces normal to the last axis from per-cell conservation, one thread per column:
 // F[k+1] = F[k] + (net inflow through the other axes' faces of cell k) - (R_k - S_k),
 // S_k = V m T_emit (emitted thermal and source power), starting from the tallied low
@@ -1049,6 +1250,9 @@ cudaError_t launch_sweep_staged(const Ctx* c, const SweepArgs& a, cudaStream_t s
     if ((e = cudaMemsetAsync(c->d_GX, 0, (size_t)c->total_bfaces * sizeof(double), s)) != cudaSuccess) return e;
   }
   const bool k32 = c->opt.tally == IUGKP_TALLY_STAGED_K32;
+  // pass-synchronous schedule: refill only when all 32 lanes are idle (the default where it
+  // applies)
+  const bool sync = c->sync_ok && a.F && (c->opt.refill_lanes == 0 || c->opt.refill_lanes == 32);
   S.R32 = k32 ? c->d_R32 : nullptr;
   S.W32 = k32 && a.W ? c->d_W32 : nullptr;
   S.F32 = k32 && a.F ? c->d_F32 : nullptr;
@@ -1060,7 +1264,10 @@ cudaError_t launch_sweep_staged(const Ctx* c, const SweepArgs& a, cudaStream_t s
       return e;
     switch (c->dim) {
       case 1: sweep_staged_kernel<1, false, true><<<blocks, STAGED_NT, smem, s>>>(a, S); break;
-      case 2: sweep_staged_kernel<2, false, true><<<blocks, STAGED_NT, smem, s>>>(a, S); break;
+      case 2:
+        if (sync) sweep_sync_kernel<true><<<blocks, STAGED_NT, smem, s>>>(a, S);
+        else sweep_staged_kernel<2, false, true><<<blocks, STAGED_NT, smem, s>>>(a, S);
+        break;
       default: sweep_staged_kernel<3, false, true><<<blocks, STAGED_NT, smem, s>>>(a, S); break;
     }
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
@@ -1071,7 +1278,10 @@ cudaError_t launch_sweep_staged(const Ctx* c, const SweepArgs& a, cudaStream_t s
   } else {
     switch (c->dim) {
       case 1: sweep_staged_kernel<1, false, false><<<blocks, STAGED_NT, smem, s>>>(a, S); break;
-      case 2: sweep_staged_kernel<2, false, false><<<blocks, STAGED_NT, smem, s>>>(a, S); break;
+      case 2:
+        if (sync) sweep_sync_kernel<false><<<blocks, STAGED_NT, smem, s>>>(a, S);
+        else sweep_staged_kernel<2, false, false><<<blocks, STAGED_NT, smem, s>>>(a, S);
+        break;
       default: sweep_staged_kernel<3, false, false><<<blocks, STAGED_NT, smem, s>>>(a, S); break;
     }
   }
@@ -1160,6 +1370,9 @@ cudaError_t configure_staged(Ctx* c) {
                         (const void*)sweep_staged_kernel<3, false, false>, (const void*)sweep_staged_kernel<1, false, true>,
                         (const void*)sweep_staged_kernel<2, false, true>, (const void*)sweep_staged_kernel<3, false, true>};
   for (const void* f : fwd)
+    if ((e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess) return e;
+  const void* syn[2] = {(const void*)sweep_sync_kernel<false>, (const void*)sweep_sync_kernel<true>};
+  for (const void* f : syn)
     if ((e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess) return e;
   int nb = 0, nk = 0;
   if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fwd[c->dim - 1], STAGED_NT, smem)) != cudaSuccess) return e;
