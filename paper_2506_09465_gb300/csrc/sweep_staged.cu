@@ -805,6 +805,7 @@ __global__ void __launch_bounds__(STAGED_NT, 1) sweep_sync_kernel(SweepArgs A, S
       }
       const unsigned take = min(32u, rend - rbeg);
       int nitem = 0;
+      int4 pa_own, pb_own;  // this lane's item parameters, stored once its list slot is known
       if ((unsigned)lane < take) {
         double w;
         int band, emitter;
@@ -880,12 +881,14 @@ __global__ void __launch_bounds__(STAGED_NT, 1) sweep_sync_kernel(SweepArgs A, S
             sp = f.s1 * n0;
             sq = f.s0;
           }
-          par[2 * lane] = make_int4(a0, sp, sq, lim);
-          par[2 * lane + 1] = make_int4(__float_as_int(u0), __float_as_int(r), (int)qwx, 0);
+          pa_own = make_int4(a0, sp, sq, lim);
+          pb_own = make_int4(__float_as_int(u0), __float_as_int(r), (int)qwx, 0);
         }
       }
       rbeg += take;
-      // ---- the pass's face items, cut into 32 equal contiguous chunks (one per lane) ----
+      // ---- the pass's face items: the non-empty item lists are numbered in lane order and
+      // their concatenation is cut into 32 equal contiguous chunks (one per lane) ----
+      const unsigned has = __ballot_sync(0xffffffffu, nitem > 0);
       int incl = nitem;
 #pragma unroll
       for (int o = 1; o < 32; o <<= 1) {
@@ -894,26 +897,29 @@ __global__ void __launch_bounds__(STAGED_NT, 1) sweep_sync_kernel(SweepArgs A, S
       }
       const int total = __shfl_sync(0xffffffffu, incl, 31);
       if (total > 0) {
-        const int first = incl - nitem;
-        lst[lane] = first;
-        if (lane == 31) lst[32] = total;
-        if (nitem > 0) par[2 * lane + 1].w = first;
+        const int nl = __popc(has);
+        if (nitem > 0) {
+          const int slot = __popc(has & ((1u << lane) - 1u));
+          lst[slot] = incl - nitem;
+          par[2 * slot] = pa_own;
+          par[2 * slot + 1] = make_int4(pb_own.x, pb_own.y, pb_own.z, incl - nitem);
+        }
+        if (lane == 0) lst[nl] = total;
         __syncwarp();
         const int c0 = (lane * total) >> 5, c1 = ((lane + 1) * total) >> 5;
         if (c0 < c1) {
+          // the list holding item c0: the last start at or before it
           int l = 0;
 #pragma unroll
           for (int st = 16; st > 0; st >>= 1)
-            if (lst[l + st] <= c0) l += st;
+            if (l + st < nl && lst[l + st] <= c0) l += st;
           int lend = lst[l + 1];
           int4 pa = par[2 * l], pb = par[2 * l + 1];
 #pragma unroll 1
           for (int kk = c0; kk < c1; ++kk) {
-            if (kk >= lend) {
-              do {
-                ++l;
-                lend = lst[l + 1];
-              } while (lend <= kk);
+            if (kk >= lend) {  // the next list (no list is empty)
+              ++l;
+              lend = lst[l + 1];
               pa = par[2 * l];
               pb = par[2 * l + 1];
             }
