@@ -24,8 +24,8 @@ sys.path.insert(0, ROOT)
 
 METRIC = "cell-crossings/s and time-to-steady (res 1e-8) vs plain FP64 sweep, same GPU"
 KNS = (0.01, 0.1, 1.0, 10.0)
-SWEEP_DRAM_BYTES = 3.80e6  # ncu dram bytes per launch of the staged sweep on this workload
-SWEEP_ISSUE_UTIL = 0.774   # ncu smsp__issue_active of the same launch
+SWEEP_DRAM_BYTES = 3.47e6  # ncu dram bytes per launch of the staged sweep on this workload
+SWEEP_ISSUE_UTIL = 0.771   # ncu smsp__issue_active of the same launch
 NGRID = 128
 NPART = 1024
 
