@@ -163,7 +163,7 @@ __device__ __forceinline__ void team_sync(cg::cluster_group& cl) {
   else cl.sync();
 }
 
-constexpr long long MG_SOLO_CELLS = 4096;
+constexpr long long MG_SOLO_CELLS = 1024;
 
 // Damped Jacobi sweeps on a level from the iterate in v.x: ping-pong between v.x and v.t;
 // returns the buffer that holds the result. Every sweep ends with a team barrier.
