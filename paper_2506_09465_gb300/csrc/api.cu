@@ -110,7 +110,8 @@ void free_all(Ctx* c) {
                   c->d_group_mag, c->d_mag, c->d_wall_unit, c->d_all_beg, c->d_all_end, c->d_all_cost_prefix,
                   c->d_all_group_mag, c->d_R32, c->d_W32, c->d_F32, c->d_m2, c->d_wallTf,
                   c->d_pslot_off, c->d_phome_off, c->d_pnband, c->d_pnwall, c->d_px, c->d_pband, c->d_phome,
-                  c->d_pdue, c->d_pcount, c->d_phome_w, c->d_wemit, c->d_DY, c->d_EY, c->d_GX, c->d_Fd};
+                  c->d_pdue, c->d_pcount, c->d_phome_w, c->d_wemit, c->d_DY, c->d_EY, c->d_GX, c->d_Fd,
+                  c->d_all_real};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (c->h_pinned) cudaFreeHost(c->h_pinned);
@@ -594,6 +595,22 @@ iugkp_status iugkp_create_batch(int n, const iugkp_grid* g, const double* const*
   UP(c->d_coef, coef);
   UP(c->d_ratio64, r64);
   UP(c->d_ratio32, r32);
+  {
+    // bands whose every cell has tau = tau_maj: every candidate is real (the uniform, below
+    // 1, always passes the test against a ratio of exactly 1)
+    std::vector<int> all_real((size_t)n * nb, 1);
+    for (int k = 0; k < n; ++k)
+      for (int bb = 0; bb < nb; ++bb) {
+        const InstDesc& in = c->h_inst[k];
+        for (long long i = 0; i < in.ncells; ++i)
+          if (r32[(size_t)in.bc_off + (size_t)bb * in.ncells + i] != 1.0f) {
+            all_real[(size_t)k * nb + bb] = 0;
+            break;
+          }
+      }
+    UP(c->d_all_real, all_real);
+    c->all_real_all = std::all_of(all_real.begin(), all_real.end(), [](int x) { return x != 0; });
+  }
   UP(c->d_taumaj, taumaj);
   {
     std::vector<float> vtm((size_t)n * nb);
@@ -741,6 +758,7 @@ SweepArgs base_args(Ctx* c) {
   a.coef = c->d_coef;
   a.ratio64 = c->d_ratio64;
   a.ratio32 = c->d_ratio32;
+  a.all_real = c->d_all_real;
   a.taumaj = c->d_taumaj;
   a.vtm32 = c->d_vtm32;
   a.v = c->d_v;

@@ -27,6 +27,7 @@ struct SweepArgs {
   const double* coef;      // [bc] C_b V / (tau N_b): weight per unit emission temperature
   const double* ratio64;   // [bc] tau_maj / tau (acceptance probability of a candidate)
   const float* ratio32;
+  const int* all_real;     // [inst * nb] 1 where tau = tau_maj in every cell (every candidate real)
   const double* taumaj;    // [inst * nb] majorant tau per instance and band
   const double* v;         // [nb] group speed
   const float* vtm32;      // [inst * nb] v_b tau_maj in FP32
@@ -77,6 +78,8 @@ struct Ctx {
   double* d_coef = nullptr;
   double* d_ratio64 = nullptr;
   float* d_ratio32 = nullptr;
+  int* d_all_real = nullptr;     // [inst * nb] tau = tau_maj in every cell of the band
+  bool all_real_all = false;     // ... in every instance and band
   double* d_taumaj = nullptr;
   float* d_vtm32 = nullptr;
   double* d_v = nullptr;

@@ -752,8 +752,9 @@ __global__ void __launch_bounds__(STAGED_NT, 1) sweep_staged_kernel(SweepArgs A,
 // sweep_staged_kernel). A particle's state lives only inside its pass, so the tally loop
 // runs with the per-particle registers free. Same particles, draws and tallies as
 // sweep_staged_kernel; chosen when the candidates per flight are few (each lane waits for
-// the longest flight of its pass).
-template <bool K32>
+// the longest flight of its pass). REAL: tau = tau_maj in every cell of every instance and
+// band, so every candidate is real and the acceptance test is left out.
+template <bool K32, bool REAL>
 __global__ void __launch_bounds__(STAGED_NT, 1) sweep_sync_kernel(SweepArgs A, StagedArgs S) {
   extern __shared__ unsigned win[];
   __shared__ int4 s_par[STAGED_NT / 32][64];
@@ -818,6 +819,7 @@ __global__ void __launch_bounds__(STAGED_NT, 1) sweep_sync_kernel(SweepArgs A, S
           const bool yg = two && f.d0 < f.d1;
           const unsigned qwx = (unsigned)((yg ? f.s1 : f.s0) > 0 ? qw : -qw);
           const float vtm = A.vtm32[(long long)k * A.nb + band];
+          const bool all_real = REAL || A.all_real[(long long)k * A.nb + band] != 0;
           const long long bcbase = in.bc_off + (long long)band * in.ncells;
           // candidates (Sec. 3.2) until the particle collides for real or reaches a wall
           bool wall_exit = false;
@@ -834,7 +836,7 @@ __global__ void __launch_bounds__(STAGED_NT, 1) sweep_sync_kernel(SweepArgs A, S
             const long long ci = bcbase + cell;
             if (K32 && S.W32) tally_k32(&S.W32[ci], w);
             else if (!K32 && A.W) atomicAdd(&A.W[ci], w);
-            if (word_uniform<float>(ub) < A.ratio32[ci]) {
+            if (all_real || word_uniform<float>(ub) < A.ratio32[ci]) {
               cnt.v[CNT_REAL] += 1;
               if (K32) tally_k32(&S.R32[ci], w);
               else atomicAdd(&A.R[ci], w);
@@ -854,33 +856,29 @@ __global__ void __launch_bounds__(STAGED_NT, 1) sweep_sync_kernel(SweepArgs A, S
           const int c1 = ex == 1 ? m1 - 1 : min(faces_before(L, f.t1, f.d1), m1 - 1);
           cnt.v[CNT_CROSSINGS] += c0 + c1;
           // face items along the tallied axis p: a0 + k sp + sq min(ceil(u0 + k r), lim)
-          int a0, sp, sq, lim;
-          float u0, r;
-          if (!yg) {
-            if (ex == 1 && f.s1 < 0) {
+          // p: the tallied axis (x for the x-group), q: the other one; selects, no branch
+          const float tp = yg ? f.t1 : f.t0, tq = yg ? f.t0 : f.t1;
+          const float dp = yg ? f.d1 : f.d0, dq = yg ? f.d0 : f.d1;
+          const int cp = yg ? c1 : c0, mq = yg ? m0 : m1, axp = yg ? 1 : 0;
+          if (ex == 1 - axp && (yg ? f.s0 : f.s1) < 0) {  // exit through the low q-wall
+            if (two) {
+              const int j = yg ? in.wface_off[0] + f.i1 + f.s1 * c1 : in.wface_off[2] + f.i0 + f.s0 * c0;
+              atomicAdd(&S.GX[in.bface_off + j], -w);
+            } else {
               const int col = f.i0 + f.s0 * c0;
-              if (two) atomicAdd(&S.GX[in.bface_off + in.wface_off[2] + col], -w);
-              else if (K32) tally_k32(&S.F32[face_off + fax1 + col], -w);
+              if (K32) tally_k32(&S.F32[face_off + fax1 + col], -w);
               else atomicAdd(&A.F[face_off + fax1 + col], -w);
             }
-            nitem = c0 + (ex == 0 ? 1 : 0);
-            const bool flat = !(f.d1 < INFINITY);
-            u0 = flat ? -1.f : __fdividef(f.t0 - f.t1, f.d1);
-            r = flat ? 0.f : __fdividef(f.d0, f.d1);
-            lim = m1 - 1;
-            a0 = (f.s0 > 0 ? f.i0 + 1 : f.i0) + sy_xf * f.i1;
-            sp = f.s0;
-            sq = f.s1 * sy_xf;
-          } else {
-            if (ex == 0 && f.s0 < 0) atomicAdd(&S.GX[in.bface_off + in.wface_off[0] + (f.i1 + f.s1 * c1)], -w);
-            nitem = c1 + (ex == 1 ? 1 : 0);
-            u0 = __fdividef(f.t1 - f.t0, f.d0);
-            r = __fdividef(f.d1, f.d0);
-            lim = m0 - 1;
-            a0 = (int)fax1 + f.i0 + n0 * (f.s1 > 0 ? f.i1 + 1 : f.i1);
-            sp = f.s1 * n0;
-            sq = f.s0;
           }
+          nitem = cp + (ex == axp ? 1 : 0);
+          const bool flat = !(dq < INFINITY);
+          const float u0 = flat ? -1.f : __fdividef(tp - tq, dq);
+          const float r = flat ? 0.f : __fdividef(dp, dq);
+          const int lim = mq - 1;
+          const int a0 = yg ? (int)fax1 + f.i0 + n0 * (f.i1 + (f.s1 > 0 ? 1 : 0))
+                            : f.i0 + (f.s0 > 0 ? 1 : 0) + sy_xf * f.i1;
+          const int sp = yg ? f.s1 * n0 : f.s0;
+          const int sq = yg ? f.s0 : f.s1 * sy_xf;
           pa_own = make_int4(a0, sp, sq, lim);
           pb_own = make_int4(__float_as_int(u0), __float_as_int(r), (int)qwx, 0);
         }
@@ -1271,7 +1269,8 @@ cudaError_t launch_sweep_staged(const Ctx* c, const SweepArgs& a, cudaStream_t s
     switch (c->dim) {
       case 1: sweep_staged_kernel<1, false, true><<<blocks, STAGED_NT, smem, s>>>(a, S); break;
       case 2:
-        if (sync) sweep_sync_kernel<true><<<blocks, STAGED_NT, smem, s>>>(a, S);
+        if (sync && c->all_real_all) sweep_sync_kernel<true, true><<<blocks, STAGED_NT, smem, s>>>(a, S);
+        else if (sync) sweep_sync_kernel<true, false><<<blocks, STAGED_NT, smem, s>>>(a, S);
         else sweep_staged_kernel<2, false, true><<<blocks, STAGED_NT, smem, s>>>(a, S);
         break;
       default: sweep_staged_kernel<3, false, true><<<blocks, STAGED_NT, smem, s>>>(a, S); break;
@@ -1285,7 +1284,8 @@ cudaError_t launch_sweep_staged(const Ctx* c, const SweepArgs& a, cudaStream_t s
     switch (c->dim) {
       case 1: sweep_staged_kernel<1, false, false><<<blocks, STAGED_NT, smem, s>>>(a, S); break;
       case 2:
-        if (sync) sweep_sync_kernel<false><<<blocks, STAGED_NT, smem, s>>>(a, S);
+        if (sync && c->all_real_all) sweep_sync_kernel<false, true><<<blocks, STAGED_NT, smem, s>>>(a, S);
+        else if (sync) sweep_sync_kernel<false, false><<<blocks, STAGED_NT, smem, s>>>(a, S);
         else sweep_staged_kernel<2, false, false><<<blocks, STAGED_NT, smem, s>>>(a, S);
         break;
       default: sweep_staged_kernel<3, false, false><<<blocks, STAGED_NT, smem, s>>>(a, S); break;
@@ -1377,7 +1377,8 @@ cudaError_t configure_staged(Ctx* c) {
                         (const void*)sweep_staged_kernel<2, false, true>, (const void*)sweep_staged_kernel<3, false, true>};
   for (const void* f : fwd)
     if ((e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess) return e;
-  const void* syn[2] = {(const void*)sweep_sync_kernel<false>, (const void*)sweep_sync_kernel<true>};
+  const void* syn[4] = {(const void*)sweep_sync_kernel<false, false>, (const void*)sweep_sync_kernel<true, false>,
+                        (const void*)sweep_sync_kernel<false, true>, (const void*)sweep_sync_kernel<true, true>};
   for (const void* f : syn)
     if ((e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess) return e;
   int nb = 0, nk = 0;
