@@ -913,7 +913,7 @@ __global__ void __launch_bounds__(STAGED_NT, 1) sweep_sync_kernel(SweepArgs A, S
             if (l + st < nl && lst[l + st] <= c0) l += st;
           int lend = lst[l + 1];
           int4 pa = par[2 * l], pb = par[2 * l + 1];
-#pragma unroll 1
+#pragma unroll 2
           for (int kk = c0; kk < c1; ++kk) {
             if (kk >= lend) {  // the next list (no list is empty)
               ++l;
