@@ -42,6 +42,7 @@ struct PArgs {
   const double* ratio64;       // [bc] tau_maj / tau
   const float* ratio32;        // [bc] tau_maj / tau in FP32
   const float* vtm32;          // [inst * nb] v_b tau_maj in FP32
+  const int* all_real;         // [inst * nb] 1 where tau = tau_maj in every cell
   const double* taumaj;        // [inst * nb]
   const double* v;             // [nb]
   const double* wcoef;         // [inst * nb * 6] C_b v_b A / (4 N_w)
@@ -278,7 +279,8 @@ __global__ void __launch_bounds__(256, 4) persistent_step_kernel(PArgs A) {
       c_cand += 1;
       const long long jb = in.bc_off + (long long)b * in.ncells + c;
       atomicAdd(&A.W[jb], w * tm);
-      if (word_uniform<Real>(ub) < accept_ratio<Real>(A, jb)) {
+      // (a band with tau = tau_maj everywhere accepts every candidate: the uniform is below 1)
+      if (A.all_real[(long long)k * A.nb + b] || word_uniform<Real>(ub) < accept_ratio<Real>(A, jb)) {
         c_real += 1;
         atomicAdd(&A.R[jb], w);
         h = c;
@@ -381,6 +383,7 @@ cudaError_t launch_persistent_step(const Ctx* c, const double* T, unsigned it, d
   a.ratio64 = c->d_ratio64;
   a.ratio32 = c->d_ratio32;
   a.vtm32 = c->d_vtm32;
+  a.all_real = c->d_all_real;
   a.taumaj = c->d_taumaj;
   a.v = c->d_v;
   a.wcoef = c->d_wcoef;
