@@ -24,8 +24,8 @@ sys.path.insert(0, ROOT)
 
 METRIC = "cell-crossings/s and time-to-steady (res 1e-8) vs plain FP64 sweep, same GPU"
 KNS = (0.01, 0.1, 1.0, 10.0)
-SWEEP_DRAM_BYTES = 3.47e6  # ncu dram bytes per launch of the staged sweep on this workload
-SWEEP_ISSUE_UTIL = 0.771   # ncu smsp__issue_active of the same launch
+SWEEP_DRAM_BYTES = 3.21e6  # ncu dram bytes per launch of the staged sweep on this workload
+SWEEP_ISSUE_UTIL = 0.785   # ncu smsp__issue_active of the same launch
 NGRID = 128
 NPART = 1024
 
@@ -375,6 +375,42 @@ def _persistent_time(wl, make_solver, prec, steps, warmup):
             "hbm_frac": gbs / peak, "tracking": prec}
 
 
+def newton_step_time(lib, L, solver, T, T_half, R, stream, sp, flush, reps):
+    """The correction solve alone (Newton right-hand side, MG-PCG, update) on the fields of
+    one iteration, timed with CUDA events on the launching stream, against the measured HBM
+    bandwidth. Algorithmic bytes per cell and CG iteration: the FP64 stencil product (three
+    coefficient arrays, p, q: 40 B), the FP64 vector updates and dot products (x, r, p, q, z:
+    10 accesses, 80 B) and the FP32 V-cycle's finest level (seven passes over b, x, t, r and
+    four coefficient arrays: 200 B), 320 B in all."""
+    import ctypes
+    import torch
+    L.check(lib.iugkp_macro(solver.ctx, R.data_ptr(), None, T_half.data_ptr(), None, sp), solver.ctx)
+    T_half0 = T_half.clone()
+    ms, its = [], 0
+    for _ in range(reps):
+        T_half.copy_(T_half0)
+        flush.zero_()
+        it = ctypes.c_int(0)
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        L.check(lib.iugkp_newton_step(solver.ctx, T.data_ptr(), T_half.data_ptr(), R.data_ptr(), sp,
+                                      ctypes.byref(it)), solver.ctx)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        ms.append(ev0.elapsed_time(ev1))
+        its = it.value
+    peak = 6783.5
+    try:
+        peak = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["hbm_gbs"]
+    except Exception:
+        pass
+    t = statistics.median(ms)
+    nbytes = 320 * solver.total_cells * its
+    gbs = nbytes / (t * 1e-3) / 1e9
+    return {"ms": t, "cg_iters": its, "algorithmic_bytes": nbytes, "achieved_gbs": gbs, "hbm_peak_gbs": peak,
+            "hbm_frac": gbs / peak, "note": "L2-resident; bound by the latency of the cluster barriers"}
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -459,6 +495,7 @@ def run_ours(args):
             torch.cuda.synchronize()
             sweep_ms.append(ev0.elapsed_time(ev1))
     sweep_counts = cnt.cpu().numpy().astype(np.int64)
+    newton = newton_step_time(lib, L, solver, T, T_half, R, stream, sp, flush, max(3, args.steps // 2))
     t_max, crossings_all = aggregate_ranks(sum(per_step_ms) / 1e3, crossings, dev)
     value = crossings_all / t_max
     ms_per_step = 1e3 * t_max / args.steps
@@ -578,6 +615,7 @@ def run_ours(args):
                        "parallelism": f"replicas x{world}" if world > 1 else "1 GPU"},
             "flights_per_step": int(flights / args.steps), "crossings_per_step": int(crossings / args.steps),
             "sweep_ms": statistics.median(sweep_ms),
+            "newton_step": newton,
             "time_to_steady": steady,
             "adjoint_gradient": adjoint,
             "persistent_scheme": persistent,
@@ -586,10 +624,11 @@ def run_ours(args):
             "speedup_vs_plain_fp64_sweep": (sweep_counts[3] / sw_s) / plain["sweep_crossings_per_s"] if plain else None,
             "e2e": {"value": e2e_value, "unit": "cell-crossings/s", "h2d_bytes_per_step": nc * 8,
                     "d2h_bytes_per_step": nc * 8},
-            # per step: group_wmax, sweep_staged, boundary_emission, derive_last_axis,
-            # wall_absorbed, macro, newton_rhs, mgpcg, add_scaled, residual (2 kernels),
-            # plus three finalize passes (R, W, F) with compensated FP32 tallies
-            "gpu_launches": args.steps * (11 + (3 if tuned.get("tally") == 2 else 0)),
+            # per step: group_wmax, sweep, scale_by_taumaj, boundary_emission,
+            # derive_last_axis, derive_two_group, assemble_two_group, wall_absorbed, macro,
+            # newton_rhs, mgpcg, add_scaled, residual (2 kernels), plus three finalize
+            # passes (R, W, F) with compensated FP32 tallies
+            "gpu_launches": args.steps * (14 + (3 if tuned.get("tally") == 2 else 0)),
             "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": peak_ops / 1e12,
                          "unit": "Tops/s (FP32+INT32 lane ops)", "frac": achieved / peak_ops,
                          # DRAM bytes (read + write) of one launch of this sweep kernel on this
