@@ -363,15 +363,18 @@ def test_adjoint_gradient_exact_for_frozen_map():
     assert torch.allclose(Twr.grad, gw, rtol=1e-9, atol=1e-12)
 
 
-def test_two_group_face_tallies_match_plain_fp64_faces():
+@pytest.mark.parametrize("n", [96, 180])
+def test_two_group_face_tallies_match_plain_fp64_faces(n):
     # 2D instances whose faces all fit the shared-memory window split the particles by the
     # axis they cross less often: each group tallies only those faces and the rest follow
-    # from the group's own power balance. Against the plain FP64 sweep of the same particles
+    # from the group's own power balance (n = 96). At n = 180 only the faces normal to x fit:
+    # every particle tallies those and the faces normal to y follow from conservation. Both
+    # run the pass-synchronous kernel. Against the plain FP64 sweep of the same particles
     # (every face tallied by FP64 atomics), on every face kind (interior, each wall) with
     # hot, cold and negative wall temperatures: a difference is a particle whose FP32 walk
     # ended within rounding of a face (a tie), so every face, cell and wall differs by at
     # most a few particle weights, and only a small fraction differs at all.
-    n, N, tau = 96, 256, 0.5
+    N, tau = 256, 0.5
     inst = WL.cavity(n, tau).instances[0]
     inst.wall_T = np.array([0.4, -0.3, 0.8, 1.0])
     rng = np.random.default_rng(21)
