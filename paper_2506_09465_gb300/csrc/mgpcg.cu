@@ -109,6 +109,33 @@ __device__ __forceinline__ float level_apply(const float* dg, const float* cx, c
   return q;
 }
 
+// y = A_l u for u = x + alpha P xc (x prolonged from the coarser level's correction xc, P
+// injection), for one cell at coordinates (X, Y, Z), without storing u. Neighbours across a
+// boundary are skipped by coordinates (their coefficient is zero).
+template <class LD>
+__device__ __forceinline__ float level_apply_prolonged(const float* dg, const float* cx, const float* cy,
+                                                       const float* cz, const float* x, const float* xc, float alpha,
+                                                       const int* n, const int* nC, int dim, long long i, int X, int Y,
+                                                       int Z) {
+  auto u = [&](long long j, int x0, int y0, int z0) {
+    const long long J = (x0 >> 1) + (long long)nC[0] * ((y0 >> 1) + (long long)nC[1] * (z0 >> 1));
+    return fmaf(alpha, LD::ld(&xc[J]), LD::ld(&x[j]));
+  };
+  const long long sy = n[0], sz = (long long)n[0] * n[1];
+  float q = dg[i] * u(i, X, Y, Z);
+  if (X + 1 < n[0]) q -= cx[i] * u(i + 1, X + 1, Y, Z);
+  if (X >= 1) q -= cx[i - 1] * u(i - 1, X - 1, Y, Z);
+  if (dim >= 2) {
+    if (Y + 1 < n[1]) q -= cy[i] * u(i + sy, X, Y + 1, Z);
+    if (Y >= 1) q -= cy[i - sy] * u(i - sy, X, Y - 1, Z);
+  }
+  if (dim >= 3) {
+    if (Z + 1 < n[2]) q -= cz[i] * u(i + sz, X, Y, Z + 1);
+    if (Z >= 1) q -= cz[i - sz] * u(i - sz, X, Y, Z - 1);
+  }
+  return q;
+}
+
 // Who works on a level: the whole cluster (cells split in contiguous ranges over the CTAs,
 // level vectors in global memory read through L2, cluster barriers) or CTA 0 alone (level
 // vectors in its shared memory, block barriers). Levels of at most MG_SOLO_CELLS cells go
@@ -200,13 +227,8 @@ __device__ void vdown(const MGArgs& A, const InstMG& m, int l, const LevelView& 
   for (long long i = lo + threadIdx.x; i < hi; i += NT) v.x[i] = A.omega * v.b[i] * v.dinv[i];
   team_sync<TM>(cl);
   float* src = jacobi<TM, NT, CS>(A, m, l, v, tm, cl, A.nu - 1);
-  // residual of the smoothed iterate; the iterate is moved into x if it ended in t
-  for (long long i = lo + threadIdx.x; i < hi; i += NT) {
-    const float ax = level_apply<TM>(v.dg, v.cx, v.cy, v.cz, src, m.n[l], m.dim, i, nc);
-    v.r[i] = v.b[i] - ax;
-    if (src != v.x) v.x[i] = src[i];
-  }
-  team_sync<TM>(cl);
+  // restriction of the smoothed iterate's residual (sum over the children, P^T r), each
+  // child's residual formed where it is summed; the iterate is moved into x if it ended in t
   const long long ncc = m.nc[l + 1];
   long long clo, chi;
   team_range<TM, NT, CS>(tm, ncc, clo, chi);
@@ -218,11 +240,15 @@ __device__ void vdown(const MGArgs& A, const InstMG& m, int l, const LevelView& 
       for (int dy = 0; dy < (m.dim >= 2 ? 2 : 1); ++dy)
         for (int dx = 0; dx < 2; ++dx) {
           const int fx = 2 * X0 + dx, fy = 2 * Y0 + dy, fz = 2 * Z0 + dz;
-          if (fx < m.n[l][0] && fy < m.n[l][1] && fz < m.n[l][2])
-            sum += TM::ld(&v.r[fx + (long long)m.n[l][0] * (fy + (long long)m.n[l][1] * fz)]);
+          if (fx < m.n[l][0] && fy < m.n[l][1] && fz < m.n[l][2]) {
+            const long long c = fx + (long long)m.n[l][0] * (fy + (long long)m.n[l][1] * fz);
+            sum += TM::ld(&v.b[c]) - level_apply<TM>(v.dg, v.cx, v.cy, v.cz, src, m.n[l], m.dim, c, nc);
+          }
         }
     vc.b[I] = sum;
   }
+  if (src != v.x)
+    for (long long i = lo + threadIdx.x; i < hi; i += NT) v.x[i] = src[i];
   team_sync<TM>(cl);
 }
 
@@ -250,14 +276,20 @@ __device__ void vup(const MGArgs& A, const InstMG& m, int l, const LevelView& v,
   const long long nc = m.nc[l];
   long long lo, hi;
   team_range<TM, NT, CS>(tm, nc, lo, hi);
+  // first sweep from u = x + alpha P xc (the prolonged iterate, formed where it is read)
+  // into t; the remaining sweeps ping-pong t and x
   for (long long i = lo + threadIdx.x; i < hi; i += NT) {
     int X0, Y0, Z0;
     level_coords(m.n[l], i, X0, Y0, Z0);
     const long long I = (X0 >> 1) + (long long)m.n[l + 1][0] * ((Y0 >> 1) + (long long)m.n[l + 1][1] * (Z0 >> 1));
-    v.x[i] += A.alpha * TM::ld(&vc.x[I]);
+    const float ui = fmaf(A.alpha, TM::ld(&vc.x[I]), v.x[i]);
+    const float au = level_apply_prolonged<TM>(v.dg, v.cx, v.cy, v.cz, v.x, vc.x, A.alpha, m.n[l], m.n[l + 1], m.dim, i,
+                                              X0, Y0, Z0);
+    v.t[i] = ui + A.omega * (v.b[i] - au) * v.dinv[i];
   }
   team_sync<TM>(cl);
-  float* src = jacobi<TM, NT, CS>(A, m, l, v, tm, cl, A.nu);
+  const LevelView vt{v.dg, v.dinv, v.cx, v.cy, v.cz, v.b, v.t, v.x, v.r};  // iterate in t, scratch x
+  float* src = jacobi<TM, NT, CS>(A, m, l, vt, tm, cl, A.nu - 1);
   if (src != v.x) {
     for (long long i = lo + threadIdx.x; i < hi; i += NT) v.x[i] = src[i];
     team_sync<TM>(cl);

@@ -99,8 +99,9 @@ __device__ __forceinline__ int clampi(int v, int n) { return min(max(v, 0), n - 
 
 }  // namespace
 
-// One block per forward group: the largest |weight| of its emitters, max-reduced into
-// its instance's slot (non-negative doubles order like their bit patterns).
+// gridDim.y blocks per forward group (blockIdx.x): the largest |weight| of the group's
+// emitters, max-reduced into its instance's slot (non-negative doubles order like their bit
+// patterns). Several blocks per group spread the FP64 weight arithmetic over the SMs.
 __global__ void group_wmax_kernel(SweepArgs A, unsigned long long* wmax_bits) {
   __shared__ double sh[32];
   const Group G = A.groups[blockIdx.x];
@@ -108,7 +109,7 @@ __global__ void group_wmax_kernel(SweepArgs A, unsigned long long* wmax_bits) {
   double m = 0.0;
   if (G.kind == 0) {
     const long long base = in.bc_off + (long long)G.band * in.ncells;
-    for (int e = threadIdx.x; e < in.ncells; e += blockDim.x) {
+    for (int e = blockIdx.y * blockDim.x + threadIdx.x; e < in.ncells; e += gridDim.y * blockDim.x) {
       double Te = A.T[in.cell_off + e];
       if (A.srcshift) Te += A.srcshift[in.cell_off + e];
       const double w = A.coef[base + e] * Te;
@@ -119,7 +120,8 @@ __global__ void group_wmax_kernel(SweepArgs A, unsigned long long* wmax_bits) {
     const int wl = G.kind - 1;
     const double wc = A.wcoef[((long long)G.inst * A.nb + G.band) * 6 + wl];
     const double* tf = A.wallTf + in.bface_off + in.wface_off[wl];
-    for (int j = threadIdx.x; j < G.n_emitters; j += blockDim.x) m = fmax(m, fabs(wc * tf[j]));
+    for (int j = blockIdx.y * blockDim.x + threadIdx.x; j < G.n_emitters; j += gridDim.y * blockDim.x)
+      m = fmax(m, fabs(wc * tf[j]));
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_down_sync(0xffffffffu, m, o));
@@ -1240,7 +1242,13 @@ cudaError_t launch_sweep_staged(const Ctx* c, const SweepArgs& a, cudaStream_t s
                                   cudaMemcpyDeviceToDevice, s);
   if (e != cudaSuccess) return e;
   if ((e = cudaMemsetAsync(c->d_wmax, 0, c->n_inst * sizeof(double), s)) != cudaSuccess) return e;
-  group_wmax_kernel<<<a.n_groups, 256, 0, s>>>(a, c->d_wmax);
+  {
+    // about four emitters per thread, at most 64 blocks per group
+    long long most = 1;
+    for (const Group& g : c->h_groups_fwd) most = std::max<long long>(most, g.n_emitters);
+    const unsigned split = (unsigned)std::min<long long>(64, (most + 1023) / 1024);
+    group_wmax_kernel<<<dim3(a.n_groups, split), 256, 0, s>>>(a, c->d_wmax);
+  }
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   const size_t smem = (size_t)c->staged_cap * sizeof(unsigned);
   const int blocks = c->sm_count * c->staged_blocks_per_sm;
