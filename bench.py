@@ -139,6 +139,12 @@ def oracle_rate(n_particles: int, budget_s: float):
                 return crossings / dt, dt, crossings, sample
 
 
+# the workload both arms report (the reference arm times a bounded sample of it)
+WORKLOAD = ("2D gray cavity 128x128 unit square, Kn {0.01,0.1,1,10} batched (4 instances), top wall T=1, "
+            "1024 particles/cell (2^24 per instance) + 1024 per wall face; one step = sweep + macro + "
+            "Newton(CG) + residual")
+
+
 def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
@@ -159,8 +165,8 @@ def run_reference(args):
             "warmup": args.warmup, "ms_per_step": 1e3 * sum(times) / len(times), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "impl": "reference",
-            "config": {"workload": "2D gray cavity 128x128, Kn {0.01,0.1,1,10}, top wall T=1 (oracle sample)",
-                       "particles_per_cell": n_part},
+            "config": {"workload": WORKLOAD, "tracking": "fp64 (oracle)", "tallies": "fp64", "draws": "frozen",
+                       "parallelism": "1 host core"},
             "cpu_baseline": {"value": value, "unit": "cell-crossings/s", "cores": 1, "kind": "oracle",
                              "sample": sample + "; one step = about 1 s of oracle sweeps"},
             "e2e": {"value": value, "unit": "cell-crossings/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -605,9 +611,7 @@ def run_ours(args):
             "metric": METRIC, "value": value, "unit": "cell-crossings/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": "2D gray cavity 128x128 unit square, Kn {0.01,0.1,1,10} batched (4 instances), "
-                                   "top wall T=1, 1024 particles/cell (2^24 per instance) + 1024 per wall face; "
-                                   "one step = sweep + macro + Newton(CG) + residual",
+            "config": {"workload": WORKLOAD,
                        "tracking": "fp32",
                        "tallies": "fp32 compensated (hi + exact-error word)" if tuned.get("tally") == 2 else "fp64",
                        "draws": "frozen", "autotuned": tuning,
