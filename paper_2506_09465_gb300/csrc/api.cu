@@ -242,6 +242,7 @@ iugkp_status rebuild_forward_groups(Ctx* c) {
   std::vector<int2> window(c->n_inst);
   c->any_two_group = false;
   c->sync_ok = c->dim == 2;
+  c->sync_partial = false;
   for (int k = 0; k < c->n_inst; ++k) {
     const InstDesc& in = c->h_inst[k];
     const long long X = (long long)(in.n[0] + 1) * in.n[1] * in.n[2];
@@ -252,7 +253,7 @@ iugkp_status rebuild_forward_groups(Ctx* c) {
     }
     const long long len = std::min<long long>(X, c->staged_cap);
     window[k] = make_int2((int)((X - len) / 2), (int)len);
-    if (len < X) c->sync_ok = false;
+    if (len < X) c->sync_partial = true;
   }
   void* olds[] = {c->d_inst_beg, c->d_inst_end, c->d_cost_prefix, c->d_window, c->d_group_mag};
   for (void* p : olds)

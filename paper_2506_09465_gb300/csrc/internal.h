@@ -92,8 +92,8 @@ struct Ctx {
   double* d_GX = nullptr;        // [total_bfaces]
   double* d_Fd = nullptr;        // [total_faces] faces derived from the group balances
   bool any_two_group = false;    // some instance of the context uses the two-group tallies
-  bool sync_ok = false;          // 2D, every instance's tallied faces in the window: the
-                                 // pass-synchronous staged kernel applies
+  bool sync_ok = false;          // 2D: the pass-synchronous staged kernel applies
+  bool sync_partial = false;     // ... and some instance's x-faces exceed the window
   double* d_wallTf = nullptr;    // [total_bfaces]
   double* d_srcshift = nullptr;  // null when no source
   double* d_source = nullptr;    // Q (kept for set_field)

@@ -755,8 +755,10 @@ __global__ void __launch_bounds__(STAGED_NT, 1) sweep_staged_kernel(SweepArgs A,
 // runs with the per-particle registers free. Same particles, draws and tallies as
 // sweep_staged_kernel; chosen when the candidates per flight are few (each lane waits for
 // the longest flight of its pass). REAL: tau = tau_maj in every cell of every instance and
-// band, so every candidate is real and the acceptance test is left out.
-template <bool K32, bool REAL>
+// band, so every candidate is real and the acceptance test is left out. PARTIAL: some
+// instance's x-faces exceed the window (a centred run of them sits there); the faces outside
+// take global atomics of the same fixed-point contribution.
+template <bool K32, bool REAL, bool PARTIAL>
 __global__ void __launch_bounds__(STAGED_NT, 1) sweep_sync_kernel(SweepArgs A, StagedArgs S) {
   extern __shared__ unsigned win[];
   __shared__ int4 s_par[STAGED_NT / 32][64];
@@ -786,8 +788,10 @@ __global__ void __launch_bounds__(STAGED_NT, 1) sweep_sync_kernel(SweepArgs A, S
     const int n0 = in.n[0], n1 = in.n[1];
     const long long face_off = in.face_off, fax1 = in.fax_off[1];
     const int sy_xf = n0 + 1;
+    const int wbase = PARTIAL ? S.window[k].x : 0;
     const unsigned wlen = (unsigned)S.window[k].y;
-    const bool two = (long long)wlen == in.nfaces;  // else the window holds every x-face
+    // every face in the window (two-group tallies); else x-faces [wbase, wbase + wlen)
+    const bool two = wbase == 0 && (long long)wlen == in.nfaces;
     for (unsigned i = threadIdx.x; i < wlen; i += STAGED_NT) win[i] = WIN_BIAS;
     __syncthreads();
     const double qinv = S.wmax[k] > 0.0 ? WIN_SCALE / S.wmax[k] : 0.0;
@@ -928,7 +932,14 @@ __global__ void __launch_bounds__(STAGED_NT, 1) sweep_sync_kernel(SweepArgs A, S
                 pa.x + kl * pa.y +
                 pa.z * min(ceil_count(fmaf(small_int_float(kl), __int_as_float(pb.y), __int_as_float(pb.x))), pa.w);
             const unsigned q = (unsigned)pb.z;
-            const unsigned old = atomicAdd(&win[face], q);
+            const unsigned rel = (unsigned)(face - wbase);
+            if (PARTIAL && rel >= wlen) {  // outside the window: the same contribution, globally
+              const double val = (double)(int)q * (S.wmax[k] / WIN_SCALE);
+              if (K32) tally_k32(&S.F32[face_off + face], val);
+              else atomicAdd(&A.F[face_off + face], val);
+              continue;
+            }
+            const unsigned old = atomicAdd(&win[rel], q);
             // |q| <= 2^26, so the word can wrap only from within 2^26 of 0 / 2^32
             if (old + 0x04000000u < 0x08000000u) {
               const int carry = ((int)q >> 31) + (old + q < old ? 1 : 0);
@@ -942,7 +953,7 @@ __global__ void __launch_bounds__(STAGED_NT, 1) sweep_sync_kernel(SweepArgs A, S
     __syncthreads();
     {
       const double qs = S.wmax[k] / WIN_SCALE;
-      double* Fx = A.F + face_off;
+      double* Fx = A.F + face_off + wbase;
       for (unsigned i = threadIdx.x; i < wlen; i += STAGED_NT) {
         const int v = (int)(win[i] - WIN_BIAS);
         if (v) atomicAdd(&Fx[i], (double)v * qs);
@@ -1222,6 +1233,17 @@ __global__ void __launch_bounds__(256) wall_absorbed_kernel(const InstDesc* inst
   }
 }
 
+template <bool K32>
+void launch_sync(const Ctx* c, const SweepArgs& a, const StagedArgs& S, int blocks, size_t smem, cudaStream_t s) {
+  if (c->all_real_all) {
+    if (c->sync_partial) sweep_sync_kernel<K32, true, true><<<blocks, STAGED_NT, smem, s>>>(a, S);
+    else sweep_sync_kernel<K32, true, false><<<blocks, STAGED_NT, smem, s>>>(a, S);
+  } else {
+    if (c->sync_partial) sweep_sync_kernel<K32, false, true><<<blocks, STAGED_NT, smem, s>>>(a, S);
+    else sweep_sync_kernel<K32, false, false><<<blocks, STAGED_NT, smem, s>>>(a, S);
+  }
+}
+
 cudaError_t launch_sweep_staged(const Ctx* c, const SweepArgs& a, cudaStream_t s) {
   StagedArgs S;
   S.n_inst = c->n_inst;
@@ -1277,8 +1299,7 @@ cudaError_t launch_sweep_staged(const Ctx* c, const SweepArgs& a, cudaStream_t s
     switch (c->dim) {
       case 1: sweep_staged_kernel<1, false, true><<<blocks, STAGED_NT, smem, s>>>(a, S); break;
       case 2:
-        if (sync && c->all_real_all) sweep_sync_kernel<true, true><<<blocks, STAGED_NT, smem, s>>>(a, S);
-        else if (sync) sweep_sync_kernel<true, false><<<blocks, STAGED_NT, smem, s>>>(a, S);
+        if (sync) launch_sync<true>(c, a, S, blocks, smem, s);
         else sweep_staged_kernel<2, false, true><<<blocks, STAGED_NT, smem, s>>>(a, S);
         break;
       default: sweep_staged_kernel<3, false, true><<<blocks, STAGED_NT, smem, s>>>(a, S); break;
@@ -1292,8 +1313,7 @@ cudaError_t launch_sweep_staged(const Ctx* c, const SweepArgs& a, cudaStream_t s
     switch (c->dim) {
       case 1: sweep_staged_kernel<1, false, false><<<blocks, STAGED_NT, smem, s>>>(a, S); break;
       case 2:
-        if (sync && c->all_real_all) sweep_sync_kernel<false, true><<<blocks, STAGED_NT, smem, s>>>(a, S);
-        else if (sync) sweep_sync_kernel<false, false><<<blocks, STAGED_NT, smem, s>>>(a, S);
+        if (sync) launch_sync<false>(c, a, S, blocks, smem, s);
         else sweep_staged_kernel<2, false, false><<<blocks, STAGED_NT, smem, s>>>(a, S);
         break;
       default: sweep_staged_kernel<3, false, false><<<blocks, STAGED_NT, smem, s>>>(a, S); break;
@@ -1385,8 +1405,10 @@ cudaError_t configure_staged(Ctx* c) {
                         (const void*)sweep_staged_kernel<2, false, true>, (const void*)sweep_staged_kernel<3, false, true>};
   for (const void* f : fwd)
     if ((e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess) return e;
-  const void* syn[4] = {(const void*)sweep_sync_kernel<false, false>, (const void*)sweep_sync_kernel<true, false>,
-                        (const void*)sweep_sync_kernel<false, true>, (const void*)sweep_sync_kernel<true, true>};
+  const void* syn[8] = {(const void*)sweep_sync_kernel<false, false, false>, (const void*)sweep_sync_kernel<true, false, false>,
+                        (const void*)sweep_sync_kernel<false, true, false>, (const void*)sweep_sync_kernel<true, true, false>,
+                        (const void*)sweep_sync_kernel<false, false, true>, (const void*)sweep_sync_kernel<true, false, true>,
+                        (const void*)sweep_sync_kernel<false, true, true>, (const void*)sweep_sync_kernel<true, true, true>};
   for (const void* f : syn)
     if ((e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess) return e;
   int nb = 0, nk = 0;
