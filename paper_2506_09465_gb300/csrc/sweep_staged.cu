@@ -298,7 +298,10 @@ __device__ __forceinline__ bool staged_emit(const SweepArgs& A, const StagedArgs
   f.tex = axis_exit(f.i0, f.s0, n0, f.t0, f.d0);
   if (DIM >= 2) {
     axis_init(sy, xi1, in.hf[1], f.t1, f.d1, f.s1);
-    f.tex = fminf(f.tex, axis_exit(f.i1, f.s1, n1, f.t1, f.d1));
+    const float e1 = axis_exit(f.i1, f.s1, n1, f.t1, f.d1);
+    // 2D: the axis of the wall the segment reaches (x on ties), kept in the unused i2
+    if (DIM == 2) f.i2 = e1 < f.tex ? 1 : 0;
+    f.tex = fminf(f.tex, e1);
   }
   if (DIM >= 3) {
     axis_init(sz, xi2, in.hf[2], f.t2, f.d2, f.s2);
@@ -829,6 +832,7 @@ __global__ void __launch_bounds__(STAGED_NT, 1) sweep_sync_kernel(SweepArgs A, S
           const long long bcbase = in.bc_off + (long long)band * in.ncells;
           // candidates (Sec. 3.2) until the particle collides for real or reaches a wall
           bool wall_exit = false;
+          int fb0 = 0, fb1 = 0;  // faces before the latest candidate, per axis
 #pragma unroll 1
           for (;;) {
             if (f.tex < f.D) {
@@ -837,8 +841,9 @@ __global__ void __launch_bounds__(STAGED_NT, 1) sweep_sync_kernel(SweepArgs A, S
               break;
             }
             cnt.v[CNT_CANDIDATES] += 1;
-            const int cell = clampi(f.i0 + f.s0 * faces_before(f.D, f.t0, f.d0), n0) +
-                             n0 * clampi(f.i1 + f.s1 * faces_before(f.D, f.t1, f.d1), n1);
+            fb0 = faces_before(f.D, f.t0, f.d0);
+            fb1 = faces_before(f.D, f.t1, f.d1);
+            const int cell = clampi(f.i0 + f.s0 * fb0, n0) + n0 * clampi(f.i1 + f.s1 * fb1, n1);
             const long long ci = bcbase + cell;
             if (K32 && S.W32) tally_k32(&S.W32[ci], w);
             else if (!K32 && A.W) atomicAdd(&A.W[ci], w);
@@ -853,13 +858,19 @@ __global__ void __launch_bounds__(STAGED_NT, 1) sweep_sync_kernel(SweepArgs A, S
             st.next_pair(ua, ub);
             f.D += -__logf(word_uniform<float>(ua)) * vtm;
           }
-          // faces crossed before the end per axis (the exit axis's count is known)
-          const float L = wall_exit ? f.tex : f.D;
-          int ex = -1;
-          if (wall_exit) ex = axis_exit(f.i0, f.s0, n0, f.t0, f.d0) <= axis_exit(f.i1, f.s1, n1, f.t1, f.d1) ? 0 : 1;
+          // faces crossed before the end per axis: at a real collision those before its
+          // candidate; at a wall the exit axis's count is known and the other axis's follows
+          // from the exit distance
           const int m0 = faces_to_wall(f.i0, f.s0, n0), m1 = faces_to_wall(f.i1, f.s1, n1);
-          const int c0 = ex == 0 ? m0 - 1 : min(faces_before(L, f.t0, f.d0), m0 - 1);
-          const int c1 = ex == 1 ? m1 - 1 : min(faces_before(L, f.t1, f.d1), m1 - 1);
+          int ex = -1, c0, c1;
+          if (wall_exit) {
+            ex = f.i2;
+            c0 = ex == 0 ? m0 - 1 : min(faces_before(f.tex, f.t0, f.d0), m0 - 1);
+            c1 = ex == 1 ? m1 - 1 : min(faces_before(f.tex, f.t1, f.d1), m1 - 1);
+          } else {
+            c0 = min(fb0, m0 - 1);
+            c1 = min(fb1, m1 - 1);
+          }
           cnt.v[CNT_CROSSINGS] += c0 + c1;
           // face items along the tallied axis p: a0 + k sp + sq min(ceil(u0 + k r), lim)
           // p: the tallied axis (x for the x-group), q: the other one; selects, no branch
