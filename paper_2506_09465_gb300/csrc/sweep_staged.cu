@@ -975,6 +975,114 @@ __global__ void __launch_bounds__(STAGED_NT, 1) sweep_sync_kernel(SweepArgs A, S
   flush_lcounts(cnt, A.counters);
 }
 
+// The adjoint re-trace of 2D contexts, pass by pass: every pass of a warp emits up to 32
+// particles (every emitter's, per unit emission temperature), follows each to its real
+// collision or wall, and gathers c_p lambda[stop] / (V m_stop) into the particle's emitter
+// cell (or its wall, summed per lane while the lane stays on one wall group). Same
+// particles and draws as the per-lane-refill re-trace of sweep_staged_kernel<DIM, true>.
+template <bool REAL>
+__global__ void __launch_bounds__(STAGED_NT, 1) adjoint_sync_kernel(SweepArgs A, StagedArgs S) {
+  __shared__ int s_inst;
+  LCounts cnt;
+#pragma unroll
+  for (int k = 0; k < CNT_N; ++k) cnt.v[k] = 0;
+  const int lane = threadIdx.x & 31;
+  const int n_inst = S.n_inst;
+  int start = 0;
+  {
+    const double pos = (blockIdx.x + 0.5) / gridDim.x * S.cost_total;
+    while (start + 1 < n_inst && S.cost_prefix[start + 1] <= pos) ++start;
+  }
+  for (int visit = 0; visit < n_inst; ++visit) {
+    const int k = (start + visit) % n_inst;
+    if (threadIdx.x == 0) s_inst = (*(volatile unsigned long long*)&S.inst_next[k] < (unsigned long long)S.inst_end[k]) ? k : -1;
+    __syncthreads();
+    if (s_inst < 0) {
+      __syncthreads();
+      continue;
+    }
+    const InstDesc& in = A.inst[k];
+    const int n0 = in.n[0], n1 = in.n[1];
+    const unsigned pend = (unsigned)S.inst_end[k];
+    unsigned rbeg = 0, rend = 0;  // this warp's private particle range
+    EmitCache ec;
+    ec.g_first = 1;
+    ec.g_end = 0;  // empty: forces a lookup on the first emission
+    ec.e = -1;
+    int acc_slot = 0;  // wall slot of the pending per-lane wall sum
+    double acc = 0.0;
+    for (;;) {
+      if (rbeg == rend) {  // private range used up: take the next one of the instance
+        unsigned long long got = 0;
+        if (lane == 0) got = atomicAdd(&S.inst_next[k], (unsigned long long)S.warp_grab);
+        got = __shfl_sync(0xffffffffu, got, 0);
+        if (got >= pend) break;
+        rbeg = (unsigned)got;
+        rend = (unsigned)min(got + (unsigned long long)S.warp_grab, (unsigned long long)pend);
+      }
+      const unsigned take = min(32u, rend - rbeg);
+      if ((unsigned)lane < take) {
+        double w;
+        int band, emitter;
+        PW f;
+        Stream st;
+        uint32_t ub;
+        if (staged_emit<2, true>(A, S, rbeg + lane, false, w, band, f, st, ub, ec, in, k, emitter, false)) {
+          if (emitter < 0 && emitter != acc_slot) {
+            if (acc != 0.0) atomicAdd(&A.adj_wall[in.wall_off + (-1 - acc_slot)], acc);
+            acc = 0.0;
+            acc_slot = emitter;
+          }
+          cnt.v[CNT_FLIGHTS] += 1;
+          const float vtm = A.vtm32[(long long)k * A.nb + band];
+          const bool all_real = REAL || A.all_real[(long long)k * A.nb + band] != 0;
+          const long long bcbase = in.bc_off + (long long)band * in.ncells;
+          bool wall_exit = false;
+          int fb0 = 0, fb1 = 0;  // faces before the latest candidate, per axis
+#pragma unroll 1
+          for (;;) {
+            if (f.tex < f.D) {
+              cnt.v[CNT_WALL_EXITS] += 1;
+              wall_exit = true;
+              break;
+            }
+            cnt.v[CNT_CANDIDATES] += 1;
+            fb0 = faces_before(f.D, f.t0, f.d0);
+            fb1 = faces_before(f.D, f.t1, f.d1);
+            const int cell = clampi(f.i0 + f.s0 * fb0, n0) + n0 * clampi(f.i1 + f.s1 * fb1, n1);
+            if (all_real || word_uniform<float>(ub) < A.ratio32[bcbase + cell]) {
+              cnt.v[CNT_REAL] += 1;
+              const long long gc = in.cell_off + cell;
+              const double val = w * A.lambda[gc] * A.invVm[gc];
+              if (emitter >= 0) atomicAdd(&A.adj_out[in.cell_off + emitter], val);
+              else acc += val;
+              break;
+            }
+            uint32_t ua;
+            st.next_pair(ua, ub);
+            f.D += -__logf(word_uniform<float>(ua)) * vtm;
+          }
+          // faces crossed, for the event counters (as in the forward sweep)
+          const int m0 = faces_to_wall(f.i0, f.s0, n0), m1 = faces_to_wall(f.i1, f.s1, n1);
+          int c0, c1;
+          if (wall_exit) {
+            c0 = f.i2 == 0 ? m0 - 1 : min(faces_before(f.tex, f.t0, f.d0), m0 - 1);
+            c1 = f.i2 == 1 ? m1 - 1 : min(faces_before(f.tex, f.t1, f.d1), m1 - 1);
+          } else {
+            c0 = min(fb0, m0 - 1);
+            c1 = min(fb1, m1 - 1);
+          }
+          cnt.v[CNT_CROSSINGS] += c0 + c1;
+        }
+      }
+      rbeg += take;
+    }
+    if (acc != 0.0) atomicAdd(&A.adj_wall[in.wall_off + (-1 - acc_slot)], acc);
+    __syncthreads();
+  }
+  flush_lcounts(cnt, A.counters);
+}
+
 // Faces normal to the last axis from per-cell conservation, one thread per column:
 // F[k+1] = F[k] + (net inflow through the other axes' faces of cell k) - (R_k - S_k),
 // S_k = V m T_emit (emitted thermal and source power), starting from the tallied low
@@ -1400,6 +1508,12 @@ cudaError_t launch_adjoint_staged(const Ctx* c, const SweepArgs& a, cudaStream_t
   S.R32 = S.W32 = S.F32 = nullptr;
   S.DY = S.EY = S.GX = nullptr;
   const int blocks = c->sm_count * c->adj_blocks_per_sm;
+  if (c->dim == 2 && (c->opt.refill_lanes == 0 || c->opt.refill_lanes == 32)) {
+    // pass-synchronous re-trace (refill only when all 32 lanes are idle)
+    if (c->all_real_all) adjoint_sync_kernel<true><<<blocks, STAGED_NT, 0, s>>>(a, S);
+    else adjoint_sync_kernel<false><<<blocks, STAGED_NT, 0, s>>>(a, S);
+    return cudaGetLastError();
+  }
   switch (c->dim) {
     case 1: sweep_staged_kernel<1, true, false><<<blocks, STAGED_NT, 0, s>>>(a, S); break;
     case 2: sweep_staged_kernel<2, true, false><<<blocks, STAGED_NT, 0, s>>>(a, S); break;
