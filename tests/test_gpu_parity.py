@@ -317,6 +317,27 @@ def test_fast_adjoint_matches_dense_transpose(orc):
         assert ok, err
 
 
+@pytest.mark.parametrize("refill", [4, 16])
+def test_pass_synchronous_adjoint_matches_per_lane_refill(refill):
+    # The 2D adjoint re-trace runs pass by pass by default (refill_lanes 0) and with the
+    # per-lane refill of the staged kernel otherwise: the same particles, draws and gathers,
+    # so the adjoint fields and gradients agree to FP64 summation order; on a non-gray
+    # (acceptance-tested) and a gray instance.
+    rng = np.random.default_rng(23)
+    insts = [WL.random_instance(rng, 2, (24, 20), 2, (0.05, 0.6), source=True), WL.cavity(32, 0.3).instances[0]]
+    for inst in insts:
+        g = np.zeros(inst.ncells)
+        g[[40, 41, 70, 71, 100]] = 0.2
+        out = []
+        for rl in (0, refill):
+            C, v = ([1.0, 0.5], [1.0, 1.5]) if inst.tau.shape[0] == 2 else ([1.0], [1.0])
+            s = gpu_solver(inst, C, v, 64, 64, seed=9, cg_rtol=1e-12, refill_lanes=rl)
+            out.append([x.cpu().numpy() for x in s.adjoint(cuda_T(g), tol=1e-11, max_iter=500)])
+        for a_, b_ in zip(out[0], out[1]):
+            ok, err = normwise_close(a_, b_, 1e-9)
+            assert ok, err
+
+
 def test_adjoint_gradient_exact_for_frozen_map():
     # With draws fixed the steady state is affine in theta = (Q, T_w) (T_ref = 0), so
     # J = g . T* satisfies J = sum_k theta_k dJ/dtheta_k and central differences equal the
