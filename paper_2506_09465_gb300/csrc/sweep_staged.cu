@@ -1,5 +1,6 @@
-// Fast forward sweep: FP32 walk, persistent blocks, face tallies staged in shared memory
-// in fixed point. Same method and draws as the plain sweep
+// Fast forward sweep and adjoint re-trace: FP32 walk, persistent blocks (a pass-synchronous
+// kernel for 2D, a per-lane-refill kernel for every dimension), face tallies staged in
+// shared memory in fixed point. Same method and draws as the plain sweep
 // (arXiv 2506.09465 Sec. 3.1 steps (1)-(3), Sec. 3.2 null collisions); only the
 // arithmetic precision of the walk and the way tallies are accumulated differ.
 //
@@ -15,6 +16,12 @@
 //    absorbed minus emitted power, and the last-axis faces follow exactly by a prefix sum
 //    along each column (derive_last_axis_kernel);
 //  * in 3D the y-faces are tallied with global FP64 atomics;
+//  * 2D instances whose faces all fit the window use two-group tallies instead: a particle
+//    tallies only the faces normal to the axis it crosses less often, and each group's
+//    other faces follow from that group's own per-cell balance (derive_two_group_kernel,
+//    assemble_two_group_kernel);
+//  * a warp tallies the face items of the particles that ended together, each lane one
+//    contiguous chunk of the concatenated item lists;
 //  * nothing is tallied per particle for the walls: the power a wall emits enters through
 //    its faces deterministically (N particles of known weight per face), and the power it
 //    absorbs is its emission plus the outward net flux through its faces
