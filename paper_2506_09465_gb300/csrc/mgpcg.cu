@@ -437,6 +437,140 @@ __global__ void __launch_bounds__(NT) mgpcg_kernel(MGArgs A) {
   if (rank == 0 && threadIdx.x == 0) A.iters_out[k] = done ? it : -1;
 }
 
+// The same V-cycle for the FP32 iterates of mgpcg32_kernel: the finest level's right-hand
+// side and iterate are the CG's residual and preconditioned residual themselves (no copies;
+// the caller's last cluster barrier ordered the residual's writes).
+template <int NT, int CS>
+__device__ void vcycle_f32(const MGArgs& A, const InstMG& m, cg::cluster_group& cl, int rank, float* smem) {
+  const ClusterTeam all{rank};
+  const SoloTeam solo;
+  const int L = m.levels;
+  const int ls = solo_level(m);
+  for (int l = 0; l < ls; ++l) vdown<ClusterTeam, NT, CS>(A, m, l, global_view(A, m, l), global_view(A, m, l + 1), all, cl);
+  if (rank == 0) {
+    const LevelView top = solo_view(A, m, ls, ls, smem);
+    const float* gb = A.lb + m.off[ls];
+    for (long long i = threadIdx.x; i < m.nc[ls]; i += NT) top.b[i] = __ldcg(&gb[i]);
+    __syncthreads();
+    for (int l = ls; l < L - 1; ++l)
+      vdown<SoloTeam, NT, CS>(A, m, l, solo_view(A, m, l, ls, smem), solo_view(A, m, l + 1, ls, smem), solo, cl);
+    vcoarsest<SoloTeam, NT, CS>(A, m, solo_view(A, m, L - 1, ls, smem), solo, cl);
+    for (int l = L - 2; l >= ls; --l)
+      vup<SoloTeam, NT, CS>(A, m, l, solo_view(A, m, l, ls, smem), solo_view(A, m, l + 1, ls, smem), solo, cl);
+    float* gx = A.lx + m.off[ls];
+    for (long long i = threadIdx.x; i < m.nc[ls]; i += NT) gx[i] = top.x[i];
+  }
+  cl.sync();
+  for (int l = ls - 1; l >= 0; --l) vup<ClusterTeam, NT, CS>(A, m, l, global_view(A, m, l), global_view(A, m, l + 1), all, cl);
+}
+
+// PCG with FP32 iterates for tolerances far above FP32's rounding (the correction is an
+// inexact Newton step: its tolerance sets the cost, not the fixed point). The right-hand
+// side is scaled to unit norm (its norm in FP64), so the FP32 sums neither underflow nor
+// overflow; the stencil product uses the FP32 copy of the fine operator (the hierarchy's
+// finest level); dot products are FP32 per thread and FP64 across the cluster; the solution
+// is scaled back into the FP64 X. On GB300 FP64 arithmetic issues on a narrow pipe, so the
+// FP64 iterates' products and updates lengthen every phase of the iteration.
+template <int NT, int CS>
+__global__ void __launch_bounds__(NT, 1) mgpcg32_kernel(MGArgs A, float* V32) {
+  __shared__ double sh[4 * 32];
+  __shared__ double slot[8];
+  extern __shared__ float mg_smem[];
+  cg::cluster_group cl = cg::this_cluster();
+  const int rank = (int)cl.block_rank();
+  const int k = blockIdx.x / CS;
+  const InstMG& m = A.mg[k];
+  const long long off = m.cell_off, n = m.nc[0];
+  const long long chunk = (n + CS - 1) / CS, lo = rank * chunk, hi = min(n, lo + chunk);
+  float* R = A.lb + m.off[0];  // residual = the V-cycle's finest right-hand side
+  float* Z = A.lx + m.off[0];  // preconditioned residual = its finest iterate
+  float* X = V32 + 3 * off;
+  float* P = X + n;
+  float* Q = P + n;
+  const float *dg = A.ldiag + m.off[0], *cx = A.lcx + m.off[0], *cy = A.lcy + m.off[0], *cz = A.lcz + m.off[0];
+  ClusterRed<NT, CS> red{slot, 0};
+  double v[4];
+  v[0] = 0.0;
+  for (long long i = lo + threadIdx.x; i < hi; i += NT) {
+    const double bi = A.rhs[off + i];
+    v[0] += bi * bi;
+  }
+  red.sum(cl, v, 1, sh);
+  const double bb = v[0];
+  if (bb == 0.0) {
+    for (long long i = lo + threadIdx.x; i < hi; i += NT) A.X[off + i] = 0.0;
+    if (rank == 0 && threadIdx.x == 0) A.iters_out[k] = 0;
+    return;
+  }
+  const double bn = sqrt(bb), sc = 1.0 / bn;
+  for (long long i = lo + threadIdx.x; i < hi; i += NT) {
+    R[i] = (float)(A.rhs[off + i] * sc);
+    X[i] = 0.f;
+  }
+  cl.sync();
+  const double tol2 = A.rtol * A.rtol;  // of the unit-norm right-hand side
+  vcycle_f32<NT, CS>(A, m, cl, rank, mg_smem);
+  float f0 = 0.f;
+  for (long long i = lo + threadIdx.x; i < hi; i += NT) {
+    const float zi = Z[i];
+    P[i] = zi;
+    f0 += R[i] * zi;
+  }
+  v[0] = f0;
+  red.sum(cl, v, 1, sh);  // also orders the P writes before the first product
+  double rz = v[0];
+  int it = 0;
+  bool done = false;
+  while (it < A.maxit) {
+    ++it;
+    f0 = 0.f;
+    for (long long i = lo + threadIdx.x; i < hi; i += NT) {
+      const float q = level_apply<ClusterTeam>(dg, cx, cy, cz, P, m.n[0], m.dim, i, n);
+      Q[i] = q;
+      f0 += __ldcg(&P[i]) * q;
+    }
+    v[0] = f0;
+    red.sum(cl, v, 1, sh);
+    const double alpha = rz / v[0];
+    const float af = (float)alpha;
+    f0 = 0.f;
+    for (long long i = lo + threadIdx.x; i < hi; i += NT) {
+      X[i] += af * P[i];
+      const float ri = R[i] - af * Q[i];
+      R[i] = ri;
+      f0 += ri * ri;
+    }
+    v[0] = f0;
+    red.sum(cl, v, 1, sh);  // also orders the residual's writes before the V-cycle
+    if (v[0] <= tol2) {
+      done = true;
+      break;
+    }
+    vcycle_f32<NT, CS>(A, m, cl, rank, mg_smem);
+    // flexible (Polak-Ribiere) beta, as in the FP64 kernel
+    float f1 = 0.f;
+    f0 = 0.f;
+    for (long long i = lo + threadIdx.x; i < hi; i += NT) {
+      const float zi = Z[i];
+      f0 += R[i] * zi;
+      f1 += Q[i] * zi;
+    }
+    v[0] = f0;
+    v[1] = f1;
+    red.sum(cl, v, 2, sh);
+    const double beta = -alpha * v[1] / rz;
+    rz = v[0];
+    const float bf = (float)beta;
+    for (long long i = lo + threadIdx.x; i < hi; i += NT) P[i] = Z[i] + bf * P[i];
+    cl.sync();
+  }
+  for (long long i = lo + threadIdx.x; i < hi; i += NT) A.X[off + i] = (double)X[i] * bn;
+  if (rank == 0 && threadIdx.x == 0) A.iters_out[k] = done ? it : -1;
+}
+
+// Tolerances from here up run the FP32 iterates.
+constexpr double MG32_MIN_RTOL = 1e-5;
+
 constexpr int MG_NT = 512;
 constexpr int MG_CS = 8;
 
@@ -453,7 +587,10 @@ size_t mg_solo_smem_bytes(const std::vector<InstMG>& h_mg) {
 
 cudaError_t configure_mgpcg(Ctx* c, size_t smem) {
   c->mg_smem_bytes = smem;
-  return cudaFuncSetAttribute(mgpcg_kernel<MG_NT, MG_CS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  const cudaError_t e =
+      cudaFuncSetAttribute(mgpcg_kernel<MG_NT, MG_CS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(mgpcg32_kernel<MG_NT, MG_CS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
 }
 
 cudaError_t launch_mgpcg(const Ctx* c, const double* rhs, cudaStream_t s) {
@@ -497,6 +634,11 @@ cudaError_t launch_mgpcg(const Ctx* c, const double* rhs, cudaStream_t s) {
   attr[0].val.clusterDim.z = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
+  if (c->opt.cg_rtol >= MG32_MIN_RTOL) {
+    // FP32 x, p, q in the space of the FP64 r, p, q, z (4 n doubles >= 3 n floats)
+    float* v32 = reinterpret_cast<float*>(c->d_pcg + c->total_cells);
+    return cudaLaunchKernelEx(&cfg, mgpcg32_kernel<MG_NT, MG_CS>, a, v32);
+  }
   return cudaLaunchKernelEx(&cfg, mgpcg_kernel<MG_NT, MG_CS>, a);
 }
 

@@ -109,6 +109,29 @@ def test_newton_step_matches_direct_solve(orc, dim):
     assert ok, err
 
 
+@pytest.mark.parametrize("dim,n", [(1, (30,)), (2, (14, 11)), (2, (160, 128)), (3, (6, 5, 4))])
+def test_fp32_correction_solve_matches_direct_solve(orc, dim, n):
+    # Tolerances from 1e-5 up run the correction solve with FP32 iterates (the default 1e-3
+    # among them). Its error is the tolerance times the operator's condition, far above FP32
+    # rounding: at cg_rtol 1e-5 the correction agrees with the oracle's direct solve to 1e-3
+    # of its size, and the solver reports its iterations.
+    rng = np.random.default_rng(60 + dim)
+    inst = WL.random_instance(rng, dim, n, 2, (0.01, 0.4))
+    C, v = [1.0, 0.5], [1.0, 1.5]
+    N = 40 if inst.ncells < 1000 else 4
+    p = oracle_problem(inst, C, v, N, N)
+    T = rng.uniform(0, 1, inst.ncells)
+    r = orc.sweep(p, T, 0)
+    Th, _ = orc.macro(p, r.R, r.W)
+    T1, dT = orc.newton(p, T, Th, r.R)
+    s = gpu_solver(inst, C, v, N, N, precision=0, cg_rtol=1e-5)
+    gT = cuda_T(Th)
+    it = s.newton_step(cuda_T(T), gT, cuda_T(r.R.ravel()))
+    assert it > 0
+    ok, err = normwise_close(gT.cpu().numpy() - Th, T1 - Th, 1e-3)
+    assert ok, err
+
+
 @pytest.mark.parametrize("newton", [0, 1])
 def test_steady_fp64_matches_oracle(orc, newton):
     inst = WL.slab(40, 0.1, 1.0, -1.0).instances[0]
