@@ -256,6 +256,28 @@ iugkp_status iugkp_autotune(iugkp_ctx *ctx, const double *T_dev, unsigned epoch,
 iugkp_status iugkp_residual(iugkp_ctx *ctx, const double *T0_dev, const double *T1_dev, double *out_dev,
                             void *cuda_stream);
 
+/* FP32 walk and its FP64 replay (no counterpart in the paper: a precision choice). With FP32
+ * tracking and a staged tally mode, every decision of a particle's walk (the cell of each
+ * candidate, i.e. the faces crossed before it along each axis; whether the first wall comes
+ * before it; acceptance with probability tau_maj / tau) is taken in FP32 only when the FP32
+ * value lies farther from the decision's boundary than a bound on its difference from the
+ * FP64 walk's value. Otherwise the particle is left untallied at that point and, after the
+ * sweep, the FP64 walk (the arithmetic of IUGKP_TRACK_FP64) replays it and makes its remaining
+ * tallies. Real collisions, wall exits and event counts are therefore those of the FP64 walk;
+ * the W tally of a null candidate near a face may sit in the neighbouring cell, and face
+ * tallies near a cell corner may swap between two adjacent faces (a few particle weights).
+ * iugkp_replayed: the number of particles the FP64 walk replayed in the context's last staged
+ *   sweep or adjoint re-trace; synchronises cuda_stream.
+ * iugkp_check_fp32_walk: measures on the current device, over every uniform the walk can draw,
+ *   the accuracy of the FP32 operations the bound relies on, and writes
+ *   out6[0] the largest error of the fast logarithm as a fraction of its allowance (<= 1);
+ *   out6[1..4] the largest relative errors, in units of 2^-23, of sincospif, of
+ *   sqrtf(1 - mu^2), of sqrtf(u) and sqrtf(1 - u), and of the fast division;
+ *   out6[5] the relative bound those imply for the face-count decision, as a fraction of
+ *   the one the walk uses (<= 1). Synchronous; errors in iugkp_last_error(NULL). */
+iugkp_status iugkp_replayed(iugkp_ctx *ctx, long long *n_out, void *cuda_stream);
+iugkp_status iugkp_check_fp32_walk(double *out6);
+
 /* Steady driver: from the initial T_inout_dev, repeats sweep -> macro -> [Newton]
  * until res = ||T^{n+1} - T^n|| / max(||T^{n+1}||, dT_ref sqrt(ncells)) <= tol over
  * all instances (dT_ref = the wall-temperature span, or max |T_w|, or 1).

@@ -72,6 +72,8 @@ SIGNATURES = {
     "iugkp_persistent_step": (_i, [_vp, _vp, _u, _vp, _vp, _vp, _vp, ctypes.POINTER(ctypes.c_longlong), _vp]),
     "iugkp_solve_steady": (_i, [_vp, _vp, _d, _i, ctypes.POINTER(_i), ctypes.POINTER(_d), _vp]),
     "iugkp_adjoint": (_i, [_vp, _vp, _vp, _d, _i, _vp, _vp, _vp, _vp]),
+    "iugkp_replayed": (_i, [_vp, ctypes.POINTER(_ll), _vp]),
+    "iugkp_check_fp32_walk": (_i, [ctypes.POINTER(_d)]),
     "iugkp_diffusion_solve_noalloc": (_i, [ctypes.POINTER(Grid), _vp, _d, _vp, _vp, _d, _i, ctypes.POINTER(_i), _vp]),
 }
 

@@ -116,6 +116,33 @@ __global__ void __launch_bounds__(256) adjoint_kernel(SweepArgs A) {
     adjoint_particle<Real, DIM>(A, pid, A.err);
 }
 
+// FP64 re-trace of the particles the staged adjoint re-trace deferred (a decision of its
+// FP32 walk within rounding of the FP64 walk's; the forward sweep defers the same particles).
+// Entry x: the staged index, particle q of emitter e taken q-major within its group.
+template <int DIM>
+__global__ void __launch_bounds__(128) adjoint_replay_kernel(SweepArgs A, const uint2* defer, const unsigned* defer_n,
+                                                             unsigned defer_cap) {
+  const unsigned n = min(*defer_n, defer_cap);
+  for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const unsigned pid = defer[i].x;
+    const Group G = A.groups[find_group(A.groups, A.n_groups, (long long)pid)];
+    const unsigned local = pid - (unsigned)G.first_particle;
+    const int q = (int)(local / (unsigned)G.n_emitters);
+    const int e = (int)(local - (unsigned)q * (unsigned)G.n_emitters);
+    adjoint_particle<double, DIM>(A, G.first_particle + (long long)e * G.per_emitter + q, A.err);
+  }
+}
+
+cudaError_t launch_adjoint_replay(const Ctx* c, const SweepArgs& a, cudaStream_t s) {
+  const int blocks = c->sm_count * 4;
+  switch (c->dim) {
+    case 1: adjoint_replay_kernel<1><<<blocks, 128, 0, s>>>(a, c->d_defer, c->d_defer_n, c->defer_cap); break;
+    case 2: adjoint_replay_kernel<2><<<blocks, 128, 0, s>>>(a, c->d_defer, c->d_defer_n, c->defer_cap); break;
+    default: adjoint_replay_kernel<3><<<blocks, 128, 0, s>>>(a, c->d_defer, c->d_defer_n, c->defer_cap); break;
+  }
+  return cudaGetLastError();
+}
+
 template <typename Real, int DIM>
 static cudaError_t launch_adj(const Ctx* c, const SweepArgs& a, cudaStream_t s) {
   long long blocks = (a.total_particles + 255) / 256;

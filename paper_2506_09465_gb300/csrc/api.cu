@@ -48,6 +48,31 @@ iugkp_status ensure_k32(Ctx* c);
 // Multiplier of the device's exact division by d (>= 1): M = floor((2^32 - 1) / d).
 unsigned div_magic(int d) { return (unsigned)(0xFFFFFFFFull / (unsigned long long)std::max(1, d)); }
 
+// Largest acceptance ratio (FP32) over each cell and its neighbours across faces, edges and
+// corners, per instance and band: a candidate whose acceptance draw exceeds it is rejected
+// whichever of those cells it lies in.
+std::vector<float> neighbour_max_ratio(const Ctx* c, const std::vector<float>& r32) {
+  std::vector<float> out(r32.size());
+  for (const InstDesc& in : c->h_inst) {
+    const int nx = in.n[0], ny = in.n[1], nz = in.n[2];
+    for (int b = 0; b < c->nb; ++b) {
+      const float* r = r32.data() + in.bc_off + (size_t)b * in.ncells;
+      float* o = out.data() + in.bc_off + (size_t)b * in.ncells;
+      for (int z = 0; z < nz; ++z)
+        for (int y = 0; y < ny; ++y)
+          for (int x = 0; x < nx; ++x) {
+            float m = 0.f;
+            for (int k = std::max(z - 1, 0); k <= std::min(z + 1, nz - 1); ++k)
+              for (int j = std::max(y - 1, 0); j <= std::min(y + 1, ny - 1); ++j)
+                for (int i = std::max(x - 1, 0); i <= std::min(x + 1, nx - 1); ++i)
+                  m = std::max(m, r[i + (size_t)nx * (j + (size_t)ny * k)]);
+            o[x + (size_t)nx * (y + (size_t)ny * z)] = m;
+          }
+    }
+  }
+  return out;
+}
+
 // Largest-remainder split of N over weights r (r > 0, N >= nb): one particle per band
 // first, the remaining N - nb in proportion to r, leftovers to the largest fractional
 // parts (lower band first on ties).
@@ -100,7 +125,7 @@ iugkp_status upload(Ctx* c, T** p, const std::vector<T>& h) {
 }
 
 void free_all(Ctx* c) {
-  void* ptrs[] = {c->d_vtm32, c->d_inst, c->d_groups_all, c->d_groups_fwd, c->d_coef, c->d_ratio64, c->d_ratio32, c->d_taumaj,
+  void* ptrs[] = {c->d_vtm32, c->d_inst, c->d_groups_all, c->d_groups_fwd, c->d_coef, c->d_ratio64, c->d_ratio32, c->d_ratio_nb32, c->d_taumaj,
                   c->d_v, c->d_wcoef, c->d_wallT, c->d_srcshift, c->d_source, c->d_m, c->d_Vm, c->d_invVm, c->d_VC,
                   c->d_theta, c->d_theta_m, c->d_diag, c->d_cx, c->d_cy, c->d_cz, c->d_pcg, c->d_work, c->d_T2,
                   c->d_R, c->d_W, c->d_F, c->d_wall, c->d_red, c->d_counters, c->d_work_counter, c->d_err,
@@ -111,7 +136,7 @@ void free_all(Ctx* c) {
                   c->d_all_group_mag, c->d_R32, c->d_W32, c->d_F32, c->d_m2, c->d_wallTf,
                   c->d_pslot_off, c->d_phome_off, c->d_pnband, c->d_pnwall, c->d_px, c->d_pband, c->d_phome,
                   c->d_pdue, c->d_pcount, c->d_phome_w, c->d_wemit, c->d_DY, c->d_EY, c->d_GX, c->d_Fd,
-                  c->d_all_real};
+                  c->d_all_real, c->d_defer, c->d_defer_n};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (c->h_pinned) cudaFreeHost(c->h_pinned);
@@ -597,6 +622,10 @@ iugkp_status iugkp_create_batch(int n, const iugkp_grid* g, const double* const*
   UP(c->d_ratio64, r64);
   UP(c->d_ratio32, r32);
   {
+    std::vector<float> rnb = neighbour_max_ratio(c, r32);
+    UP(c->d_ratio_nb32, rnb);
+  }
+  {
     // bands whose every cell has tau = tau_maj: every candidate is real (the uniform, below
     // 1, always passes the test against a ratio of exactly 1)
     std::vector<int> all_real((size_t)n * nb, 1);
@@ -685,6 +714,19 @@ iugkp_status iugkp_create_batch(int n, const iugkp_grid* g, const double* const*
   if ((s = dalloc(c, &c->d_W, (size_t)nb * cell_off)) != IUGKP_OK) return bail(s);
   if ((s = dalloc(c, &c->d_F, face_off)) != IUGKP_OK) return bail(s);
   if ((s = dalloc(c, &c->d_wemit, (size_t)nb * cell_off)) != IUGKP_OK) return bail(s);
+  {
+    // queue of the particles the FP32 walk leaves to the FP64 replay: about 1e-4 of them on
+    // the workloads measured; room for 1/32 of every emitter's particles
+    const long long cap = std::min<long long>(c->total_particles / 32 + 65536, 1ll << 31);
+    c->defer_cap = (unsigned)cap;
+    if ((s = dalloc(c, &c->d_defer, (size_t)cap)) != IUGKP_OK) return bail(s);
+    if ((s = dalloc(c, &c->d_defer_n, 1)) != IUGKP_OK) return bail(s);
+    if (cudaMemset(c->d_defer_n, 0, sizeof(unsigned)) != cudaSuccess) {
+      cudaGetLastError();
+      fail(c, IUGKP_ECUDA, "clear of the replay queue");
+      return bail(IUGKP_ECUDA);
+    }
+  }
   if (c->dim == 2) {
     if ((s = dalloc(c, &c->d_DY, cell_off)) != IUGKP_OK) return bail(s);
     if ((s = dalloc(c, &c->d_EY, (size_t)c->total_bfaces)) != IUGKP_OK) return bail(s);
@@ -759,6 +801,7 @@ SweepArgs base_args(Ctx* c) {
   a.coef = c->d_coef;
   a.ratio64 = c->d_ratio64;
   a.ratio32 = c->d_ratio32;
+  a.ratio_nb32 = c->d_ratio_nb32;
   a.all_real = c->d_all_real;
   a.taumaj = c->d_taumaj;
   a.vtm32 = c->d_vtm32;
@@ -786,6 +829,8 @@ iugkp_status check_device(Ctx* c, cudaStream_t s) {
     CK(cudaMemsetAsync(c->d_err, 0, sizeof(int), s), "error reset");
     if (e & ERR_BUDGET) return fail(c, IUGKP_EBUDGET, "a particle exceeded the step budget and was dropped");
     if (e & ERR_PCG) return fail(c, IUGKP_ENOCONV, "PCG reached cg_maxit before cg_rtol");
+    if (e & ERR_DEFER)
+      return fail(c, IUGKP_EDEVICE, "more particles than the replay queue holds needed the FP64 walk (queue overflow)");
     return fail(c, IUGKP_EDEVICE, "device-side check failed (code " + std::to_string(e) + ")");
   }
   return IUGKP_OK;
@@ -1031,6 +1076,36 @@ iugkp_status iugkp_residual(iugkp_ctx* ctx, const double* T0_dev, const double* 
   Ctx* c = &ctx->c;
   if (!T0_dev || !T1_dev || !out_dev) return fail(c, IUGKP_EINVAL, "NULL device pointer");
   CK(launch_residual(c, T0_dev, T1_dev, 0.0, out_dev, (cudaStream_t)cuda_stream), "residual");
+  return IUGKP_OK;
+}
+
+iugkp_status iugkp_replayed(iugkp_ctx* ctx, long long* n_out, void* cuda_stream) {
+  if (!ctx || !n_out) return IUGKP_EINVAL;
+  Ctx* c = &ctx->c;
+  cudaStream_t s = (cudaStream_t)cuda_stream;
+  unsigned* h = reinterpret_cast<unsigned*>(c->h_pinned + 14);
+  CK(cudaMemcpyAsync(h, c->d_defer_n, sizeof(unsigned), cudaMemcpyDeviceToHost, s), "replay count readback");
+  CK(cudaStreamSynchronize(s), "stream synchronise");
+  *n_out = (long long)*h;
+  return IUGKP_OK;
+}
+
+iugkp_status iugkp_check_fp32_walk(double* out6) {
+  Ctx* c = nullptr;
+  if (!out6) return fail(c, IUGKP_EINVAL, "NULL output");
+  unsigned long long* d = nullptr;
+  CK(cudaMalloc((void**)&d, 5 * sizeof(unsigned long long)), "check buffer");
+  unsigned long long h[5];
+  cudaError_t e = launch_walk_bounds(d, nullptr);
+  if (e == cudaSuccess) e = cudaMemcpy(h, d, sizeof(h), cudaMemcpyDeviceToHost);
+  cudaFree(d);
+  if (e != cudaSuccess) return cuda_fail(c, e, "FP32 walk bound check");
+  for (int k = 0; k < 5; ++k) {
+    double x;
+    std::memcpy(&x, &h[k], sizeof(x));
+    out6[k] = x;
+  }
+  out6[5] = walk_bound_fraction(out6);
   return IUGKP_OK;
 }
 

@@ -27,6 +27,7 @@ struct SweepArgs {
   const double* coef;      // [bc] C_b V / (tau N_b): weight per unit emission temperature
   const double* ratio64;   // [bc] tau_maj / tau (acceptance probability of a candidate)
   const float* ratio32;
+  const float* ratio_nb32; // [bc] largest ratio32 over the cell and its neighbours
   const int* all_real;     // [inst * nb] 1 where tau = tau_maj in every cell (every candidate real)
   const double* taumaj;    // [inst * nb] majorant tau per instance and band
   const double* v;         // [nb] group speed
@@ -78,6 +79,7 @@ struct Ctx {
   double* d_coef = nullptr;
   double* d_ratio64 = nullptr;
   float* d_ratio32 = nullptr;
+  float* d_ratio_nb32 = nullptr; // [nb * cells] largest FP32 ratio over each cell's neighbourhood
   int* d_all_real = nullptr;     // [inst * nb] tau = tau_maj in every cell of the band
   bool all_real_all = false;     // ... in every instance and band
   double* d_taumaj = nullptr;
@@ -172,6 +174,10 @@ struct Ctx {
   double all_cost_total = 0.0;
   unsigned* d_all_group_mag = nullptr;
   int adj_blocks_per_sm = 1;
+  // particles the staged FP32 walk left to the FP64 replay (sweep and adjoint re-trace)
+  uint2* d_defer = nullptr;
+  unsigned* d_defer_n = nullptr;
+  unsigned defer_cap = 0;
   unsigned* d_mag = nullptr;         // [n_inst * 5]: division magics of n_x, n_y, n(o1) for walls normal to x, y, z
   int staged_cap = 0;           // x-faces per shared-memory window
   int staged_blocks_per_sm = 1;
@@ -202,6 +208,10 @@ cudaError_t launch_axpy_grad(const Ctx* c, const double* at, const double* g, do
 cudaError_t launch_sweep_staged(const Ctx* c, const SweepArgs& a, cudaStream_t s);
 cudaError_t configure_staged(Ctx* c);
 cudaError_t launch_adjoint_staged(const Ctx* c, const SweepArgs& a, cudaStream_t s);
+cudaError_t launch_replay(const Ctx* c, const SweepArgs& a, const StagedArgs& S, cudaStream_t s);
+cudaError_t launch_adjoint_replay(const Ctx* c, const SweepArgs& a, cudaStream_t s);
+cudaError_t launch_walk_bounds(unsigned long long* out, cudaStream_t s);
+double walk_bound_fraction(const double* measured);
 cudaError_t launch_mgpcg(const Ctx* c, const double* rhs, cudaStream_t s);
 size_t mg_solo_smem_bytes(const std::vector<InstMG>& h_mg);
 cudaError_t configure_mgpcg(Ctx* c, size_t smem);

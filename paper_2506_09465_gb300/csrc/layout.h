@@ -42,6 +42,6 @@ struct Group {
 enum { CNT_FLIGHTS = 0, CNT_CANDIDATES, CNT_REAL, CNT_CROSSINGS, CNT_WALL_EXITS, CNT_DROPPED, CNT_N };
 
 // Device error bits.
-enum { ERR_BUDGET = 1, ERR_RANGE = 2, ERR_PCG = 4, ERR_WAIT = 8 };
+enum { ERR_BUDGET = 1, ERR_RANGE = 2, ERR_PCG = 4, ERR_WAIT = 8, ERR_DEFER = 16 };
 
 }  // namespace iugkp

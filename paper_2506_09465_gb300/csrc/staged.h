@@ -41,6 +41,13 @@ struct StagedArgs {
                                   // flux: + on the low walls, - on the high walls)
   double* GX;                     // [total_bfaces] exits of the x-group through the low y-wall and
                                   // of the y-group through the low x-wall (signed flux)
+  // Particles whose FP32 walk lies within rounding of a decision of the FP64 walk are left
+  // untallied and replayed by the FP64 walk after the sweep (replay_kernel): entry
+  // {forward index, (candidates already tallied << 1) | y-group}.
+  uint2* defer;                   // [defer_cap]
+  unsigned* defer_n;              // entries pushed by this sweep (beyond defer_cap: overflow)
+  unsigned defer_cap;
+  int* err;                       // device error word (ERR_DEFER on overflow)
 };
 
 }  // namespace iugkp

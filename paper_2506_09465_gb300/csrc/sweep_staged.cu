@@ -28,6 +28,8 @@
 //    (boundary_emission_kernel, wall_absorbed_kernel).
 #include <cuda_runtime.h>
 
+#include <algorithm>
+
 #include "device.cuh"
 #include "internal.h"
 #include "staged.h"
@@ -103,6 +105,122 @@ __device__ __forceinline__ float axis_exit(int i, int s, int n, float t, float d
 }
 
 __device__ __forceinline__ int clampi(int v, int n) { return min(max(v, 0), n - 1); }
+
+// ---- FP32 decisions checked against the FP64 walk ----
+// The FP32 walk and the FP64 walk follow each particle with the same draws, so their path
+// lengths differ by rounding only, and a decision taken in FP32 is the FP64 walk's unless the
+// FP32 value lies within a bound of the decision's boundary: a face (the count of faces before
+// a candidate along an axis, hence its cell), the first wall (a candidate or an absorption),
+// the acceptance ratio. A particle with such a decision is not tallied further: it goes to a
+// queue that the FP64 walk replays after the sweep (replay_kernel, adjoint_replay_kernel).
+// Path-length bounds, FP32 against FP64:
+//  * a face count's quotient u = (D - t) / d, times d: TIE_REL (D + d) + eD, TIE_REL covering
+//    the rounding of the direction (sqrtf, sincospif, products), cell size, first-face
+//    distance, quotient (__fdividef) and difference, about 2^-19.4 in all, taken as 2^-18;
+//    the wall distance tex likewise within TIE_REL tex;
+//  * eD bounds |D32 - D64|: per flight TIE_LOG_ABS v tau_maj + TIE_LOG_REL l for the fast
+//    logarithm (absolute 2^-21.41 on [0.5, 2], 3 ulp elsewhere), the FP32 v tau_maj and the
+//    product's rounding, plus TIE_SUM D for each addition to D.
+// The acceptance ratio in FP32 is within 2^-24 of the FP64 ratio (both below 1).
+constexpr float TIE_REL = 0x1p-18f;
+constexpr float TIE_LOG_ABS = 0x1p-21f;
+constexpr float TIE_LOG_REL = 0x1p-19f;
+constexpr float TIE_SUM = 0x1p-23f;
+constexpr float TIE_ACC = 0x1p-24f;
+
+// Tie bits of one axis for the count n = faces_before(D, t, d): bit sh when D lies within the
+// bound (base = TIE_REL D + eD, plus TIE_REL d) below a face, so that the FP64 walk may count
+// one face more; bit sh + 1 when within it above one (one fewer). None when d = inf (NaN).
+__device__ __forceinline__ unsigned tie_bits(float D, float t, float d, float base, int n, int sh) {
+  const float u = __fdividef(D - t, d);
+  const float fr = small_int_float(n) - u;  // up to the next face, in cells: [0, 1]
+  const float tol = fmaf(TIE_REL, d, base);
+  if (fr * d <= tol) return 1u << sh;
+  if ((1.f - fr) * d <= tol && n > 0) return 2u << sh;
+  return 0u;
+}
+
+// faces_before and tie_bits together (one quotient): the count, with its tie bits or'd into tie.
+__device__ __forceinline__ int count_tie(float D, float t, float d, float base, unsigned& tie, int sh) {
+  const float u = __fdividef(D - t, d);
+  const float c = __fadd_ru(fmaxf(u, 0.f), 8388608.f);  // 2^23 + ceil(max(u, 0))
+  const float fr = (c - 8388608.f) - u;
+  const int n = __float_as_int(c) - 0x4B000000;
+  const float tol = fmaf(TIE_REL, d, base);
+  if (fr * d <= tol) tie |= 1u << sh;
+  else if ((1.f - fr) * d <= tol && n > 0) tie |= 2u << sh;
+  return n;
+}
+
+// Axis a's bit of `hit` when the count one more than n reaches the wall (m faces to it).
+__device__ __forceinline__ unsigned tie_hits_wall(unsigned tie, int a, int n, int m) {
+  return ((tie >> (2 * a)) & 1u) && n + 1 >= m ? 1u << (2 * a) : 0u;
+}
+
+// A candidate flagged near faces (tie, two bits per axis) may lie, in the FP64 walk, in a cell
+// across the flagged faces. True when every such cell rejects it by more than the ratio's
+// rounding: the FP64 walk then goes on identically, and only the cell of this candidate's W
+// may differ. False when an alternative lies beyond a wall (hit) or any cell may accept.
+// st_a: the cell index step of one more face along axis a (s_a times the axis stride).
+__device__ __forceinline__ bool all_reject(const float* ratio, int ncells, int cell, unsigned tie, unsigned hit, int st0,
+                                           int st1, int st2, float u) {
+  if (tie & hit) return false;
+#pragma unroll 1
+  for (unsigned k = 0; k < 8u; ++k) {
+    int c = cell;
+    bool ok = true;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      if (!((k >> a) & 1u)) continue;
+      const unsigned t = (tie >> (2 * a)) & 3u;
+      const int st = a == 0 ? st0 : (a == 1 ? st1 : st2);
+      ok = ok && t != 0u;
+      c += t == 1u ? st : -st;
+    }
+    if (!ok) continue;
+    if (c < 0 || c >= ncells || !(u - ratio[c] >= TIE_ACC)) return false;
+  }
+  return true;
+}
+
+// Queues a particle for the FP64 replay: forward index and (candidates tallied << 1) | group.
+__device__ __forceinline__ void defer_particle(const StagedArgs& S, unsigned pid, unsigned meta) {
+  const unsigned i = atomicAdd(S.defer_n, 1u);
+  if (i < S.defer_cap) S.defer[i] = make_uint2(pid, meta);
+  else atomicOr(S.err, ERR_DEFER);
+}
+
+enum { CAND_NULL = 0, CAND_REAL = 1, CAND_DEFER = 2 };
+
+// Outcome of the candidate at path length f.D, whose face counts fb and cell the caller took
+// in FP32 (the first wall lies beyond it by more than the bound, so it is a candidate for the
+// FP64 walk too): CAND_NULL or CAND_REAL when the FP64 walk decides the same, CAND_DEFER
+// otherwise. A candidate whose acceptance draw exceeds the largest ratio of its cell's
+// neighbourhood (by more than the ratio's rounding) is rejected wherever it lies, and needs no
+// face test; its W may sit in the neighbouring cell. ub: the acceptance word; sy, sz: cell
+// index steps along y and z.
+// all_real: every candidate of the band is real, and tie holds the counts' tie bits already
+// (count_tie); otherwise they are found here when needed.
+template <int DIM>
+__device__ __forceinline__ int candidate_outcome(const SweepArgs& A, long long bcbase, int ncells, const PW& f,
+                                                 float base, int fb0, int fb1, int fb2, int cell, bool all_real,
+                                                 unsigned tie, uint32_t ub, int n0, int n1, int n2, int sy, int sz) {
+  if (all_real) return tie ? CAND_DEFER : CAND_REAL;
+  const float ua = word_uniform<float>(ub);
+  if (ua - A.ratio_nb32[bcbase + cell] >= TIE_ACC) return CAND_NULL;
+  tie = tie_bits(f.D, f.t0, f.d0, base, fb0, 0);
+  if (DIM >= 2) tie |= tie_bits(f.D, f.t1, f.d1, base, fb1, 2);
+  if (DIM == 3) tie |= tie_bits(f.D, f.t2, f.d2, base, fb2, 4);
+  const float ra = A.ratio32[bcbase + cell];
+  if (tie) {
+    unsigned hit = tie_hits_wall(tie, 0, fb0, faces_to_wall(f.i0, f.s0, n0));
+    if (DIM >= 2) hit |= tie_hits_wall(tie, 1, fb1, faces_to_wall(f.i1, f.s1, n1));
+    if (DIM == 3) hit |= tie_hits_wall(tie, 2, fb2, faces_to_wall(f.i2, f.s2, n2));
+    if (!all_reject(A.ratio32 + bcbase, ncells, cell, tie, hit, f.s0, f.s1 * sy, f.s2 * sz, ua)) return CAND_DEFER;
+  }
+  if (fabsf(ua - ra) < TIE_ACC) return CAND_DEFER;
+  return ua < ra ? CAND_REAL : CAND_NULL;
+}
 
 }  // namespace
 
@@ -230,7 +348,7 @@ __device__ __forceinline__ bool staged_emit(const SweepArgs& A, const StagedArgs
     const float mu = 2.f * u_mu - 1.f;
     sx = mu;
     if (DIM >= 2) {
-      const float sn = sqrtf(1.f - mu * mu);
+      const float sn = sqrtf(fmaf(-mu, mu, 1.f));  // 1 - mu^2 with one rounding
       float sp, cp;
       sincospif(2.f * u_phi, &sp, &cp);
       sy = sn * cp;
@@ -325,7 +443,7 @@ __device__ __forceinline__ bool staged_emit(const SweepArgs& A, const StagedArgs
   }
   uint32_t ua;
   st.next_pair(ua, ub);
-  f.D = -__logf(word_uniform<float>(ua)) * A.vtm32[(long long)k * A.nb + b];
+  f.D = __fmul_rn(-__logf(word_uniform<float>(ua)), A.vtm32[(long long)k * A.nb + b]);
   return true;
 }
 
@@ -441,6 +559,9 @@ __global__ void __launch_bounds__(STAGED_NT, 1) sweep_staged_kernel(SweepArgs A,
     int emitter = 0;        // adjoint: gather target of the lane's particle
     int acc_slot = 0;       // adjoint: wall slot of the pending per-lane wall sum
     double acc = 0.0;
+    float eD = 0.f;         // bound of |D - D_fp64| of the lane's particle
+    int kc = 0;             // its candidates tallied so far
+    unsigned pid = 0;       // its forward (or adjoint) index
     for (;;) {
       // ---- refill idle lanes together ----
       const unsigned dead = __ballot_sync(0xffffffffu, !alive);
@@ -473,6 +594,9 @@ __global__ void __launch_bounds__(STAGED_NT, 1) sweep_staged_kernel(SweepArgs A,
             qwx = (unsigned)(((two && f.d0 < f.d1) ? f.s1 : f.s0) > 0 ? qw : -qw);
             vtm = A.vtm32[(long long)k * A.nb + band];
             bcbase = bc_off + (long long)band * ncells;
+            eD = fmaf(f.D, TIE_LOG_REL, vtm * TIE_LOG_ABS);
+            kc = 0;
+            pid = rbeg + rank;
           }
         }
         rbeg += take;
@@ -487,23 +611,47 @@ __global__ void __launch_bounds__(STAGED_NT, 1) sweep_staged_kernel(SweepArgs A,
       // draws the next flight length and the particle goes on in the same direction ----
       int nitem = 0;  // cooperative tallies: face items of the lane's particle ended in this pass
       if (alive && !tally) {
-        bool ended = false, wall_exit = false;
+        bool ended = false, wall_exit = false, deferred = false;
+        const bool all_real = A.all_real[(long long)k * A.nb + band] != 0;
 #pragma unroll 1
         for (int it = 0; it < S.walk_k; ++it) {
-          if (f.tex < f.D) {  // the segment reaches a wall first: absorbed there
-            cnt.v[CNT_WALL_EXITS] += 1;
+          // a decision within rounding of the FP64 walk's defers the particle to the FP64 replay
+          const float base = fmaf(TIE_REL, f.D, eD);
+          if (f.D - f.tex > base) {  // the segment reaches a wall first: absorbed there
             ended = wall_exit = true;
             break;
           }
-          cnt.v[CNT_CANDIDATES] += 1;
-          int cell = clampi(f.i0 + f.s0 * faces_before(f.D, f.t0, f.d0), n0);
-          if (DIM >= 2) cell += sy_cell * clampi(f.i1 + f.s1 * faces_before(f.D, f.t1, f.d1), n1);
-          if (DIM == 3) cell += sz_cell * clampi(f.i2 + f.s2 * faces_before(f.D, f.t2, f.d2), n2);
+          if (f.tex - f.D <= fmaf(TIE_REL, f.tex, eD)) {  // at the first wall within rounding
+            ended = deferred = true;
+            break;
+          }
+          unsigned tie = 0;  // tie bits of the counts, found with them for all-real bands
+          int fb0, fb1 = 0, fb2 = 0;
+          if (all_real) {
+            fb0 = count_tie(f.D, f.t0, f.d0, base, tie, 0);
+            if (DIM >= 2) fb1 = count_tie(f.D, f.t1, f.d1, base, tie, 2);
+            if (DIM == 3) fb2 = count_tie(f.D, f.t2, f.d2, base, tie, 4);
+          } else {
+            fb0 = faces_before(f.D, f.t0, f.d0);
+            if (DIM >= 2) fb1 = faces_before(f.D, f.t1, f.d1);
+            if (DIM == 3) fb2 = faces_before(f.D, f.t2, f.d2);
+          }
+          int cell = clampi(f.i0 + f.s0 * fb0, n0);
+          if (DIM >= 2) cell += sy_cell * clampi(f.i1 + f.s1 * fb1, n1);
+          if (DIM == 3) cell += sz_cell * clampi(f.i2 + f.s2 * fb2, n2);
           const long long ci = bcbase + cell;
+          const int oc = candidate_outcome<DIM>(A, bcbase, ncells, f, base, fb0, fb1, fb2, cell, all_real, tie, ub, n0,
+                                                n1, n2, sy_cell, sz_cell);
+          if (oc == CAND_DEFER) {
+            ended = deferred = true;
+            break;
+          }
+          cnt.v[CNT_CANDIDATES] += 1;
+          ++kc;
           // W collects w here; the sweep scales it by tau_maj afterwards (scale_by_taumaj)
           if (!ADJ && K32 && S.W32) tally_k32(&S.W32[ci], w);
           else if (!ADJ && !K32 && A.W) atomicAdd(&A.W[ci], w);
-          if (word_uniform<float>(ub) < A.ratio32[ci]) {
+          if (oc == CAND_REAL) {
             cnt.v[CNT_REAL] += 1;
             if (ADJ) {
               const long long gc = in.cell_off + cell;
@@ -519,9 +667,16 @@ __global__ void __launch_bounds__(STAGED_NT, 1) sweep_staged_kernel(SweepArgs A,
             ended = true;
             break;
           }
-          uint32_t ua;
-          st.next_pair(ua, ub);
-          f.D += -__logf(word_uniform<float>(ua)) * vtm;
+          uint32_t uw;
+          st.next_pair(uw, ub);
+          const float ell = __fmul_rn(-__logf(word_uniform<float>(uw)), vtm);
+          f.D = __fadd_rn(f.D, ell);
+          eD = fmaf(f.D, TIE_SUM, fmaf(ell, TIE_LOG_REL, eD + vtm * TIE_LOG_ABS));
+        }
+        if (deferred) {
+          defer_particle(S, pid, ADJ ? 0u : (((unsigned)kc << 1) | ((two && f.d0 < f.d1) ? 1u : 0u)));
+          ended = false;
+          alive = false;
         }
         if (ended) {
           // interior faces crossed before the end, per axis; on the exit axis the wall face
@@ -534,92 +689,113 @@ __global__ void __launch_bounds__(STAGED_NT, 1) sweep_staged_kernel(SweepArgs A,
             const float e2 = DIM == 3 ? axis_exit(f.i2, f.s2, n2, f.t2, f.d2) : INFINITY;
             ex = (e0 <= e1 && e0 <= e2) ? 0 : (e1 <= e2 ? 1 : 2);
           }
+          // at a wall, the faces of the other axes crossed before it: a count within rounding
+          // of the FP64 walk's (the segment leaves near a cell corner) defers the particle
+          unsigned tie = 0;
+          const float bx = TIE_REL * f.tex;
           const int m0 = faces_to_wall(f.i0, f.s0, n0);
-          const int c0 = ex == 0 ? m0 - 1 : min(faces_before(L, f.t0, f.d0), m0 - 1);
-          int c1 = 0, c2 = 0, m1 = 1;
+          int c0 = m0 - 1, c1 = 0, c2 = 0, m1 = 1;
+          if (ex != 0) {
+            const int q = count_tie(L, f.t0, f.d0, bx, tie, 0);
+            c0 = min(q, m0 - 1);
+          }
           if (DIM >= 2) {
             m1 = faces_to_wall(f.i1, f.s1, n1);
-            c1 = ex == 1 ? m1 - 1 : min(faces_before(L, f.t1, f.d1), m1 - 1);
+            c1 = m1 - 1;
+            if (ex != 1) {
+              const int q = count_tie(L, f.t1, f.d1, bx, tie, 2);
+              c1 = min(q, m1 - 1);
+            }
           }
           if (DIM == 3) {
             const int m2 = faces_to_wall(f.i2, f.s2, n2);
-            c2 = ex == 2 ? m2 - 1 : min(faces_before(L, f.t2, f.d2), m2 - 1);
+            c2 = m2 - 1;
+            if (ex != 2) {
+              const int q = count_tie(L, f.t2, f.d2, bx, tie, 4);
+              c2 = min(q, m2 - 1);
+            }
           }
-          cnt.v[CNT_CROSSINGS] += c0 + c1 + c2;
-          if (DIM == 2 && (two || wfull)) {
-            // Face items k = 0 .. kend-1 along the tallied axis p (the other axis: q). Item k
-            // is the face index a0 + k sp + sq min(ceil(u0 + k r), lim): the k-th face normal
-            // to p, in the row (or column) given by the faces normal to q crossed before it,
-            // ceil(u0 + k r) with u0 = (t_p - t_q) / d_q and r = d_p / d_q, at most lim.
-            const bool yg = two && f.d0 < f.d1;
-            int a0, sp, sq, lim;
-            float u0, r;
-            if (!yg) {
-              // exit through the low y-wall: the one face normal to y this group tallies
-              if (ex == 1 && f.s1 < 0) {
-                const int col = f.i0 + f.s0 * c0;
-                if (two) atomicAdd(&S.GX[in.bface_off + in.wface_off[2] + col], -w);
-                else if (K32) tally_k32(&S.F32[face_off + fax1 + col], -w);
-                else atomicAdd(&A.F[face_off + fax1 + col], -w);
-              }
-              kend = c0 + (ex == 0 ? 1 : 0);
-              const bool flat = !(f.d1 < INFINITY);
-              u0 = flat ? -1.f : __fdividef(f.t0 - f.t1, f.d1);
-              r = flat ? 0.f : __fdividef(f.d0, f.d1);
-              lim = m1 - 1;
-              a0 = (f.s0 > 0 ? f.i0 + 1 : f.i0) + sy_xf * f.i1;
-              sp = f.s0;
-              sq = f.s1 * sy_xf;
-            } else {
-              // exit through the low x-wall: the one face normal to x this group tallies
-              if (ex == 0 && f.s0 < 0) atomicAdd(&S.GX[in.bface_off + in.wface_off[0] + (f.i1 + f.s1 * c1)], -w);
-              kend = c1 + (ex == 1 ? 1 : 0);
-              u0 = __fdividef(f.t1 - f.t0, f.d0);
-              r = __fdividef(f.d1, f.d0);
-              lim = m0 - 1;
-              a0 = (int)fax1 + f.i0 + n0 * (f.s1 > 0 ? f.i1 + 1 : f.i1);
-              sp = f.s1 * n0;
-              sq = f.s0;
-            }
-            f.i0 = a0;
-            f.s0 = sp;
-            f.s1 = sq;
-            f.i2 = lim;
-            f.D = u0;
-            f.tex = r;
-            nitem = kend;  // tallied below by the whole warp
+          if (!ADJ && wall_exit && tie) {
+            defer_particle(S, pid, ((unsigned)kc << 1) | ((two && f.d0 < f.d1) ? 1u : 0u));
             alive = false;
-          } else if (useF) {
-            // faces normal to the last axis: only the low boundary is tallied (the rest
-            // follow from conservation)
-            if (DIM == 2 && ex == 1 && f.s1 < 0) {
-              const long long fi = face_off + fax1 + (f.i0 + f.s0 * c0);
-              if (K32) tally_k32(&S.F32[fi], -w);
-              else atomicAdd(&A.F[fi], -w);
-            } else if (DIM == 3 && ex == 2 && f.s2 < 0) {
-              const long long fi = face_off + fax2 + (f.i0 + f.s0 * c0) + (long long)n0 * (f.i1 + f.s1 * c1);
-              if (K32) tally_k32(&S.F32[fi], -w);
-              else atomicAdd(&A.F[fi], -w);
-            }
-            // x-faces crossed (the wall face too when the particle leaves through x),
-            // then in 3D the y-faces
-            kcur = 0;
-            kend = c0 + (ex == 0 ? 1 : 0);
-            if (DIM == 3) {
-              f.tex = small_int_float(kend);  // first y-face item
-              kend += c1 + (ex == 1 ? 1 : 0);
-            } else if (DIM == 2) {
-              // rows of the x-face crossings, incrementally: faces normal to y before the
-              // k-th x-face = ceil(u0 + k r), u0 = (t0 - t1) / d1, r = d0 / d1
-              const bool flat = !(f.d1 < INFINITY);
-              f.D = flat ? -1.f : __fdividef(f.t0 - f.t1, f.d1);
-              f.tex = flat ? 0.f : __fdividef(f.d0, f.d1);
-              f.i2 = m1 - 1;  // largest count of y-faces a row index may take
-            }
-            tally = kend > 0;
-            alive = tally;
           } else {
-            alive = false;
+            if (wall_exit) cnt.v[CNT_WALL_EXITS] += 1;
+            cnt.v[CNT_CROSSINGS] += c0 + c1 + c2;
+            if (DIM == 2 && (two || wfull)) {
+              // Face items k = 0 .. kend-1 along the tallied axis p (the other axis: q). Item k
+              // is the face index a0 + k sp + sq min(ceil(u0 + k r), lim): the k-th face normal
+              // to p, in the row (or column) given by the faces normal to q crossed before it,
+              // ceil(u0 + k r) with u0 = (t_p - t_q) / d_q and r = d_p / d_q, at most lim.
+              const bool yg = two && f.d0 < f.d1;
+              int a0, sp, sq, lim;
+              float u0, r;
+              if (!yg) {
+                // exit through the low y-wall: the one face normal to y this group tallies
+                if (ex == 1 && f.s1 < 0) {
+                  const int col = f.i0 + f.s0 * c0;
+                  if (two) atomicAdd(&S.GX[in.bface_off + in.wface_off[2] + col], -w);
+                  else if (K32) tally_k32(&S.F32[face_off + fax1 + col], -w);
+                  else atomicAdd(&A.F[face_off + fax1 + col], -w);
+                }
+                kend = c0 + (ex == 0 ? 1 : 0);
+                const bool flat = !(f.d1 < INFINITY);
+                u0 = flat ? -1.f : __fdividef(f.t0 - f.t1, f.d1);
+                r = flat ? 0.f : __fdividef(f.d0, f.d1);
+                lim = m1 - 1;
+                a0 = (f.s0 > 0 ? f.i0 + 1 : f.i0) + sy_xf * f.i1;
+                sp = f.s0;
+                sq = f.s1 * sy_xf;
+              } else {
+                // exit through the low x-wall: the one face normal to x this group tallies
+                if (ex == 0 && f.s0 < 0) atomicAdd(&S.GX[in.bface_off + in.wface_off[0] + (f.i1 + f.s1 * c1)], -w);
+                kend = c1 + (ex == 1 ? 1 : 0);
+                u0 = __fdividef(f.t1 - f.t0, f.d0);
+                r = __fdividef(f.d1, f.d0);
+                lim = m0 - 1;
+                a0 = (int)fax1 + f.i0 + n0 * (f.s1 > 0 ? f.i1 + 1 : f.i1);
+                sp = f.s1 * n0;
+                sq = f.s0;
+              }
+              f.i0 = a0;
+              f.s0 = sp;
+              f.s1 = sq;
+              f.i2 = lim;
+              f.D = u0;
+              f.tex = r;
+              nitem = kend;  // tallied below by the whole warp
+              alive = false;
+            } else if (useF) {
+              // faces normal to the last axis: only the low boundary is tallied (the rest
+              // follow from conservation)
+              if (DIM == 2 && ex == 1 && f.s1 < 0) {
+                const long long fi = face_off + fax1 + (f.i0 + f.s0 * c0);
+                if (K32) tally_k32(&S.F32[fi], -w);
+                else atomicAdd(&A.F[fi], -w);
+              } else if (DIM == 3 && ex == 2 && f.s2 < 0) {
+                const long long fi = face_off + fax2 + (f.i0 + f.s0 * c0) + (long long)n0 * (f.i1 + f.s1 * c1);
+                if (K32) tally_k32(&S.F32[fi], -w);
+                else atomicAdd(&A.F[fi], -w);
+              }
+              // x-faces crossed (the wall face too when the particle leaves through x),
+              // then in 3D the y-faces
+              kcur = 0;
+              kend = c0 + (ex == 0 ? 1 : 0);
+              if (DIM == 3) {
+                f.tex = small_int_float(kend);  // first y-face item
+                kend += c1 + (ex == 1 ? 1 : 0);
+              } else if (DIM == 2) {
+                // rows of the x-face crossings, incrementally: faces normal to y before the
+                // k-th x-face = ceil(u0 + k r), u0 = (t0 - t1) / d1, r = d0 / d1
+                const bool flat = !(f.d1 < INFINITY);
+                f.D = flat ? -1.f : __fdividef(f.t0 - f.t1, f.d1);
+                f.tex = flat ? 0.f : __fdividef(f.d0, f.d1);
+                f.i2 = m1 - 1;  // largest count of y-faces a row index may take
+              }
+              tally = kend > 0;
+              alive = tally;
+            } else {
+              alive = false;
+            }
           }
         }
       }
@@ -837,74 +1013,109 @@ __global__ void __launch_bounds__(STAGED_NT, 1) sweep_sync_kernel(SweepArgs A, S
           const float vtm = A.vtm32[(long long)k * A.nb + band];
           const bool all_real = REAL || A.all_real[(long long)k * A.nb + band] != 0;
           const long long bcbase = in.bc_off + (long long)band * in.ncells;
-          // candidates (Sec. 3.2) until the particle collides for real or reaches a wall
-          bool wall_exit = false;
+          // candidates (Sec. 3.2) until the particle collides for real or reaches a wall; a
+          // decision within rounding of the FP64 walk's defers the particle to the FP64 replay
+          const int m0 = faces_to_wall(f.i0, f.s0, n0), m1 = faces_to_wall(f.i1, f.s1, n1);
+          const float ea = vtm * TIE_LOG_ABS;
+          float eD = fmaf(f.D, TIE_LOG_REL, ea);  // bound of |D - D_fp64|
+          bool wall_exit = false, deferred = false;
           int fb0 = 0, fb1 = 0;  // faces before the latest candidate, per axis
+          int kc = 0;            // candidates tallied
 #pragma unroll 1
           for (;;) {
-            if (f.tex < f.D) {
-              cnt.v[CNT_WALL_EXITS] += 1;
+            const float base = fmaf(TIE_REL, f.D, eD);
+            if (f.D - f.tex > base) {
               wall_exit = true;
               break;
             }
-            cnt.v[CNT_CANDIDATES] += 1;
-            fb0 = faces_before(f.D, f.t0, f.d0);
-            fb1 = faces_before(f.D, f.t1, f.d1);
+            if (f.tex - f.D <= fmaf(TIE_REL, f.tex, eD)) {  // at the first wall within rounding
+              deferred = true;
+              break;
+            }
+            unsigned tie = 0;  // tie bits of the counts, found with them for all-real bands
+            if (all_real) {
+              fb0 = count_tie(f.D, f.t0, f.d0, base, tie, 0);
+              fb1 = count_tie(f.D, f.t1, f.d1, base, tie, 2);
+            } else {
+              fb0 = faces_before(f.D, f.t0, f.d0);
+              fb1 = faces_before(f.D, f.t1, f.d1);
+            }
             const int cell = clampi(f.i0 + f.s0 * fb0, n0) + n0 * clampi(f.i1 + f.s1 * fb1, n1);
             const long long ci = bcbase + cell;
+            const int oc = candidate_outcome<2>(A, bcbase, in.ncells, f, base, fb0, fb1, 0, cell, all_real, tie, ub, n0,
+                                                n1, 1, n0, 0);
+            if (oc == CAND_DEFER) {
+              deferred = true;
+              break;
+            }
+            cnt.v[CNT_CANDIDATES] += 1;
+            ++kc;
             if (K32 && S.W32) tally_k32(&S.W32[ci], w);
             else if (!K32 && A.W) atomicAdd(&A.W[ci], w);
-            if (all_real || word_uniform<float>(ub) < A.ratio32[ci]) {
+            if (oc == CAND_REAL) {
               cnt.v[CNT_REAL] += 1;
               if (K32) tally_k32(&S.R32[ci], w);
               else atomicAdd(&A.R[ci], w);
               if (yg) atomicAdd(&S.DY[in.cell_off + cell], w);
               break;
             }
-            uint32_t ua;
-            st.next_pair(ua, ub);
-            f.D += -__logf(word_uniform<float>(ua)) * vtm;
+            uint32_t uw;
+            st.next_pair(uw, ub);
+            const float ell = __fmul_rn(-__logf(word_uniform<float>(uw)), vtm);
+            f.D = __fadd_rn(f.D, ell);
+            eD = fmaf(f.D, TIE_SUM, fmaf(ell, TIE_LOG_REL, eD + ea));
           }
           // faces crossed before the end per axis: at a real collision those before its
           // candidate; at a wall the exit axis's count is known and the other axis's follows
-          // from the exit distance
-          const int m0 = faces_to_wall(f.i0, f.s0, n0), m1 = faces_to_wall(f.i1, f.s1, n1);
+          // from the exit distance (within rounding of one of its faces, near a cell corner,
+          // the particle is deferred too)
           int ex = -1, c0, c1;
           if (wall_exit) {
+            // the face count of the axis not exited, near a cell corner within rounding of
+            // the FP64 walk's: deferred too
+            const float bx = TIE_REL * f.tex;
             ex = f.i2;
-            c0 = ex == 0 ? m0 - 1 : min(faces_before(f.tex, f.t0, f.d0), m0 - 1);
-            c1 = ex == 1 ? m1 - 1 : min(faces_before(f.tex, f.t1, f.d1), m1 - 1);
+            unsigned tie = 0;
+            const int q = count_tie(f.tex, ex == 0 ? f.t1 : f.t0, ex == 0 ? f.d1 : f.d0, bx, tie, 0);
+            deferred = tie != 0;
+            c0 = ex == 0 ? m0 - 1 : min(q, m0 - 1);
+            c1 = ex == 1 ? m1 - 1 : min(q, m1 - 1);
           } else {
             c0 = min(fb0, m0 - 1);
             c1 = min(fb1, m1 - 1);
           }
-          cnt.v[CNT_CROSSINGS] += c0 + c1;
-          // face items along the tallied axis p: a0 + k sp + sq min(ceil(u0 + k r), lim)
-          // p: the tallied axis (x for the x-group), q: the other one; selects, no branch
-          const float tp = yg ? f.t1 : f.t0, tq = yg ? f.t0 : f.t1;
-          const float dp = yg ? f.d1 : f.d0, dq = yg ? f.d0 : f.d1;
-          const int cp = yg ? c1 : c0, mq = yg ? m0 : m1, axp = yg ? 1 : 0;
-          if (ex == 1 - axp && (yg ? f.s0 : f.s1) < 0) {  // exit through the low q-wall
-            if (two) {
-              const int j = yg ? in.wface_off[0] + f.i1 + f.s1 * c1 : in.wface_off[2] + f.i0 + f.s0 * c0;
-              atomicAdd(&S.GX[in.bface_off + j], -w);
-            } else {
-              const int col = f.i0 + f.s0 * c0;
-              if (K32) tally_k32(&S.F32[face_off + fax1 + col], -w);
-              else atomicAdd(&A.F[face_off + fax1 + col], -w);
+          if (deferred) {
+            defer_particle(S, rbeg + lane, ((unsigned)kc << 1) | (yg ? 1u : 0u));
+          } else {
+            if (wall_exit) cnt.v[CNT_WALL_EXITS] += 1;
+            cnt.v[CNT_CROSSINGS] += c0 + c1;
+            // face items along the tallied axis p: a0 + k sp + sq min(ceil(u0 + k r), lim)
+            // p: the tallied axis (x for the x-group), q: the other one; selects, no branch
+            const float tp = yg ? f.t1 : f.t0, tq = yg ? f.t0 : f.t1;
+            const float dp = yg ? f.d1 : f.d0, dq = yg ? f.d0 : f.d1;
+            const int cp = yg ? c1 : c0, mq = yg ? m0 : m1, axp = yg ? 1 : 0;
+            if (ex == 1 - axp && (yg ? f.s0 : f.s1) < 0) {  // exit through the low q-wall
+              if (two) {
+                const int j = yg ? in.wface_off[0] + f.i1 + f.s1 * c1 : in.wface_off[2] + f.i0 + f.s0 * c0;
+                atomicAdd(&S.GX[in.bface_off + j], -w);
+              } else {
+                const int col = f.i0 + f.s0 * c0;
+                if (K32) tally_k32(&S.F32[face_off + fax1 + col], -w);
+                else atomicAdd(&A.F[face_off + fax1 + col], -w);
+              }
             }
+            nitem = cp + (ex == axp ? 1 : 0);
+            const bool flat = !(dq < INFINITY);
+            const float u0 = flat ? -1.f : __fdividef(tp - tq, dq);
+            const float r = flat ? 0.f : __fdividef(dp, dq);
+            const int lim = mq - 1;
+            const int a0 = yg ? (int)fax1 + f.i0 + n0 * (f.i1 + (f.s1 > 0 ? 1 : 0))
+                              : f.i0 + (f.s0 > 0 ? 1 : 0) + sy_xf * f.i1;
+            const int sp = yg ? f.s1 * n0 : f.s0;
+            const int sq = yg ? f.s0 : f.s1 * sy_xf;
+            pa_own = make_int4(a0, sp, sq, lim);
+            pb_own = make_int4(__float_as_int(u0), __float_as_int(r), (int)qwx, 0);
           }
-          nitem = cp + (ex == axp ? 1 : 0);
-          const bool flat = !(dq < INFINITY);
-          const float u0 = flat ? -1.f : __fdividef(tp - tq, dq);
-          const float r = flat ? 0.f : __fdividef(dp, dq);
-          const int lim = mq - 1;
-          const int a0 = yg ? (int)fax1 + f.i0 + n0 * (f.i1 + (f.s1 > 0 ? 1 : 0))
-                            : f.i0 + (f.s0 > 0 ? 1 : 0) + sy_xf * f.i1;
-          const int sp = yg ? f.s1 * n0 : f.s0;
-          const int sq = yg ? f.s0 : f.s1 * sy_xf;
-          pa_own = make_int4(a0, sp, sq, lim);
-          pb_own = make_int4(__float_as_int(u0), __float_as_int(r), (int)qwx, 0);
         }
       }
       rbeg += take;
@@ -1044,20 +1255,41 @@ __global__ void __launch_bounds__(STAGED_NT, 1) adjoint_sync_kernel(SweepArgs A,
           const float vtm = A.vtm32[(long long)k * A.nb + band];
           const bool all_real = REAL || A.all_real[(long long)k * A.nb + band] != 0;
           const long long bcbase = in.bc_off + (long long)band * in.ncells;
-          bool wall_exit = false;
+          // the forward sweep's decisions, with the same deferrals to the FP64 replay
+          const int m0 = faces_to_wall(f.i0, f.s0, n0), m1 = faces_to_wall(f.i1, f.s1, n1);
+          const float ea = vtm * TIE_LOG_ABS;
+          float eD = fmaf(f.D, TIE_LOG_REL, ea);
+          bool wall_exit = false, deferred = false;
           int fb0 = 0, fb1 = 0;  // faces before the latest candidate, per axis
 #pragma unroll 1
           for (;;) {
-            if (f.tex < f.D) {
+            const float base = fmaf(TIE_REL, f.D, eD);
+            if (f.D - f.tex > base) {
               cnt.v[CNT_WALL_EXITS] += 1;
               wall_exit = true;
               break;
             }
-            cnt.v[CNT_CANDIDATES] += 1;
-            fb0 = faces_before(f.D, f.t0, f.d0);
-            fb1 = faces_before(f.D, f.t1, f.d1);
+            if (f.tex - f.D <= fmaf(TIE_REL, f.tex, eD)) {
+              deferred = true;
+              break;
+            }
+            unsigned tie = 0;  // tie bits of the counts, found with them for all-real bands
+            if (all_real) {
+              fb0 = count_tie(f.D, f.t0, f.d0, base, tie, 0);
+              fb1 = count_tie(f.D, f.t1, f.d1, base, tie, 2);
+            } else {
+              fb0 = faces_before(f.D, f.t0, f.d0);
+              fb1 = faces_before(f.D, f.t1, f.d1);
+            }
             const int cell = clampi(f.i0 + f.s0 * fb0, n0) + n0 * clampi(f.i1 + f.s1 * fb1, n1);
-            if (all_real || word_uniform<float>(ub) < A.ratio32[bcbase + cell]) {
+            const int oc = candidate_outcome<2>(A, bcbase, in.ncells, f, base, fb0, fb1, 0, cell, all_real, tie, ub, n0,
+                                                n1, 1, n0, 0);
+            if (oc == CAND_DEFER) {
+              deferred = true;
+              break;
+            }
+            cnt.v[CNT_CANDIDATES] += 1;
+            if (oc == CAND_REAL) {
               cnt.v[CNT_REAL] += 1;
               const long long gc = in.cell_off + cell;
               const double val = w * A.lambda[gc] * A.invVm[gc];
@@ -1065,21 +1297,26 @@ __global__ void __launch_bounds__(STAGED_NT, 1) adjoint_sync_kernel(SweepArgs A,
               else acc += val;
               break;
             }
-            uint32_t ua;
-            st.next_pair(ua, ub);
-            f.D += -__logf(word_uniform<float>(ua)) * vtm;
+            uint32_t uw;
+            st.next_pair(uw, ub);
+            const float ell = __fmul_rn(-__logf(word_uniform<float>(uw)), vtm);
+            f.D = __fadd_rn(f.D, ell);
+            eD = fmaf(f.D, TIE_SUM, fmaf(ell, TIE_LOG_REL, eD + ea));
           }
-          // faces crossed, for the event counters (as in the forward sweep)
-          const int m0 = faces_to_wall(f.i0, f.s0, n0), m1 = faces_to_wall(f.i1, f.s1, n1);
-          int c0, c1;
-          if (wall_exit) {
-            c0 = f.i2 == 0 ? m0 - 1 : min(faces_before(f.tex, f.t0, f.d0), m0 - 1);
-            c1 = f.i2 == 1 ? m1 - 1 : min(faces_before(f.tex, f.t1, f.d1), m1 - 1);
+          if (deferred) {
+            defer_particle(S, rbeg + lane, 0u);
           } else {
-            c0 = min(fb0, m0 - 1);
-            c1 = min(fb1, m1 - 1);
+            // faces crossed, for the event counters (as in the forward sweep)
+            int c0, c1;
+            if (wall_exit) {
+              c0 = f.i2 == 0 ? m0 - 1 : min(faces_before(f.tex, f.t0, f.d0), m0 - 1);
+              c1 = f.i2 == 1 ? m1 - 1 : min(faces_before(f.tex, f.t1, f.d1), m1 - 1);
+            } else {
+              c0 = min(fb0, m0 - 1);
+              c1 = min(fb1, m1 - 1);
+            }
+            cnt.v[CNT_CROSSINGS] += c0 + c1;
           }
-          cnt.v[CNT_CROSSINGS] += c0 + c1;
         }
       }
       rbeg += take;
@@ -1386,10 +1623,15 @@ cudaError_t launch_sweep_staged(const Ctx* c, const SweepArgs& a, cudaStream_t s
   S.mag_n0 = c->d_mag;
   S.mag_n1 = c->d_mag + c->n_inst;
   S.mag_wall = c->d_mag + 2 * c->n_inst;
+  S.defer = c->d_defer;
+  S.defer_n = c->d_defer_n;
+  S.defer_cap = c->defer_cap;
+  S.err = c->d_err;
   cudaError_t e = cudaMemcpyAsync(c->d_inst_next, c->d_inst_beg, c->n_inst * sizeof(long long),
                                   cudaMemcpyDeviceToDevice, s);
   if (e != cudaSuccess) return e;
   if ((e = cudaMemsetAsync(c->d_wmax, 0, c->n_inst * sizeof(double), s)) != cudaSuccess) return e;
+  if ((e = cudaMemsetAsync(c->d_defer_n, 0, sizeof(unsigned), s)) != cudaSuccess) return e;
   {
     // about four emitters per thread, at most 64 blocks per group
     long long most = 1;
@@ -1435,6 +1677,8 @@ cudaError_t launch_sweep_staged(const Ctx* c, const SweepArgs& a, cudaStream_t s
     k32_finalize_kernel<<<fb, 256, 0, s>>>(c->d_R32, a.R, (long long)bc, 0);
     if (a.W) k32_finalize_kernel<<<fb, 256, 0, s>>>(c->d_W32, a.W, (long long)bc, 0);
     if (a.F) k32_finalize_kernel<<<fb, 256, 0, s>>>(c->d_F32, a.F, c->total_faces, 1);
+    // the deferred particles add to the FP64 outputs (after the finalize, which overwrites R and W)
+    if ((e = launch_replay(c, a, S, s)) != cudaSuccess) return e;
   } else {
     switch (c->dim) {
       case 1: sweep_staged_kernel<1, false, false><<<blocks, STAGED_NT, smem, s>>>(a, S); break;
@@ -1444,6 +1688,8 @@ cudaError_t launch_sweep_staged(const Ctx* c, const SweepArgs& a, cudaStream_t s
         break;
       default: sweep_staged_kernel<3, false, false><<<blocks, STAGED_NT, smem, s>>>(a, S); break;
     }
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if ((e = launch_replay(c, a, S, s)) != cudaSuccess) return e;
   }
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   if (a.W) {
@@ -1509,9 +1755,14 @@ cudaError_t launch_adjoint_staged(const Ctx* c, const SweepArgs& a, cudaStream_t
   S.mag_n0 = c->d_mag;
   S.mag_n1 = c->d_mag + c->n_inst;
   S.mag_wall = c->d_mag + 2 * c->n_inst;
+  S.defer = c->d_defer;
+  S.defer_n = c->d_defer_n;
+  S.defer_cap = c->defer_cap;
+  S.err = c->d_err;
   cudaError_t e = cudaMemcpyAsync(c->d_inst_next, c->d_all_beg, c->n_inst * sizeof(long long),
                                   cudaMemcpyDeviceToDevice, s);
   if (e != cudaSuccess) return e;
+  if ((e = cudaMemsetAsync(c->d_defer_n, 0, sizeof(unsigned), s)) != cudaSuccess) return e;
   S.R32 = S.W32 = S.F32 = nullptr;
   S.DY = S.EY = S.GX = nullptr;
   const int blocks = c->sm_count * c->adj_blocks_per_sm;
@@ -1519,14 +1770,74 @@ cudaError_t launch_adjoint_staged(const Ctx* c, const SweepArgs& a, cudaStream_t
     // pass-synchronous re-trace (refill only when all 32 lanes are idle)
     if (c->all_real_all) adjoint_sync_kernel<true><<<blocks, STAGED_NT, 0, s>>>(a, S);
     else adjoint_sync_kernel<false><<<blocks, STAGED_NT, 0, s>>>(a, S);
-    return cudaGetLastError();
+  } else {
+    switch (c->dim) {
+      case 1: sweep_staged_kernel<1, true, false><<<blocks, STAGED_NT, 0, s>>>(a, S); break;
+      case 2: sweep_staged_kernel<2, true, false><<<blocks, STAGED_NT, 0, s>>>(a, S); break;
+      default: sweep_staged_kernel<3, true, false><<<blocks, STAGED_NT, 0, s>>>(a, S); break;
+    }
   }
-  switch (c->dim) {
-    case 1: sweep_staged_kernel<1, true, false><<<blocks, STAGED_NT, 0, s>>>(a, S); break;
-    case 2: sweep_staged_kernel<2, true, false><<<blocks, STAGED_NT, 0, s>>>(a, S); break;
-    default: sweep_staged_kernel<3, true, false><<<blocks, STAGED_NT, 0, s>>>(a, S); break;
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  return launch_adjoint_replay(c, a, s);  // the deferred particles, in FP64
+}
+
+// Measured accuracy of the FP32 operations the tie bounds rely on, over every uniform the
+// walk can draw ((2m + 1) 2^-24, m < 2^23), against FP64:
+//  out[0] max |__logf(u) - ln u| / (TIE_LOG_ABS + (TIE_LOG_REL - 2^-23) |ln u|) (the log's
+//         share of the bound on a flight length; <= 1 required);
+//  out[1] max relative error of sincospif(2u), both outputs, in units of 2^-23;
+//  out[2] max relative error of sqrtf(fmaf(-mu, mu, 1)), mu = 2u - 1, units of 2^-23;
+//  out[3] max relative error of sqrtf(u) and sqrtf(1 - u), units of 2^-23;
+//  out[4] max relative error of __fdividef(x, y) over pairs of uniforms, units of 2^-23.
+// Results are max-reduced as the bit patterns of non-negative doubles.
+__global__ void walk_bounds_kernel(unsigned long long* out) {
+  double e[5] = {0, 0, 0, 0, 0};
+  for (unsigned m = blockIdx.x * blockDim.x + threadIdx.x; m < (1u << 23); m += gridDim.x * blockDim.x) {
+    const float u = word_uniform<float>(m << 9);
+    const double ud = (double)u;
+    const double lg = log(ud);
+    e[0] = fmax(e[0], fabs((double)__logf(u) - lg) / ((double)TIE_LOG_ABS + ((double)TIE_LOG_REL - 0x1p-23) * fabs(lg)));
+    float sp, cp;
+    sincospif(2.f * u, &sp, &cp);
+    double sd, cd;
+    sincospi(2.0 * ud, &sd, &cd);
+    e[1] = fmax(e[1], fmax(fabs(sp - sd) / fabs(sd), fabs(cp - cd) / fabs(cd)) * 0x1p23);
+    const float mu = 2.f * u - 1.f;
+    const double sn = sqrt(1.0 - (double)mu * (double)mu);
+    e[2] = fmax(e[2], fabs((double)sqrtf(fmaf(-mu, mu, 1.f)) - sn) / sn * 0x1p23);
+    e[3] = fmax(e[3], fmax(fabs((double)sqrtf(u) - sqrt(ud)) / sqrt(ud),
+                           fabs((double)sqrtf(1.f - u) - sqrt(1.0 - ud)) / sqrt(1.0 - ud)) * 0x1p23);
+    // pairs (u, u') with u' another uniform, the divisor scaled over several binades
+    const float v = word_uniform<float>((m * 2654435761u) << 9) * __int_as_float((127 - (int)(m & 15u)) << 23);
+    const double q = ud / (double)v;
+    e[4] = fmax(e[4], fabs((double)__fdividef(u, v) - q) / q * 0x1p23);
   }
+  for (int k = 0; k < 5; ++k) {
+    double x = e[k];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x = fmax(x, __shfl_down_sync(0xffffffffu, x, o));
+    if ((threadIdx.x & 31) == 0) atomicMax(&out[k], (unsigned long long)__double_as_longlong(x));
+  }
+}
+
+cudaError_t launch_walk_bounds(unsigned long long* out, cudaStream_t s) {
+  cudaError_t e = cudaMemsetAsync(out, 0, 5 * sizeof(unsigned long long), s);
+  if (e != cudaSuccess) return e;
+  walk_bounds_kernel<<<1024, 256, 0, s>>>(out);
   return cudaGetLastError();
+}
+
+// The relative bound the face-count decision needs, from the measured errors above (units of
+// 2^-23): direction s = product of a square root and a sine/cosine (one more rounding), cell
+// size h in FP32 (half an ulp), d = h / |s| (__fdividef), t = (1 - xi) d (one rounding), the
+// quotient (D - t) / d (__fdividef) and the difference D - t (half an ulp each), and half an
+// ulp for the distance to the face. Returned as a fraction of TIE_REL (<= 1 required).
+double walk_bound_fraction(const double* m) {
+  const double ulp = 0x1p-23;
+  const double Es = (std::max(m[2], m[3]) + m[1] + 0.5) * ulp;
+  const double Ed = 0.5 * ulp + Es + m[4] * ulp;
+  const double Et = Ed + 0.5 * ulp;
+  return (Et + Ed + m[4] * ulp + ulp) / (double)TIE_REL;
 }
 
 cudaError_t configure_staged(Ctx* c) {

@@ -197,6 +197,12 @@ class Solver:
         return {"refill_lanes": t.refill_lanes, "warp_grab": t.warp_grab, "walk_k": t.walk_k, "tally": t.tally,
                 "sweep_ms": t.sweep_ms, "baseline_ms": t.baseline_ms}
 
+    def replayed(self, stream=None) -> int:
+        """Particles of the last staged sweep (or adjoint re-trace) the FP64 walk replayed."""
+        n = ctypes.c_longlong(0)
+        L.check(self.lib.iugkp_replayed(self.ctx, ctypes.byref(n), _stream_ptr(stream)), self.ctx)
+        return n.value
+
     def set_source(self, Q, stream=None):
         self._set(L.FIELD_SOURCE, Q, stream)
 

@@ -21,7 +21,7 @@ def lib():
 
 def test_library_exports_every_declared_symbol(lib):
     header = open(os.path.join(ROOT, "include", "iugkp.h")).read()
-    declared = set(re.findall(r"\b(iugkp_[a-z_]+)\s*\(", header))
+    declared = set(re.findall(r"\b(iugkp_[a-z0-9_]+)\s*\(", header))
     assert "iugkp_sweep" in declared and "iugkp_diffusion_solve_noalloc" in declared
     L = lib.load()
     for name in sorted(declared):

@@ -1,0 +1,156 @@
+"""FP32 walk with FP64 decisions: the fast path (FP32 tracking, staged tallies) takes each
+decision of a particle's walk in FP32 only where the FP32 value is farther from the
+decision's boundary than a bound on its difference from the FP64 walk's value, and hands the
+particle to an FP64 replay otherwise. Real collisions, wall exits and event counts are then
+those of the FP64 walk, so the steady temperature matches the FP64 oracle's to rounding, far
+inside the 5e-4 of the wall-temperature span that FP32 tracking must meet.
+
+Checked here: the FP32 operations the bound rests on, over every uniform the walk draws;
+per-sweep tallies against the oracle (counters equal, R to 1e-10); the benchmark's 128^2
+cavity at all four Knudsen numbers against the plain FP64 path (sweep and steady state); a
+32^2 reduction of it against the oracle's steady state; the fast adjoint against the
+oracle's dense transpose."""
+import ctypes
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from paper_2506_09465_gb300 import workloads as WL  # noqa: E402
+from gpu_helpers import gpu_solver, normwise_close, oracle_problem  # noqa: E402
+
+KNS = (0.01, 0.1, 1.0, 10.0)
+
+
+def cuda_T(x):
+    return torch.as_tensor(np.asarray(x, dtype=np.float64), device="cuda")
+
+
+def test_fp32_walk_error_bounds():
+    # The bound on |FP32 - FP64| of a flight length and of a face-count quotient assumes
+    # error levels of __logf, sincospif, sqrtf and __fdividef; measured over all 2^23
+    # uniforms (and pairs of them for the division), they stay inside it with room.
+    from paper_2506_09465_gb300 import _lib as L
+    lib = L.load()
+    out = (ctypes.c_double * 6)()
+    L.check(lib.iugkp_check_fp32_walk(out))
+    m = list(out)
+    assert all(np.isfinite(m)), m
+    assert m[0] <= 1.0, m          # fast log within its allowance
+    assert max(m[1:5]) <= 4.0, m   # each operation within a few units of 2^-23
+    assert m[5] <= 0.6, m          # the implied face-count bound within the one used
+
+
+@pytest.mark.parametrize("tally", [1, 2])
+@pytest.mark.parametrize("dim,n,tau", [(1, (40,), (0.05, 0.8)), (2, (16, 12), (0.05, 0.8)),
+                                      (2, (16, 12), None), (3, (6, 6, 5), (0.05, 0.8))])
+def test_staged_sweep_takes_the_fp64_decisions(orc, dim, n, tau, tally):
+    # Same draws as the oracle: counters equal and R equal to FP64 summation order. W may
+    # differ where a null candidate lay within rounding of a face but every cell it may lie in
+    # rejects it (its cell is then the FP32 one), and faces where a particle passed within
+    # rounding of a cell corner: a few particle weights, in a few places.
+    rng = np.random.default_rng(30 + dim)
+    if tau is None:  # constant tau: every candidate real (the pass-synchronous kernel without the test)
+        inst = WL.Instance(2, n, (1.0, 1.0), np.full((1, n[0] * n[1]), 0.4), np.array([0.2, -0.5, 0.0, 1.0]))
+    else:
+        inst = WL.random_instance(rng, dim, n, 1, tau)
+    N = 200
+    T = rng.uniform(-0.3, 1.0, size=inst.ncells)
+    p = oracle_problem(inst, [1.0], [1.0], N, N, seed=3)
+    s = gpu_solver(inst, [1.0], [1.0], N, N, precision=1, tally=tally, seed=3)
+    for epoch in (0, 7):
+        r = orc.sweep(p, T, epoch)
+        g = s.sweep(cuda_T(T), epoch)
+        assert g["counters"].cpu().numpy().tolist() == r.counters.astype(np.int64).tolist()
+        ok, err = normwise_close(g["R"].cpu().numpy(), r.R, 1e-10 if tally == 1 else 1e-9)
+        assert ok, ("R", err)
+        for key, ora in (("W", r.W), ("F", r.F), ("wall", r.wall)):
+            ok, err = normwise_close(g[key].cpu().numpy(), ora, 2e-3)
+            assert ok, (key, err)
+            if key != "wall":
+                # beyond the fixed-point rounding of the face window (2^-26 of the largest
+                # weight per particle), only a few entries differ
+                d = np.abs(g[key].cpu().numpy().ravel() - np.asarray(ora).ravel())
+                assert np.mean(d > 1e-6 * np.abs(ora).max()) < 0.02, key
+
+
+@pytest.fixture(scope="module")
+def cavity_pair():
+    # The benchmark batch (128^2, Kn 0.01 / 0.1 / 1 / 10, 1024 particles per cell and wall face)
+    # on the fast path, and each instance on the plain FP64 path with the same instance id.
+    wl = WL.cavity_sweep(128, KNS, 1024)
+    fast = gpu_solver(wl.instances, [1.0], [1.0], 1024, 1024, seed=0)
+    plain = [gpu_solver(wl.instances[j], [1.0], [1.0], 1024, 1024, seed=0, instance_base=j, precision=0, tally=0,
+                        schedule=0, use_graphs=0) for j in range(len(KNS))]
+    return wl, fast, plain
+
+
+def test_bench_cavity_sweep_equals_fp64_walk(cavity_pair):
+    wl, fast, plain = cavity_pair
+    T = torch.full((fast.total_cells,), 0.3, dtype=torch.float64, device="cuda")
+    g = fast.sweep(T, 0)
+    replayed = fast.replayed()
+    cnt = np.zeros(6, dtype=np.int64)
+    n1 = 128 * 128
+    for j, sp in enumerate(plain):
+        gp = sp.sweep(T[j * n1:(j + 1) * n1].contiguous(), 0)
+        cnt += np.array(gp["counters"].cpu().tolist(), dtype=np.int64)
+        R = g["R"][j * n1:(j + 1) * n1].cpu().numpy()
+        ok, err = normwise_close(R, gp["R"].cpu().numpy(), 1e-12)
+        assert ok, (KNS[j], err)
+        ok, err = normwise_close(g["W"][j * n1:(j + 1) * n1].cpu().numpy(), gp["W"].cpu().numpy(), 1e-12)
+        assert ok, (KNS[j], "W", err)
+    assert g["counters"].cpu().numpy().tolist() == cnt.tolist()
+    flights = int(cnt[0])
+    assert 0 < replayed < 1e-3 * flights, (replayed, flights)
+
+
+def test_bench_cavity_steady_state_equals_fp64_walk(cavity_pair):
+    # Time-to-steady workload (frozen draws, Newton, residual 1e-8): the batched fast path
+    # and the plain FP64 path reach the same steady state to solver tolerance.
+    wl, fast, plain = cavity_pair
+    Tf, it, res = fast.solve_steady(None, 1e-8, 400)
+    assert res <= 1e-8
+    n1 = 128 * 128
+    for j, sp in enumerate(plain):
+        Tp, itp, resp = sp.solve_steady(None, 1e-8, 400)
+        d = (Tf[j * n1:(j + 1) * n1] - Tp).abs()
+        assert float(d.max()) <= 5e-4, (KNS[j], float(d.max()))   # the span is 1
+        assert float(d.max()) <= 1e-6, (KNS[j], float(d.max()))   # and in fact to solver tolerance
+
+
+@pytest.mark.parametrize("kn", KNS)
+def test_reduced_cavity_steady_state_matches_oracle(orc, kn):
+    # The same cavity at 32^2 (1024 particles per cell and wall face) against the oracle's
+    # frozen-draw steady state (direct Newton solve): within 5e-4 of the span, element by element.
+    inst = WL.cavity(32, kn).instances[0]
+    N = 1024
+    p = oracle_problem(inst, [1.0], [1.0], N, N, seed=5)
+    T_o, it_o, res_o, _ = orc.solve_steady(p, np.zeros(inst.ncells), 1e-9, 300, frozen=True, newton=True, dT_ref=1.0)
+    assert res_o <= 1e-9
+    s = gpu_solver(inst, [1.0], [1.0], N, N, seed=5)
+    T_g, it_g, res_g = s.solve_steady(None, 1e-9, 300)
+    assert res_g <= 1e-9
+    d = np.abs(T_g.cpu().numpy() - T_o)
+    assert d.max() <= 5e-4, d.max()
+    assert d.max() <= 1e-6, d.max()
+
+
+def test_fast_adjoint_equals_dense_transpose(orc):
+    # The adjoint re-trace defers the same particles as the forward sweep, so the fast
+    # adjoint is the transpose of the FP64 map: against the oracle's dense transpose at 1e-9.
+    rng = np.random.default_rng(18)
+    inst = WL.random_instance(rng, 2, (7, 6), 1, (0.1, 0.8), source=True)
+    N = 48
+    p = oracle_problem(inst, [1.0], [1.0], N, N, seed=6)
+    g = np.zeros(inst.ncells)
+    g[[8, 9, 15, 16]] = 0.25
+    gQ, gW, lam, A, Bw = orc.adjoint_dense(p, g)
+    for refill in (0, 8):
+        s = gpu_solver(inst, [1.0], [1.0], N, N, seed=6, cg_rtol=1e-12, refill_lanes=refill)
+        gs, gw, gl = s.adjoint(cuda_T(g), tol=1e-12, max_iter=500)
+        for got, ref in ((gl, lam), (gs, gQ), (gw, gW)):
+            ok, err = normwise_close(got.cpu().numpy(), ref, 1e-9)
+            assert ok, (refill, err)

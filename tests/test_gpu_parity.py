@@ -323,23 +323,6 @@ def test_graph_replay_matches_plain_loop():
     assert outs[0][1] >= outs[1][1] and outs[0][1] - outs[1][1] <= 1
 
 
-def test_fast_adjoint_matches_dense_transpose(orc):
-    # FP32 walk, staged kernel: same particles as the oracle up to rare single-precision
-    # classification differences.
-    rng = np.random.default_rng(18)
-    inst = WL.random_instance(rng, 2, (7, 6), 1, (0.1, 0.8), source=True)
-    N = 48
-    p = oracle_problem(inst, [1.0], [1.0], N, N, seed=6)
-    g = np.zeros(inst.ncells)
-    g[[8, 9, 15, 16]] = 0.25
-    gQ, gW, lam, A, Bw = orc.adjoint_dense(p, g)
-    s = gpu_solver(inst, [1.0], [1.0], N, N, seed=6, cg_rtol=1e-12)
-    gs, gw, gl = s.adjoint(cuda_T(g), tol=1e-12, max_iter=500)
-    for got, ref in ((gl, lam), (gs, gQ), (gw, gW)):
-        ok, err = normwise_close(got.cpu().numpy(), ref, 3e-3)
-        assert ok, err
-
-
 @pytest.mark.parametrize("refill", [4, 16])
 def test_pass_synchronous_adjoint_matches_per_lane_refill(refill):
     # The 2D adjoint re-trace runs pass by pass by default (refill_lanes 0) and with the

@@ -61,12 +61,11 @@ def test_hot_segment_fast_path_conserves_and_reaches_oracle_steady_state(orc):
     assert abs(g["wall"].cpu().numpy().sum() - seg - (emitted.sum() - R.sum())) <= 1e-7
     p = oracle_problem(inst, wl.C, wl.v, 64, 64, seed=3)
     T_o, _, res_o, _ = orc.solve_steady(p, np.zeros(inst.ncells), 1e-8, 200, frozen=True, newton=True, dT_ref=1.0)
-    # Same draws. At 64 particles per face a particle of the hot segment carries ~8 % of a
-    # cell's equilibrium energy (w / (V m) = 0.25 / (20 * 64) / 0.0025), so the rare particle
-    # that an FP32 near-tie moves by one cell shifts its neighbourhood by ~1e-3 of the span;
-    # elsewhere the two steady states agree far inside 5e-4.
+    # Same draws, and every real collision and wall exit of the fast path is the FP64
+    # walk's (decisions within rounding of the FP64 one are replayed in FP64): the steady
+    # states agree element by element within 5e-4 of the span.
     d = np.abs(T.cpu().numpy() - T_o)
-    assert d.max() <= 2e-3 and np.quantile(d, 0.99) <= 5e-4
+    assert d.max() <= 5e-4, d.max()
 
 
 def test_hot_segment_ballistic_view_factors_on_gpu():
