@@ -9,6 +9,7 @@
 
 #include "device.cuh"
 #include "internal.h"
+#include "replay.cuh"
 
 namespace iugkp {
 
@@ -30,20 +31,16 @@ __device__ __forceinline__ double adj_ratio<double>(const SweepArgs& A, long lon
 template <>
 __device__ __forceinline__ float adj_ratio<float>(const SweepArgs& A, long long i) { return A.ratio32[i]; }
 
-// Re-traces particle pid; returns its contribution c_p lam[stop] / (V m_stop) and the
-// accumulation target (cell index for cell particles, wall slot | 1<<62 for walls).
+// Emission of adjoint particle pid (every emitter, emitter-major numbering within its group):
+// the walk, the stream, and the particle's weight per unit emission temperature.
 template <typename Real, int DIM>
-__device__ __forceinline__ void adjoint_particle(const SweepArgs& A, long long pid, int* err) {
-  const int gi = find_group(A.groups, A.n_groups, pid);
-  const Group G = A.groups[gi];
+__device__ __forceinline__ void adjoint_emit(const SweepArgs& A, long long pid, const Group& G, Walk<Real, DIM>& wk,
+                                             Stream& st, double& coefp, int& e) {
   const long long local = pid - G.first_particle;
-  const int e = (int)(local / G.per_emitter);
+  e = (int)(local / G.per_emitter);
   const int q = (int)(local - (long long)e * G.per_emitter);
   const InstDesc& in = A.inst[G.inst];
   const int b = G.band;
-  Walk<Real, DIM> wk;
-  Stream st;
-  double coefp;
   if (G.kind == 0) {
     coefp = A.coef[in.bc_off + (long long)b * in.ncells + e];
     st.init(A.seed, in.inst_id, (uint32_t)b, A.epoch, (uint32_t)e, (uint32_t)q);
@@ -63,6 +60,21 @@ __device__ __forceinline__ void adjoint_particle(const SweepArgs& A, long long p
     st.init(A.seed, in.inst_id, (uint32_t)b, A.epoch, (uint32_t)(in.ncells + face), (uint32_t)q);
     emit_wall<Real, DIM>(wk, st, in, wl, j1, j2);
   }
+}
+
+// Re-traces particle pid and adds its contribution c_p lam[stop] / (V m_stop) to its emitter
+// cell or wall.
+template <typename Real, int DIM>
+__device__ __forceinline__ void adjoint_particle(const SweepArgs& A, long long pid, int* err) {
+  const int gi = find_group(A.groups, A.n_groups, pid);
+  const Group G = A.groups[gi];
+  const InstDesc& in = A.inst[G.inst];
+  const int b = G.band;
+  Walk<Real, DIM> wk;
+  Stream st;
+  double coefp;
+  int e;
+  adjoint_emit<Real, DIM>(A, pid, G, wk, st, coefp, e);
   const double tm = A.taumaj[(long long)G.inst * A.nb + b];
   const double vb = A.v[b];
   const float vtm_f = (float)(vb * tm);
@@ -116,9 +128,21 @@ __global__ void __launch_bounds__(256) adjoint_kernel(SweepArgs A) {
     adjoint_particle<Real, DIM>(A, pid, A.err);
 }
 
-// FP64 re-trace of the particles the staged adjoint re-trace deferred (a decision of its
-// FP32 walk within rounding of the FP64 walk's; the forward sweep defers the same particles).
-// Entry x: the staged index, particle q of emitter e taken q-major within its group.
+// The gather of a replayed adjoint particle: c_p lam / (V m) at its real collision.
+struct AdjointGather {
+  const SweepArgs& A;
+  const InstDesc& in;
+  double coefp, val;
+  __device__ void candidate(int, long long, int) {}
+  __device__ void real(long long, int cell) {
+    const long long g = in.cell_off + cell;
+    val = coefp * A.lambda[g] * A.invVm[g];
+  }
+};
+
+// FP64 re-trace (analytic along the straight segment, replay.cuh) of the particles the staged
+// adjoint re-trace deferred; the forward sweep defers the same particles. One thread per
+// entry; entry x: the staged index, particle q of emitter e taken q-major within its group.
 template <int DIM>
 __global__ void __launch_bounds__(128) adjoint_replay_kernel(SweepArgs A, const uint2* defer, const unsigned* defer_n,
                                                              unsigned defer_cap) {
@@ -126,10 +150,27 @@ __global__ void __launch_bounds__(128) adjoint_replay_kernel(SweepArgs A, const 
   for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
     const unsigned pid = defer[i].x;
     const Group G = A.groups[find_group(A.groups, A.n_groups, (long long)pid)];
+    const InstDesc& in = A.inst[G.inst];
     const unsigned local = pid - (unsigned)G.first_particle;
     const int q = (int)(local / (unsigned)G.n_emitters);
-    const int e = (int)(local - (unsigned)q * (unsigned)G.n_emitters);
-    adjoint_particle<double, DIM>(A, G.first_particle + (long long)e * G.per_emitter + q, A.err);
+    const int e0 = (int)(local - (unsigned)q * (unsigned)G.n_emitters);
+    Walk<double, DIM> wk;
+    Stream st;
+    double coefp;
+    int e;
+    adjoint_emit<double, DIM>(A, G.first_particle + (long long)e0 * G.per_emitter + q, G, wk, st, coefp, e);
+    Seg64<DIM> sg;
+    sg.init(wk, in);
+    AdjointGather pol{A, in, coefp, 0.0};
+    int fb[DIM];
+    const int res = replay_candidates<DIM>(A, in, G.inst, G.band, wk, sg, st, fb, pol);
+    if (res < 0) {
+      atomicOr(A.err, ERR_BUDGET);
+      continue;
+    }
+    if (res == 0) continue;  // absorbed by a wall: no gather
+    if (G.kind == 0) atomicAdd(&A.adj_out[in.cell_off + e], pol.val);
+    else atomicAdd(&A.adj_wall[in.wall_off + G.kind - 1], pol.val);
   }
 }
 

@@ -266,6 +266,7 @@ iugkp_status rebuild_forward_groups(Ctx* c) {
   // them (the rest take global atomics).
   std::vector<int2> window(c->n_inst);
   c->any_two_group = false;
+  c->all_two_group = c->dim == 2;
   c->sync_ok = c->dim == 2;
   c->sync_partial = false;
   for (int k = 0; k < c->n_inst; ++k) {
@@ -276,6 +277,7 @@ iugkp_status rebuild_forward_groups(Ctx* c) {
       c->any_two_group = true;
       continue;
     }
+    c->all_two_group = false;
     const long long len = std::min<long long>(X, c->staged_cap);
     window[k] = make_int2((int)((X - len) / 2), (int)len);
     if (len < X) c->sync_partial = true;

@@ -94,6 +94,7 @@ struct Ctx {
   double* d_GX = nullptr;        // [total_bfaces]
   double* d_Fd = nullptr;        // [total_faces] faces derived from the group balances
   bool any_two_group = false;    // some instance of the context uses the two-group tallies
+  bool all_two_group = false;    // ... every instance does (no face follows from a column walk)
   bool sync_ok = false;          // 2D: the pass-synchronous staged kernel applies
   bool sync_partial = false;     // ... and some instance's x-faces exceed the window
   double* d_wallTf = nullptr;    // [total_bfaces]

@@ -5,6 +5,7 @@
 
 #include "device.cuh"
 #include "internal.h"
+#include "replay.cuh"
 
 namespace iugkp {
 
@@ -182,84 +183,179 @@ __device__ __forceinline__ void run_particle(const SweepArgs& A, long long pid, 
   walk_particle<Real, DIM>(A, in, G.inst, G.band, wk, st, cnt, pol);
 }
 
-// Tallies of a particle the staged sweep left to this FP64 replay: exactly those the staged
-// sweep would have made for it. W is summed as w (the staged sweep scales it by tau_maj
-// afterwards), and only from candidate k_done on (the earlier ones are tallied already).
-// Faces: those normal to the axes the staged sweep tallies (x in 1D; x and y in 3D; x in 2D,
-// or y for a y-group particle of a two-group instance), the wall faces among them included;
-// an exit through the low wall of an untallied axis goes to that wall's face (one-group
-// instances) or to the group's exit tally GX (two-group); a y-group particle's real
-// collision also enters its group balance DY. Emission needs nothing: the staged sweep and
-// its post-passes account for it.
-struct ReplayTally {
+// Deposit tallies of a replayed particle: W as w (the staged sweep scales it by tau_maj
+// afterwards), from candidate k_done on (the earlier ones were tallied by the staged sweep); R,
+// and the y-group balance DY for a y-group particle of a two-group instance.
+struct ReplayDeposits {
   const SweepArgs& A;
   const StagedArgs& S;
   const InstDesc& in;
   double w;
-  int k_done, dim;
-  bool two, yg;
-  __device__ bool tallied(int a) const { return dim == 1 || (two ? a == (yg ? 1 : 0) : a < dim - 1); }
-  __device__ bool candidate(int k, long long ci) {
-    if (k < k_done) return false;
+  int k_done;
+  bool ydy;
+  Counts& cnt;
+  __device__ void candidate(int k, long long ci, int) {
+    if (k < k_done) return;
+    cnt.v[CNT_CANDIDATES] += 1;
     if (A.W) atomicAdd(&A.W[ci], w);
-    return true;
   }
   __device__ void real(long long ci, int cell) {
+    cnt.v[CNT_REAL] += 1;
     atomicAdd(&A.R[ci], w);
-    if (two && yg) atomicAdd(&S.DY[in.cell_off + cell], w);
-  }
-  __device__ void cross(int a, int stp, long long face) {
-    if (A.F && tallied(a)) atomicAdd(&A.F[in.face_off + face], stp > 0 ? w : -w);
-  }
-  __device__ void exit(int a, int stp, long long face) {
-    if (!A.F || tallied(a) || stp > 0) return;
-    if (two) {
-      // the low wall's face index within its wall: the column (x-group, low y-wall) or the
-      // row (y-group, low x-wall)
-      const long long j = yg ? (face - in.fax_off[0]) / (in.n[0] + 1) : face - in.fax_off[1];
-      atomicAdd(&S.GX[in.bface_off + in.wface_off[yg ? 0 : 2] + j], -w);
-    } else {
-      atomicAdd(&A.F[in.face_off + face], -w);
-    }
+    if (ydy) atomicAdd(&S.DY[in.cell_off + cell], w);
   }
 };
 
-// FP64 replay of the particles the staged sweep deferred (one thread per queue entry). The
-// entry holds the staged sweep's forward index (particle q of emitter e, q-major within its
-// group) and the candidates it tallied before the decision it could not take in FP32.
+// Face index within the instance of face coordinate f along axis a, cell coordinates c[] on
+// the other axes.
+__device__ __forceinline__ long long face_at(const InstDesc& in, int a, int f, const int* c) {
+  if (a == 0) return in.fax_off[0] + f + (long long)(in.n[0] + 1) * (c[1] + (long long)in.n[1] * c[2]);
+  if (a == 1) return in.fax_off[1] + c[0] + (long long)in.n[0] * (f + (long long)(in.n[1] + 1) * c[2]);
+  return in.fax_off[2] + c[0] + (long long)in.n[0] * (c[1] + (long long)in.n[1] * f);
+}
+
+__device__ __forceinline__ double shfl_d(double x, int src) {
+  return __hiloint2double(__shfl_sync(0xffffffffu, __double2hiint(x), src),
+                          __shfl_sync(0xffffffffu, __double2loint(x), src));
+}
+
+// One thread per queue entry follows the particle's candidates in FP64 and makes its deposit
+// tallies; then the warp tallies the face items of its particles together, one particle at a
+// time (its segment broadcast from its lane), the lanes taking successive items. Faces
+// tallied: those the staged sweep tallies for this particle (x in 1D; x and y in 3D; x in 2D,
+// or y for a y-group particle of a two-group instance), the wall faces among them included;
+// an exit through the low wall of an untallied axis goes to that wall's face (one-group
+// instances) or to the group's exit tally GX (two-group). Emission needs nothing: the staged
+// sweep and its post-passes account for it.
 template <int DIM>
-__global__ void __launch_bounds__(128) replay_kernel(SweepArgs A, StagedArgs S) {
+__global__ void __launch_bounds__(256) replay_kernel(SweepArgs A, StagedArgs S) {
   Counts cnt;
 #pragma unroll
   for (int k = 0; k < CNT_N; ++k) cnt.v[k] = 0;
+  const int lane = threadIdx.x & 31;
   const unsigned n = min(*S.defer_n, S.defer_cap);
-  for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-    const uint2 ent = S.defer[i];
-    const int gi = find_group(A.groups, A.n_groups, (long long)ent.x);
-    const Group G = A.groups[gi];
-    const InstDesc& in = A.inst[G.inst];
-    const unsigned local = ent.x - (unsigned)G.first_particle;
-    const int q = (int)(local / (unsigned)G.n_emitters);
-    const int e = (int)(local - (unsigned)q * (unsigned)G.n_emitters);
-    const long long plain = G.first_particle + (long long)e * G.per_emitter + q;
-    int gj;
-    double w;
-    Walk<double, DIM> wk;
-    Stream st;
-    if (!emit_particle<double, DIM, false>(A, plain, gj, w, wk, st)) continue;
-    const bool two = DIM == 2 && A.F && S.window[G.inst].x == 0 && (long long)S.window[G.inst].y == in.nfaces;
-    ReplayTally pol{A, S, in, w, (int)(ent.y >> 1), DIM, two, (ent.y & 1u) != 0};
-    walk_particle<double, DIM>(A, in, G.inst, G.band, wk, st, cnt, pol);
+  const unsigned stride = gridDim.x * blockDim.x;
+  // all lanes of a warp run the same rounds (the face items are tallied by the whole warp)
+  for (unsigned i0 = blockIdx.x * blockDim.x + threadIdx.x - lane; i0 < n; i0 += stride) {
+    const unsigned i = i0 + lane;
+    // the lane's particle, kept for the face items
+    int kinst = 0, ex = 0, tall = 0;  // instance, exit axis (-1: real collision), tallied axes (bits)
+    double w = 0.0;
+    double t[3] = {0, 0, 0}, d[3] = {0, 0, 0}, id[3] = {0, 0, 0};
+    int idx[3] = {0, 0, 0}, step[3] = {1, 1, 1}, m[3] = {1, 1, 1}, items[3] = {0, 0, 0};
+    if (i < n) {
+      const uint2 ent = S.defer[i];
+      const Group G = A.groups[find_group(A.groups, A.n_groups, (long long)ent.x)];
+      const InstDesc& in = A.inst[G.inst];
+      const unsigned local = ent.x - (unsigned)G.first_particle;
+      const int q = (int)(local / (unsigned)G.n_emitters);
+      const int e = (int)(local - (unsigned)q * (unsigned)G.n_emitters);
+      int gj;
+      Walk<double, DIM> wk;
+      Stream st;
+      if (emit_particle<double, DIM, false>(A, G.first_particle + (long long)e * G.per_emitter + q, gj, w, wk, st)) {
+        Seg64<DIM> sg;
+        sg.init(wk, in);
+        const bool two = DIM == 2 && A.F && S.window[G.inst].x == 0 && (long long)S.window[G.inst].y == in.nfaces;
+        const bool yg = two && (ent.y & 1u);
+        ReplayDeposits pol{A, S, in, w, (int)(ent.y >> 1), yg, cnt};
+        int fb[DIM];
+        const int res = replay_candidates<DIM>(A, in, G.inst, G.band, wk, sg, st, fb, pol);
+        if (res < 0) {
+          cnt.v[CNT_DROPPED] += 1;
+          atomicOr(A.err, ERR_BUDGET);
+        } else {
+          // interior faces crossed per axis; at a wall the exit axis's are all of them
+          const bool exit = res == 0;
+          int c[3] = {0, 0, 0};
+#pragma unroll
+          for (int a = 0; a < DIM; ++a) {
+            c[a] = exit ? (a == sg.ex ? sg.m[a] - 1 : min(count_before64(sg.tex, sg.t[a], sg.id[a]), sg.m[a] - 1))
+                        : fb[a];
+            cnt.v[CNT_CROSSINGS] += c[a];
+            t[a] = sg.t[a];
+            d[a] = sg.d[a];
+            id[a] = sg.id[a];
+            idx[a] = wk.idx[a];
+            step[a] = wk.step[a];
+            m[a] = sg.m[a];
+          }
+          if (exit) cnt.v[CNT_WALL_EXITS] += 1;
+          kinst = G.inst;
+          ex = exit ? sg.ex : -1;
+          if (A.F) {
+#pragma unroll
+            for (int a = 0; a < DIM; ++a) {
+              const bool ta = DIM == 1 || (two ? a == (yg ? 1 : 0) : a < DIM - 1);
+              if (ta) {
+                tall |= 1 << a;
+                items[a] = c[a] + (exit && sg.ex == a ? 1 : 0);
+              }
+            }
+            if (exit && !((tall >> sg.ex) & 1) && wk.step[sg.ex] < 0) {
+              // exit through the low wall of an untallied axis
+              int cc[3] = {0, 0, 0};
+#pragma unroll
+              for (int a = 0; a < DIM; ++a) cc[a] = wk.idx[a] + wk.step[a] * c[a];
+              if (two) {
+                const int j = sg.ex == 1 ? cc[0] : cc[1];  // the low y-wall's column or the low x-wall's row
+                atomicAdd(&S.GX[in.bface_off + in.wface_off[sg.ex == 1 ? 2 : 0] + j], -w);
+              } else {
+                atomicAdd(&A.F[in.face_off + face_at(in, sg.ex, 0, cc)], -w);
+              }
+            }
+          }
+        }
+      }
+    }
+    // face items, particle by particle: item j along the tallied axis p is its j-th face, at
+    // path length t_p + j d_p; the cell there on each other axis follows from its face count
+    unsigned pend = __ballot_sync(0xffffffffu, tall != 0);
+    while (pend) {
+      const int src = __ffs(pend) - 1;
+      pend &= pend - 1;
+      const int k = __shfl_sync(0xffffffffu, kinst, src);
+      const InstDesc& in = A.inst[k];
+      const double ws = shfl_d(w, src);
+      const int tl = __shfl_sync(0xffffffffu, tall, src);
+      double ts[3], ds[3], is[3];
+      int xs[3], ss[3], ms[3], ns[3];
+#pragma unroll
+      for (int a = 0; a < DIM; ++a) {
+        ts[a] = shfl_d(t[a], src);
+        ds[a] = shfl_d(d[a], src);
+        is[a] = shfl_d(id[a], src);
+        xs[a] = __shfl_sync(0xffffffffu, idx[a], src);
+        ss[a] = __shfl_sync(0xffffffffu, step[a], src);
+        ms[a] = __shfl_sync(0xffffffffu, m[a], src);
+        ns[a] = __shfl_sync(0xffffffffu, items[a], src);
+      }
+#pragma unroll
+      for (int p = 0; p < DIM; ++p) {
+        if (!((tl >> p) & 1)) continue;
+        const double sgn = ss[p] > 0 ? ws : -ws;
+        for (int j = lane; j < ns[p]; j += 32) {
+          const double T = ts[p] + (double)j * ds[p];
+          int cc[3] = {0, 0, 0};
+#pragma unroll
+          for (int a = 0; a < DIM; ++a)
+            if (a != p) cc[a] = xs[a] + ss[a] * min(count_before64(T, ts[a], is[a]), ms[a] - 1);
+          const int f = ss[p] > 0 ? xs[p] + 1 + j : xs[p] - j;
+          atomicAdd(&A.F[in.face_off + face_at(in, p, f, cc)], sgn);
+        }
+      }
+    }
+    (void)ex;
   }
   flush_counts(cnt, A.counters);
 }
 
 cudaError_t launch_replay(const Ctx* c, const SweepArgs& a, const StagedArgs& S, cudaStream_t s) {
-  const int blocks = c->sm_count * 4;
+  const int blocks = c->sm_count * 8;
   switch (c->dim) {
-    case 1: replay_kernel<1><<<blocks, 128, 0, s>>>(a, S); break;
-    case 2: replay_kernel<2><<<blocks, 128, 0, s>>>(a, S); break;
-    default: replay_kernel<3><<<blocks, 128, 0, s>>>(a, S); break;
+    case 1: replay_kernel<1><<<blocks, 256, 0, s>>>(a, S); break;
+    case 2: replay_kernel<2><<<blocks, 256, 0, s>>>(a, S); break;
+    default: replay_kernel<3><<<blocks, 256, 0, s>>>(a, S); break;
   }
   return cudaGetLastError();
 }

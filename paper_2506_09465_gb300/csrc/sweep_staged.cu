@@ -1327,19 +1327,31 @@ __global__ void __launch_bounds__(STAGED_NT, 1) adjoint_sync_kernel(SweepArgs A,
   flush_lcounts(cnt, A.counters);
 }
 
+// Absorbed minus emitted power of every cell, sum_b R_b - V m T_emit (T_emit = T + Q/m), in
+// one pass over the [band][cell] tallies (coalesced; the column walk below then reads one
+// value per cell instead of one per band).
+__global__ void cell_balance_kernel(const InstDesc* inst, int n_inst, int nb, long long total, const double* T,
+                                    const double* srcshift, const double* Vm, const double* R, double* out) {
+  for (long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x; g < total; g += (long long)gridDim.x * blockDim.x) {
+    int k = 0;
+    while (k + 1 < n_inst && inst[k + 1].cell_off <= g) ++k;
+    const InstDesc& in = inst[k];
+    const long long c = g - in.cell_off;
+    double r = 0.0;
+    for (int b = 0; b < nb; ++b) r += R[in.bc_off + (long long)b * in.ncells + c];
+    double te = T[g];
+    if (srcshift) te += srcshift[g];
+    out[g] = r - Vm[g] * te;
+  }
+}
+
 // Faces normal to the last axis from per-cell conservation, one thread per column:
 // F[k+1] = F[k] + (net inflow through the other axes' faces of cell k) - (R_k - S_k),
-// S_k = V m T_emit (emitted thermal and source power), starting from the tallied low
-// boundary face.
+// S_k = V m T_emit (emitted thermal and source power; bal = R - S from cell_balance_kernel),
+// starting from the tallied low boundary face.
 template <int DIM>
-__device__ __forceinline__ double column_step(const InstDesc& in, int nb, const double* T, const double* srcshift,
-                                              const double* Vm, const double* R, const double* Fi, long long c) {
+__device__ __forceinline__ double column_step(const InstDesc& in, const double* bal, const double* Fi, long long c) {
   const int n0 = in.n[0], n1 = in.n[1];
-  const long long g = in.cell_off + c;
-  double r = 0.0;
-  for (int b = 0; b < nb; ++b) r += R[in.bc_off + (long long)b * in.ncells + c];
-  double te = T[g];
-  if (srcshift) te += srcshift[g];
   const long long row = c / n0;  // x-face index of the cell's low face = c + row
   double inflow = Fi[in.fax_off[0] + c + row] - Fi[in.fax_off[0] + c + row + 1];
   if (DIM == 3) {
@@ -1347,7 +1359,7 @@ __device__ __forceinline__ double column_step(const InstDesc& in, int nb, const 
     const long long fy = in.fax_off[1] + c + (long long)n0 * cz;
     inflow += Fi[fy] - Fi[fy + n0];
   }
-  return inflow - (r - Vm[g] * te);
+  return inflow - bal[in.cell_off + c];
 }
 
 // Block: 32 adjacent columns x DERIVE_SEG segments (one warp per segment, so loads are
@@ -1362,10 +1374,9 @@ __device__ __forceinline__ bool two_group(const InstDesc& in, const int2* window
 }
 
 template <int DIM>
-__global__ void __launch_bounds__(32 * DERIVE_SEG) derive_last_axis_kernel(const InstDesc* inst, int n_inst, int nb,
-                                                                         const int2* window, const double* T,
-                                                                         const double* srcshift, const double* Vm,
-                                                                         const double* R, double* F) {
+__global__ void __launch_bounds__(32 * DERIVE_SEG) derive_last_axis_kernel(const InstDesc* inst, int n_inst,
+                                                                         const int2* window, const double* bal,
+                                                                         double* F) {
   __shared__ double segsum[DERIVE_SEG][32];
   const int k = blockIdx.y;
   if (k >= n_inst) return;
@@ -1386,7 +1397,7 @@ __global__ void __launch_bounds__(32 * DERIVE_SEG) derive_last_axis_kernel(const
     const long long base_cell = DIM == 2 ? ix : ix + (long long)n0 * iy;
     double part = 0.0;
     if (ok)
-      for (int kk = k0; kk < k1; ++kk) part += column_step<DIM>(in, nb, T, srcshift, Vm, R, Fi, base_cell + kk * stride);
+      for (int kk = k0; kk < k1; ++kk) part += column_step<DIM>(in, bal, Fi, base_cell + kk * stride);
     segsum[seg][lane] = part;
     __syncthreads();
     if (ok) {
@@ -1396,7 +1407,7 @@ __global__ void __launch_bounds__(32 * DERIVE_SEG) derive_last_axis_kernel(const
       for (int sg = 0; sg < seg; ++sg) acc += segsum[sg][lane];
       for (int kk = k0; kk < k1; ++kk) {
         const long long c = base_cell + kk * stride;
-        acc += column_step<DIM>(in, nb, T, srcshift, Vm, R, Fi, c);
+        acc += column_step<DIM>(in, bal, Fi, c);
         const long long fn = DIM == 2 ? in.fax_off[1] + c + n0 : in.fax_off[2] + c + (long long)n0 * n1;
         Fi[fn] = acc;
       }
@@ -1702,17 +1713,20 @@ cudaError_t launch_sweep_staged(const Ctx* c, const SweepArgs& a, cudaStream_t s
                                                                            c->d_wall_unit, c->d_wallTf, a.F);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
-  if (a.F && c->dim >= 2) {
+  if (a.F && c->dim >= 2 && !c->all_two_group) {
     // one block per 32 columns of the largest instance (columns of the last axis)
     long long maxcol = 0;
     for (const InstDesc& in : c->h_inst) maxcol = std::max<long long>(maxcol, in.ncells / (c->dim == 2 ? in.n[1] : in.n[2]));
     dim3 grid((unsigned)std::min<long long>((maxcol + 31) / 32, 4096), (unsigned)c->n_inst);
+    // absorbed minus emitted power per cell, into the correction solve's scratch (free until
+    // the Newton step, which runs after the sweep on the same stream)
+    cell_balance_kernel<<<c->sm_count * 4, 256, 0, s>>>(c->d_inst, c->n_inst, c->nb, c->total_cells, a.T, a.srcshift,
+                                                        c->d_Vm, a.R, c->d_work);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
     if (c->dim == 2)
-      derive_last_axis_kernel<2><<<grid, 32 * DERIVE_SEG, 0, s>>>(c->d_inst, c->n_inst, c->nb, c->d_window, a.T,
-                                                                  a.srcshift, c->d_Vm, a.R, a.F);
+      derive_last_axis_kernel<2><<<grid, 32 * DERIVE_SEG, 0, s>>>(c->d_inst, c->n_inst, c->d_window, c->d_work, a.F);
     else
-      derive_last_axis_kernel<3><<<grid, 32 * DERIVE_SEG, 0, s>>>(c->d_inst, c->n_inst, c->nb, c->d_window, a.T,
-                                                                  a.srcshift, c->d_Vm, a.R, a.F);
+      derive_last_axis_kernel<3><<<grid, 32 * DERIVE_SEG, 0, s>>>(c->d_inst, c->n_inst, c->d_window, c->d_work, a.F);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }
