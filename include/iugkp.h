@@ -158,9 +158,16 @@ iugkp_status iugkp_get_layout(const iugkp_ctx *ctx, iugkp_layout *lay, long long
  * non-uniform walls such as the heated segment of Sec. 4.5; instance-major, walls in the
  * order -x, +x, -y, +y, -z, +z, on the wall normal to axis a the faces run over the axes
  * (a+1)%3 and (a+2)%3, the first fastest). Wall emission per face is C_b v_b T_face A / 4
- * (Sec. 4 black isothermal walls, per face). `data` is host memory unless on_device != 0
- * (then read back, synchronising cuda_stream). Values must be finite (EINVAL). */
-enum { IUGKP_FIELD_SOURCE = 0, IUGKP_FIELD_WALL_T = 1, IUGKP_FIELD_WALL_FACE_T = 2 };
+ * (Sec. 4 black isothermal walls, per face). IUGKP_FIELD_TAU ([instance][band][cell], the
+ * layout of iugkp_create_batch's tau: finite and > 0) replaces the relaxation times tau(omega,
+ * x) (Sec. 3.2, spatially varying tau): the band split of the particles, the emitter weights,
+ * the per-band majorant and acceptance ratios, kappa and the Newton correction's operator and
+ * damping, and the source shift are rebuilt exactly as iugkp_create_batch would build them
+ * (device buffers are reallocated; the wall temperatures, per-face ones included, the source
+ * and the options carry over; a persistent population must be reset again). `data` is host
+ * memory unless on_device != 0 (then read back, synchronising cuda_stream). Values must be
+ * finite (EINVAL). */
+enum { IUGKP_FIELD_SOURCE = 0, IUGKP_FIELD_WALL_T = 1, IUGKP_FIELD_WALL_FACE_T = 2, IUGKP_FIELD_TAU = 3 };
 iugkp_status iugkp_set_field(iugkp_ctx *ctx, int which, const double *data, int on_device,
                              void *cuda_stream);
 
@@ -186,10 +193,14 @@ iugkp_status iugkp_macro(iugkp_ctx *ctx, const double *R_dev, const double *W_de
                          double *T_half_dev, double *T_E_dev, void *cuda_stream);
 
 /* Inexact-Newton correction (Sec. 3.3): s = (sum_b R_b - sum_b C_b T_n V / tau_b) / V,
- * solves -div(kappa grad dT) = s by Jacobi-preconditioned CG (FP64) and sets
- * T_half += theta dT (theta = min(1, 1.5 / cell optical thickness)). Synchronises
- * the stream to read the CG status; *cg_iters_out (may be NULL) gets the largest
- * iteration count over instances. ENOCONV if cg_maxit is reached. */
+ * solves -div(kappa grad dT) = s to ||s - A dT|| <= cg_rtol ||s|| and sets T_half += theta dT
+ * (theta = min(1, 1.5 / cell optical thickness)). Solver: CG preconditioned by one
+ * aggregation-multigrid V-cycle in FP32, one thread-block cluster per instance. For
+ * cg_rtol >= 1e-5 (the default 1e-3) the CG iterates are FP32 inside FP64 iterative
+ * refinement: the solution is accumulated in FP64 and its residual s - A dT is formed and
+ * measured in FP64, which is what cg_rtol bounds; below 1e-5 the CG iterates and residual
+ * are FP64. Synchronises the stream to read the CG status; *cg_iters_out (may be NULL) gets
+ * the largest iteration count over instances. ENOCONV if cg_maxit is reached. */
 iugkp_status iugkp_newton_step(iugkp_ctx *ctx, const double *T_n_dev, double *T_half_inout_dev,
                                const double *R_dev, void *cuda_stream, int *cg_iters_out);
 
@@ -317,8 +328,10 @@ iugkp_status iugkp_adjoint(iugkp_ctx *ctx, const double *T_star_dev, const doubl
  * process exits. Larger grids return IUGKP_EINVAL. Every call reuses that array, so
  * calls whose work overlaps on the GPU (two streams, two host threads) race. The first
  * call on a device looks the array's address up once with that device current; make
- * that first call before any stream capture. Synchronises cuda_stream to read the
- * iteration count; IUGKP_ENOCONV if maxit is reached. Errors: iugkp_last_error(NULL). */
+ * that first call before any stream capture. Every call synchronises cuda_stream to read
+ * the iteration count back. IUGKP_ENOCONV if maxit is reached; IUGKP_EINVAL (x_dev then
+ * holds no solution) if some kappa is not positive and finite, or if a non-finite value
+ * arises from rhs_dev. Errors: iugkp_last_error(NULL). */
 #define IUGKP_NOALLOC_MAX_CELLS 65536
 iugkp_status iugkp_diffusion_solve_noalloc(const iugkp_grid *g, const double *kappa_dev, double wall_cv,
                                            const double *rhs_dev, double *x_dev, double rtol, int maxit,

@@ -16,7 +16,7 @@ TRACK_FP64, TRACK_FP32 = 0, 1
 TALLY_FP64, TALLY_STAGED, TALLY_STAGED_K32 = 0, 1, 2
 DRAWS_FRESH, DRAWS_FROZEN = 0, 1
 SCHED_PLAIN, SCHED_PERSISTENT = 0, 1
-FIELD_SOURCE, FIELD_WALL_T, FIELD_WALL_FACE_T = 0, 1, 2
+FIELD_SOURCE, FIELD_WALL_T, FIELD_WALL_FACE_T, FIELD_TAU = 0, 1, 2, 3
 
 
 class Grid(ctypes.Structure):

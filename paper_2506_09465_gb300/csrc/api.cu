@@ -376,6 +376,7 @@ iugkp_status iugkp_create_batch(int n, const iugkp_grid* g, const double* const*
   c->opt = *o;
   c->n_inst = n;
   c->dim = dim;
+  c->h_grids.assign(g, g + n);
   c->nb = b->nb;
   c->h_C.assign(b->C, b->C + b->nb);
   c->h_v.assign(b->v, b->v + b->nb);
@@ -926,6 +927,52 @@ iugkp_status pcg_status(Ctx* c, cudaStream_t s, int* iters) {
   return IUGKP_OK;
 }
 
+// New relaxation times: every tau-dependent part of the context (band split of the particles,
+// emitter groups, weights, majorants and acceptance ratios, m, the diffusion operator and its
+// multigrid hierarchy, the Newton damping, the source shift Q/m) is rebuilt by creating the
+// context afresh from its grids, bands, options, wall temperatures (per face) and source, and
+// the fresh state replaces the old one (whose buffers are freed).
+iugkp_status set_tau(iugkp_ctx* ctx, const std::vector<double>& tau) {
+  Ctx* c = &ctx->c;
+  for (double x : tau)
+    if (!(x > 0.0)) return fail(c, IUGKP_EINVAL, "tau must be finite and > 0");
+  std::vector<double> Q((size_t)c->total_cells);
+  CK(cudaMemcpy(Q.data(), c->d_source, Q.size() * sizeof(double), cudaMemcpyDeviceToHost), "source readback");
+  const int n = c->n_inst;
+  std::vector<const double*> taus(n), walls(n), srcs(n);
+  for (int k = 0; k < n; ++k) {
+    const InstDesc& in = c->h_inst[k];
+    taus[k] = tau.data() + in.bc_off;
+    walls[k] = c->h_wallT.data() + in.wall_off;
+    srcs[k] = Q.data() + in.cell_off;
+  }
+  const iugkp_bands bands{c->nb, c->h_C.data(), c->h_v.data()};
+  iugkp_ctx* fresh = nullptr;
+  const iugkp_status st =
+      iugkp_create_batch(n, c->h_grids.data(), taus.data(), &bands, walls.data(), srcs.data(), &c->opt, &fresh);
+  if (st != IUGKP_OK) return fail(c, st, std::string("tau: rebuilding the context: ") + iugkp_last_error(nullptr));
+  Ctx* f = &fresh->c;
+  if (f->h_wallTf != c->h_wallTf) {  // per-face wall temperatures set since creation
+    f->h_wallTf = c->h_wallTf;
+    iugkp_status ws = IUGKP_OK;
+    if (cudaMemcpy(f->d_wallTf, f->h_wallTf.data(), f->h_wallTf.size() * sizeof(double), cudaMemcpyHostToDevice) !=
+        cudaSuccess) {
+      cudaGetLastError();
+      ws = fail(c, IUGKP_ECUDA, "tau: wall face upload");
+    } else {
+      ws = rebuild_forward_groups(f);
+      if (ws != IUGKP_OK) fail(c, ws, f->err);
+    }
+    if (ws != IUGKP_OK) {
+      iugkp_destroy(fresh);
+      return ws;
+    }
+  }
+  std::swap(ctx->c, fresh->c);
+  iugkp_destroy(fresh);  // frees the old state
+  return IUGKP_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -936,7 +983,8 @@ iugkp_status iugkp_set_field(iugkp_ctx* ctx, int which, const double* data, int 
   cudaStream_t s = (cudaStream_t)cuda_stream;
   size_t count = which == IUGKP_FIELD_SOURCE ? (size_t)c->total_cells
                  : which == IUGKP_FIELD_WALL_T ? (size_t)c->total_walls
-                 : which == IUGKP_FIELD_WALL_FACE_T ? (size_t)c->total_bfaces : 0;
+                 : which == IUGKP_FIELD_WALL_FACE_T ? (size_t)c->total_bfaces
+                 : which == IUGKP_FIELD_TAU ? (size_t)c->nb * c->total_cells : 0;
   if (!count) return fail(c, IUGKP_EINVAL, "unknown field");
   std::vector<double> h(count);
   if (on_device) {
@@ -948,6 +996,7 @@ iugkp_status iugkp_set_field(iugkp_ctx* ctx, int which, const double* data, int 
   for (double x : h)
     if (!std::isfinite(x)) return fail(c, IUGKP_EINVAL, "field values must be finite");
   CK(cudaStreamSynchronize(s), "field sync");
+  if (which == IUGKP_FIELD_TAU) return set_tau(ctx, h);
   if (which == IUGKP_FIELD_SOURCE) {
     CK(cudaMemcpy(c->d_source, h.data(), count * sizeof(double), cudaMemcpyHostToDevice), "source upload");
     std::vector<double> m(count);

@@ -71,6 +71,7 @@ struct Ctx {
   std::vector<long long> h_nband, h_nwall;
   std::vector<double> h_theta;      // per instance damping of the Newton correction
   std::vector<double> h_Vcell;      // per instance cell volume
+  std::vector<iugkp_grid> h_grids;  // the grids the context was created with
 
   // device buffers
   InstDesc* d_inst = nullptr;

@@ -464,13 +464,44 @@ __device__ void vcycle_f32(const MGArgs& A, const InstMG& m, cg::cluster_group& 
   for (int l = ls - 1; l >= 0; --l) vup<ClusterTeam, NT, CS>(A, m, l, global_view(A, m, l), global_view(A, m, l + 1), all, cl);
 }
 
+// The FP64 residual b - A x of the FP64 iterate over this CTA's cells, into Rt (FP64 fine
+// operator); returns this thread's share of its squared norm.
+__device__ __forceinline__ double true_residual(const MGArgs& A, const InstMG& m, double* Rt, long long off,
+                                                long long lo, long long hi, long long n, int NT) {
+  const long long sy = m.n[0][0], sz = (long long)m.n[0][0] * m.n[0][1];
+  double rr = 0.0;
+  for (long long i = lo + threadIdx.x; i < hi; i += NT) {
+    const long long g = off + i;
+    double q = A.diag[g] * __ldcg(&A.X[g]);
+    if (i + 1 < n) q -= A.cx[g] * __ldcg(&A.X[g + 1]);
+    if (i >= 1) q -= A.cx[g - 1] * __ldcg(&A.X[g - 1]);
+    if (m.dim >= 2) {
+      if (i + sy < n) q -= A.cy[g] * __ldcg(&A.X[g + sy]);
+      if (i >= sy) q -= A.cy[g - sy] * __ldcg(&A.X[g - sy]);
+    }
+    if (m.dim >= 3) {
+      if (i + sz < n) q -= A.cz[g] * __ldcg(&A.X[g + sz]);
+      if (i >= sz) q -= A.cz[g - sz] * __ldcg(&A.X[g - sz]);
+    }
+    const double r = A.rhs[g] - q;
+    Rt[g] = r;
+    rr += r * r;
+  }
+  return rr;
+}
+
 // PCG with FP32 iterates for tolerances far above FP32's rounding (the correction is an
-// inexact Newton step: its tolerance sets the cost, not the fixed point). The right-hand
-// side is scaled to unit norm (its norm in FP64), so the FP32 sums neither underflow nor
-// overflow; the stencil product uses the FP32 copy of the fine operator (the hierarchy's
-// finest level); dot products are FP32 per thread and FP64 across the cluster; the solution
-// is scaled back into the FP64 X. On GB300 FP64 arithmetic issues on a narrow pipe, so the
-// FP64 iterates' products and updates lengthen every phase of the iteration.
+// inexact Newton step: its tolerance sets the cost, not the fixed point), inside FP64
+// iterative refinement: the solution is accumulated in FP64 and its residual b - A x is
+// formed and measured in FP64 with the FP64 operator; while that residual exceeds the
+// tolerance (at most MG32_PASSES times) the FP32 PCG solves for the correction of that
+// residual. Each pass scales its right-hand side to unit norm (so the FP32 sums neither
+// underflow nor overflow); the stencil product uses the FP32 copy of the fine operator (the
+// hierarchy's finest level); dot products are FP32 per thread and FP64 across the cluster.
+// On GB300 FP64 arithmetic issues on a narrow pipe, so FP64 iterates would lengthen every
+// phase of the iteration; here FP64 enters once per pass.
+constexpr int MG32_PASSES = 4;
+
 template <int NT, int CS>
 __global__ void __launch_bounds__(NT, 1) mgpcg32_kernel(MGArgs A, float* V32) {
   __shared__ double sh[4 * 32];
@@ -490,81 +521,96 @@ __global__ void __launch_bounds__(NT, 1) mgpcg32_kernel(MGArgs A, float* V32) {
   const float *dg = A.ldiag + m.off[0], *cx = A.lcx + m.off[0], *cy = A.lcy + m.off[0], *cz = A.lcz + m.off[0];
   ClusterRed<NT, CS> red{slot, 0};
   double v[4];
+  // x = 0, FP64 residual r = b
   v[0] = 0.0;
   for (long long i = lo + threadIdx.x; i < hi; i += NT) {
     const double bi = A.rhs[off + i];
+    A.X[off + i] = 0.0;
+    A.Z[off + i] = bi;
     v[0] += bi * bi;
   }
   red.sum(cl, v, 1, sh);
   const double bb = v[0];
   if (bb == 0.0) {
-    for (long long i = lo + threadIdx.x; i < hi; i += NT) A.X[off + i] = 0.0;
     if (rank == 0 && threadIdx.x == 0) A.iters_out[k] = 0;
     return;
   }
-  const double bn = sqrt(bb), sc = 1.0 / bn;
-  for (long long i = lo + threadIdx.x; i < hi; i += NT) {
-    R[i] = (float)(A.rhs[off + i] * sc);
-    X[i] = 0.f;
-  }
-  cl.sync();
-  const double tol2 = A.rtol * A.rtol;  // of the unit-norm right-hand side
-  vcycle_f32<NT, CS>(A, m, cl, rank, mg_smem);
-  float f0 = 0.f;
-  for (long long i = lo + threadIdx.x; i < hi; i += NT) {
-    const float zi = Z[i];
-    P[i] = zi;
-    f0 += R[i] * zi;
-  }
-  v[0] = f0;
-  red.sum(cl, v, 1, sh);  // also orders the P writes before the first product
-  double rz = v[0];
+  const double tol2 = A.rtol * A.rtol * bb;
+  double rr = bb;  // FP64 squared norm of the FP64 residual
   int it = 0;
   bool done = false;
-  while (it < A.maxit) {
-    ++it;
-    f0 = 0.f;
+  for (int pass = 0; pass < MG32_PASSES && it < A.maxit; ++pass) {
+    // FP32 PCG for A e = r (scaled to unit norm) to the relative tolerance the FP64 residual
+    // still needs, at least the requested one and at most 1/2
+    const double rn = sqrt(rr), sc = 1.0 / rn;
+    const double rin = fmin(0.5, fmax(A.rtol, A.rtol * sqrt(bb) / rn));
+    const double in2 = rin * rin;
     for (long long i = lo + threadIdx.x; i < hi; i += NT) {
-      const float q = level_apply<ClusterTeam>(dg, cx, cy, cz, P, m.n[0], m.dim, i, n);
-      Q[i] = q;
-      f0 += __ldcg(&P[i]) * q;
+      R[i] = (float)(A.Z[off + i] * sc);
+      X[i] = 0.f;
+    }
+    cl.sync();
+    vcycle_f32<NT, CS>(A, m, cl, rank, mg_smem);
+    float f0 = 0.f;
+    for (long long i = lo + threadIdx.x; i < hi; i += NT) {
+      const float zi = Z[i];
+      P[i] = zi;
+      f0 += R[i] * zi;
     }
     v[0] = f0;
-    red.sum(cl, v, 1, sh);
-    const double alpha = rz / v[0];
-    const float af = (float)alpha;
-    f0 = 0.f;
-    for (long long i = lo + threadIdx.x; i < hi; i += NT) {
-      X[i] += af * P[i];
-      const float ri = R[i] - af * Q[i];
-      R[i] = ri;
-      f0 += ri * ri;
+    red.sum(cl, v, 1, sh);  // also orders the P writes before the first product
+    double rz = v[0];
+    while (it < A.maxit) {
+      ++it;
+      f0 = 0.f;
+      for (long long i = lo + threadIdx.x; i < hi; i += NT) {
+        const float q = level_apply<ClusterTeam>(dg, cx, cy, cz, P, m.n[0], m.dim, i, n);
+        Q[i] = q;
+        f0 += __ldcg(&P[i]) * q;
+      }
+      v[0] = f0;
+      red.sum(cl, v, 1, sh);
+      const double alpha = rz / v[0];
+      const float af = (float)alpha;
+      f0 = 0.f;
+      for (long long i = lo + threadIdx.x; i < hi; i += NT) {
+        X[i] += af * P[i];
+        const float ri = R[i] - af * Q[i];
+        R[i] = ri;
+        f0 += ri * ri;
+      }
+      v[0] = f0;
+      red.sum(cl, v, 1, sh);  // also orders the residual's writes before the V-cycle
+      if (v[0] <= in2) break;
+      vcycle_f32<NT, CS>(A, m, cl, rank, mg_smem);
+      // flexible (Polak-Ribiere) beta, as in the FP64 kernel
+      float f1 = 0.f;
+      f0 = 0.f;
+      for (long long i = lo + threadIdx.x; i < hi; i += NT) {
+        const float zi = Z[i];
+        f0 += R[i] * zi;
+        f1 += Q[i] * zi;
+      }
+      v[0] = f0;
+      v[1] = f1;
+      red.sum(cl, v, 2, sh);
+      const double beta = -alpha * v[1] / rz;
+      rz = v[0];
+      const float bf = (float)beta;
+      for (long long i = lo + threadIdx.x; i < hi; i += NT) P[i] = Z[i] + bf * P[i];
+      cl.sync();
     }
-    v[0] = f0;
-    red.sum(cl, v, 1, sh);  // also orders the residual's writes before the V-cycle
-    if (v[0] <= tol2) {
+    // x += rn e in FP64, then the FP64 residual of x
+    for (long long i = lo + threadIdx.x; i < hi; i += NT) A.X[off + i] += (double)X[i] * rn;
+    cl.sync();
+    v[0] = true_residual(A, m, A.Z, off, lo, hi, n, NT);
+    red.sum(cl, v, 1, sh);  // also orders the residual's writes before the next pass
+    rr = v[0];
+    if (rr <= tol2) {
       done = true;
       break;
     }
-    vcycle_f32<NT, CS>(A, m, cl, rank, mg_smem);
-    // flexible (Polak-Ribiere) beta, as in the FP64 kernel
-    float f1 = 0.f;
-    f0 = 0.f;
-    for (long long i = lo + threadIdx.x; i < hi; i += NT) {
-      const float zi = Z[i];
-      f0 += R[i] * zi;
-      f1 += Q[i] * zi;
-    }
-    v[0] = f0;
-    v[1] = f1;
-    red.sum(cl, v, 2, sh);
-    const double beta = -alpha * v[1] / rz;
-    rz = v[0];
-    const float bf = (float)beta;
-    for (long long i = lo + threadIdx.x; i < hi; i += NT) P[i] = Z[i] + bf * P[i];
-    cl.sync();
   }
-  for (long long i = lo + threadIdx.x; i < hi; i += NT) A.X[off + i] = (double)X[i] * bn;
   if (rank == 0 && threadIdx.x == 0) A.iters_out[k] = done ? it : -1;
 }
 
@@ -635,7 +681,8 @@ cudaError_t launch_mgpcg(const Ctx* c, const double* rhs, cudaStream_t s) {
   cfg.attrs = attr;
   cfg.numAttrs = 1;
   if (c->opt.cg_rtol >= MG32_MIN_RTOL) {
-    // FP32 x, p, q in the space of the FP64 r, p, q, z (4 n doubles >= 3 n floats)
+    // FP32 x, p, q in the space of the FP64 r and p (2 n doubles = 4 n floats >= 3 n floats);
+    // the FP64 residual of the refinement in that of z
     float* v32 = reinterpret_cast<float*>(c->d_pcg + c->total_cells);
     return cudaLaunchKernelEx(&cfg, mgpcg32_kernel<MG_NT, MG_CS>, a, v32);
   }

@@ -25,7 +25,8 @@
 namespace {
 
 constexpr long long kMaxCells = IUGKP_NOALLOC_MAX_CELLS;
-// Layout: diag, cx, cy, cz, r, p, q (7 x kMaxCells doubles), then the iteration count.
+// Layout: diag, cx, cy, cz, r, p, q (7 x kMaxCells doubles), then the iteration count and a
+// flag set when some kappa is not positive and finite.
 constexpr long long kScratchDoubles = 7 * kMaxCells + 32;
 
 __device__ __align__(256) double g_noalloc_scratch[kScratchDoubles];
@@ -58,9 +59,11 @@ struct NGrid {
 
 // Stencil of -div(kappa grad x) per cell: harmonic face kappa over h^2 between cells; at
 // a wall the half-cell conduction in series with the vacuum condition (flux = cv/2 x).
+// A kappa that is not positive and finite sets *bad (the solve then stops before iterating).
 __global__ void noalloc_stencil_kernel(NGrid g, const double* kappa, double cv, double* diag, double* cx, double* cy,
-                                       double* cz) {
+                                       double* cz, double* bad) {
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < g.nc; i += (long long)gridDim.x * blockDim.x) {
+    if (!(kappa[i] > 0.0) || !isfinite(kappa[i])) *bad = 1.0;
     const int ix = (int)(i % g.n0), iy = (int)((i / g.n0) % g.n1), iz = (int)(i / ((long long)g.n0 * g.n1));
     const int idx[3] = {ix, iy, iz};
     const int n[3] = {g.n0, g.n1, g.n2};
@@ -104,14 +107,19 @@ __device__ __forceinline__ double nblock_sum(double x, double* sh) {
   return sh[32];
 }
 
-// Jacobi-preconditioned CG, one block, x0 = 0 (x is cleared here). Writes the iteration
-// count (or -1 when maxit is reached) into *iters.
+// Jacobi-preconditioned CG, one block, x0 = 0 (x is cleared here). Writes into *iters the
+// iteration count, -1 when maxit is reached, -2 when a kappa was not positive and finite
+// (nothing solved), -3 when a product or residual turned out not finite (NaN or Inf in rhs).
 __global__ void __launch_bounds__(1024) noalloc_pcg_kernel(NGrid g, const double* diag, const double* cx,
                                                            const double* cy, const double* cz, const double* b,
                                                            double* x, double* r, double* p, double* q, double rtol,
                                                            int maxit, double* iters) {
   __shared__ double sh[33];
   const long long n = g.nc, sy = g.n0, sz = (long long)g.n0 * g.n1;
+  if (iters[1] != 0.0) {
+    if (threadIdx.x == 0) iters[0] = -2.0;
+    return;
+  }
   double bb = 0.0, rz = 0.0;
   for (long long i = threadIdx.x; i < n; i += blockDim.x) {
     const double bi = b[i];
@@ -123,13 +131,14 @@ __global__ void __launch_bounds__(1024) noalloc_pcg_kernel(NGrid g, const double
   }
   bb = nblock_sum(bb, sh);
   rz = nblock_sum(rz, sh);
-  if (bb == 0.0) {
-    if (threadIdx.x == 0) iters[0] = 0.0;
+  if (bb == 0.0 || !isfinite(bb)) {
+    for (long long i = threadIdx.x; i < n; i += blockDim.x) x[i] = 0.0;
+    if (threadIdx.x == 0) iters[0] = bb == 0.0 ? 0.0 : -3.0;
     return;
   }
   const double tol2 = rtol * rtol * bb;
   int it = 0;
-  bool done = false;
+  bool done = false, bad = false;
   while (it < maxit) {
     ++it;
     double pq = 0.0;
@@ -149,6 +158,10 @@ __global__ void __launch_bounds__(1024) noalloc_pcg_kernel(NGrid g, const double
       pq += p[i] * qi;
     }
     pq = nblock_sum(pq, sh);
+    if (!isfinite(pq) || !(pq > 0.0)) {  // the operator is positive definite: anything else is bad data
+      bad = true;
+      break;
+    }
     const double alpha = rz / pq;
     double rr = 0.0, rzn = 0.0;
     for (long long i = threadIdx.x; i < n; i += blockDim.x) {
@@ -160,6 +173,10 @@ __global__ void __launch_bounds__(1024) noalloc_pcg_kernel(NGrid g, const double
     }
     rr = nblock_sum(rr, sh);
     rzn = nblock_sum(rzn, sh);
+    if (!isfinite(rr)) {
+      bad = true;
+      break;
+    }
     if (rr <= tol2) {
       done = true;
       break;
@@ -169,7 +186,7 @@ __global__ void __launch_bounds__(1024) noalloc_pcg_kernel(NGrid g, const double
     for (long long i = threadIdx.x; i < n; i += blockDim.x) p[i] = r[i] / diag[i] + beta * p[i];
     __syncthreads();
   }
-  if (threadIdx.x == 0) iters[0] = done ? (double)it : -1.0;
+  if (threadIdx.x == 0) iters[0] = bad ? -3.0 : (done ? (double)it : -1.0);
 }
 
 }  // namespace
@@ -210,7 +227,9 @@ extern "C" iugkp_status iugkp_diffusion_solve_noalloc(const iugkp_grid* grid, co
   double* it = base + 7 * kMaxCells;
   unsigned blocks = (unsigned)((g.nc + 255) / 256);
   if (blocks > 1024) blocks = 1024;
-  noalloc_stencil_kernel<<<blocks, 256, 0, s>>>(g, kappa_dev, wall_cv, diag, cx, cy, cz);
+  if ((e = cudaMemsetAsync(it + 1, 0, sizeof(double), s)) != cudaSuccess)
+    return fail(nullptr, IUGKP_ECUDA, std::string("noalloc solve: ") + cudaGetErrorString(e));
+  noalloc_stencil_kernel<<<blocks, 256, 0, s>>>(g, kappa_dev, wall_cv, diag, cx, cy, cz, it + 1);
   if ((e = cudaGetLastError()) != cudaSuccess) return fail(nullptr, IUGKP_ECUDA, std::string("noalloc solve: ") + cudaGetErrorString(e));
   noalloc_pcg_kernel<<<1, 1024, 0, s>>>(g, diag, cx, cy, cz, rhs_dev, x_dev, r, p, q, rtol, maxit, it);
   if ((e = cudaGetLastError()) != cudaSuccess) return fail(nullptr, IUGKP_ECUDA, std::string("noalloc solve: ") + cudaGetErrorString(e));
@@ -219,6 +238,8 @@ extern "C" iugkp_status iugkp_diffusion_solve_noalloc(const iugkp_grid* grid, co
       (e = cudaStreamSynchronize(s)) != cudaSuccess)
     return fail(nullptr, IUGKP_ECUDA, std::string("noalloc solve: ") + cudaGetErrorString(e));
   if (iters_out) *iters_out = (int)h_it;
+  if (h_it == -2.0) return fail(nullptr, IUGKP_EINVAL, "noalloc solve: kappa must be positive and finite in every cell");
+  if (h_it == -3.0) return fail(nullptr, IUGKP_EINVAL, "noalloc solve: a non-finite value arose (rhs not finite)");
   if (h_it < 0.0) return fail(nullptr, IUGKP_ENOCONV, "noalloc solve: maxit reached before rtol");
   return IUGKP_OK;
 }

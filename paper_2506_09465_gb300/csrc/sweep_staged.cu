@@ -140,16 +140,14 @@ __device__ __forceinline__ unsigned tie_bits(float D, float t, float d, float ba
   return 0u;
 }
 
-// faces_before and tie_bits together (one quotient): the count, with its tie bits or'd into tie.
-__device__ __forceinline__ int count_tie(float D, float t, float d, float base, unsigned& tie, int sh) {
+// faces_before, and in `near` whether D lies within the bound of a face of this axis (either
+// side; the direction is not needed when every candidate is real).
+__device__ __forceinline__ int count_near(float D, float t, float d, float base, bool& near) {
   const float u = __fdividef(D - t, d);
   const float c = __fadd_ru(fmaxf(u, 0.f), 8388608.f);  // 2^23 + ceil(max(u, 0))
   const float fr = (c - 8388608.f) - u;
-  const int n = __float_as_int(c) - 0x4B000000;
-  const float tol = fmaf(TIE_REL, d, base);
-  if (fr * d <= tol) tie |= 1u << sh;
-  else if ((1.f - fr) * d <= tol && n > 0) tie |= 2u << sh;
-  return n;
+  near |= fminf(fr, 1.f - fr) * d <= fmaf(TIE_REL, d, base);
+  return __float_as_int(c) - 0x4B000000;
 }
 
 // Axis a's bit of `hit` when the count one more than n reaches the wall (m faces to it).
@@ -199,16 +197,16 @@ enum { CAND_NULL = 0, CAND_REAL = 1, CAND_DEFER = 2 };
 // neighbourhood (by more than the ratio's rounding) is rejected wherever it lies, and needs no
 // face test; its W may sit in the neighbouring cell. ub: the acceptance word; sy, sz: cell
 // index steps along y and z.
-// all_real: every candidate of the band is real, and tie holds the counts' tie bits already
-// (count_tie); otherwise they are found here when needed.
+// all_real: every candidate of the band is real, and near tells whether a count lies within
+// the bound of a face (count_near); otherwise the tie bits are found here when needed.
 template <int DIM>
 __device__ __forceinline__ int candidate_outcome(const SweepArgs& A, long long bcbase, int ncells, const PW& f,
                                                  float base, int fb0, int fb1, int fb2, int cell, bool all_real,
-                                                 unsigned tie, uint32_t ub, int n0, int n1, int n2, int sy, int sz) {
-  if (all_real) return tie ? CAND_DEFER : CAND_REAL;
+                                                 bool near, uint32_t ub, int n0, int n1, int n2, int sy, int sz) {
+  if (all_real) return near ? CAND_DEFER : CAND_REAL;
   const float ua = word_uniform<float>(ub);
   if (ua - A.ratio_nb32[bcbase + cell] >= TIE_ACC) return CAND_NULL;
-  tie = tie_bits(f.D, f.t0, f.d0, base, fb0, 0);
+  unsigned tie = tie_bits(f.D, f.t0, f.d0, base, fb0, 0);
   if (DIM >= 2) tie |= tie_bits(f.D, f.t1, f.d1, base, fb1, 2);
   if (DIM == 3) tie |= tie_bits(f.D, f.t2, f.d2, base, fb2, 4);
   const float ra = A.ratio32[bcbase + cell];
@@ -625,12 +623,12 @@ __global__ void __launch_bounds__(STAGED_NT, 1) sweep_staged_kernel(SweepArgs A,
             ended = deferred = true;
             break;
           }
-          unsigned tie = 0;  // tie bits of the counts, found with them for all-real bands
+          bool near = false;  // a count within the bound of a face, found with it for all-real bands
           int fb0, fb1 = 0, fb2 = 0;
           if (all_real) {
-            fb0 = count_tie(f.D, f.t0, f.d0, base, tie, 0);
-            if (DIM >= 2) fb1 = count_tie(f.D, f.t1, f.d1, base, tie, 2);
-            if (DIM == 3) fb2 = count_tie(f.D, f.t2, f.d2, base, tie, 4);
+            fb0 = count_near(f.D, f.t0, f.d0, base, near);
+            if (DIM >= 2) fb1 = count_near(f.D, f.t1, f.d1, base, near);
+            if (DIM == 3) fb2 = count_near(f.D, f.t2, f.d2, base, near);
           } else {
             fb0 = faces_before(f.D, f.t0, f.d0);
             if (DIM >= 2) fb1 = faces_before(f.D, f.t1, f.d1);
@@ -640,8 +638,8 @@ __global__ void __launch_bounds__(STAGED_NT, 1) sweep_staged_kernel(SweepArgs A,
           if (DIM >= 2) cell += sy_cell * clampi(f.i1 + f.s1 * fb1, n1);
           if (DIM == 3) cell += sz_cell * clampi(f.i2 + f.s2 * fb2, n2);
           const long long ci = bcbase + cell;
-          const int oc = candidate_outcome<DIM>(A, bcbase, ncells, f, base, fb0, fb1, fb2, cell, all_real, tie, ub, n0,
-                                                n1, n2, sy_cell, sz_cell);
+          const int oc = candidate_outcome<DIM>(A, bcbase, ncells, f, base, fb0, fb1, fb2, cell, all_real, near, ub,
+                                                n0, n1, n2, sy_cell, sz_cell);
           if (oc == CAND_DEFER) {
             ended = deferred = true;
             break;
@@ -691,19 +689,19 @@ __global__ void __launch_bounds__(STAGED_NT, 1) sweep_staged_kernel(SweepArgs A,
           }
           // at a wall, the faces of the other axes crossed before it: a count within rounding
           // of the FP64 walk's (the segment leaves near a cell corner) defers the particle
-          unsigned tie = 0;
+          bool tie = false;
           const float bx = TIE_REL * f.tex;
           const int m0 = faces_to_wall(f.i0, f.s0, n0);
           int c0 = m0 - 1, c1 = 0, c2 = 0, m1 = 1;
           if (ex != 0) {
-            const int q = count_tie(L, f.t0, f.d0, bx, tie, 0);
+            const int q = count_near(L, f.t0, f.d0, bx, tie);
             c0 = min(q, m0 - 1);
           }
           if (DIM >= 2) {
             m1 = faces_to_wall(f.i1, f.s1, n1);
             c1 = m1 - 1;
             if (ex != 1) {
-              const int q = count_tie(L, f.t1, f.d1, bx, tie, 2);
+              const int q = count_near(L, f.t1, f.d1, bx, tie);
               c1 = min(q, m1 - 1);
             }
           }
@@ -711,7 +709,7 @@ __global__ void __launch_bounds__(STAGED_NT, 1) sweep_staged_kernel(SweepArgs A,
             const int m2 = faces_to_wall(f.i2, f.s2, n2);
             c2 = m2 - 1;
             if (ex != 2) {
-              const int q = count_tie(L, f.t2, f.d2, bx, tie, 4);
+              const int q = count_near(L, f.t2, f.d2, bx, tie);
               c2 = min(q, m2 - 1);
             }
           }
@@ -1032,18 +1030,18 @@ __global__ void __launch_bounds__(STAGED_NT, 1) sweep_sync_kernel(SweepArgs A, S
               deferred = true;
               break;
             }
-            unsigned tie = 0;  // tie bits of the counts, found with them for all-real bands
+            bool near = false;  // a count within the bound of a face, found with it for all-real bands
             if (all_real) {
-              fb0 = count_tie(f.D, f.t0, f.d0, base, tie, 0);
-              fb1 = count_tie(f.D, f.t1, f.d1, base, tie, 2);
+              fb0 = count_near(f.D, f.t0, f.d0, base, near);
+              fb1 = count_near(f.D, f.t1, f.d1, base, near);
             } else {
               fb0 = faces_before(f.D, f.t0, f.d0);
               fb1 = faces_before(f.D, f.t1, f.d1);
             }
             const int cell = clampi(f.i0 + f.s0 * fb0, n0) + n0 * clampi(f.i1 + f.s1 * fb1, n1);
             const long long ci = bcbase + cell;
-            const int oc = candidate_outcome<2>(A, bcbase, in.ncells, f, base, fb0, fb1, 0, cell, all_real, tie, ub, n0,
-                                                n1, 1, n0, 0);
+            const int oc = candidate_outcome<2>(A, bcbase, in.ncells, f, base, fb0, fb1, 0, cell, all_real, near, ub,
+                                                n0, n1, 1, n0, 0);
             if (oc == CAND_DEFER) {
               deferred = true;
               break;
@@ -1075,9 +1073,7 @@ __global__ void __launch_bounds__(STAGED_NT, 1) sweep_sync_kernel(SweepArgs A, S
             // the FP64 walk's: deferred too
             const float bx = TIE_REL * f.tex;
             ex = f.i2;
-            unsigned tie = 0;
-            const int q = count_tie(f.tex, ex == 0 ? f.t1 : f.t0, ex == 0 ? f.d1 : f.d0, bx, tie, 0);
-            deferred = tie != 0;
+            const int q = count_near(f.tex, ex == 0 ? f.t1 : f.t0, ex == 0 ? f.d1 : f.d0, bx, deferred);
             c0 = ex == 0 ? m0 - 1 : min(q, m0 - 1);
             c1 = ex == 1 ? m1 - 1 : min(q, m1 - 1);
           } else {
@@ -1273,17 +1269,17 @@ __global__ void __launch_bounds__(STAGED_NT, 1) adjoint_sync_kernel(SweepArgs A,
               deferred = true;
               break;
             }
-            unsigned tie = 0;  // tie bits of the counts, found with them for all-real bands
+            bool near = false;  // a count within the bound of a face, found with it for all-real bands
             if (all_real) {
-              fb0 = count_tie(f.D, f.t0, f.d0, base, tie, 0);
-              fb1 = count_tie(f.D, f.t1, f.d1, base, tie, 2);
+              fb0 = count_near(f.D, f.t0, f.d0, base, near);
+              fb1 = count_near(f.D, f.t1, f.d1, base, near);
             } else {
               fb0 = faces_before(f.D, f.t0, f.d0);
               fb1 = faces_before(f.D, f.t1, f.d1);
             }
             const int cell = clampi(f.i0 + f.s0 * fb0, n0) + n0 * clampi(f.i1 + f.s1 * fb1, n1);
-            const int oc = candidate_outcome<2>(A, bcbase, in.ncells, f, base, fb0, fb1, 0, cell, all_real, tie, ub, n0,
-                                                n1, 1, n0, 0);
+            const int oc = candidate_outcome<2>(A, bcbase, in.ncells, f, base, fb0, fb1, 0, cell, all_real, near, ub,
+                                                n0, n1, 1, n0, 0);
             if (oc == CAND_DEFER) {
               deferred = true;
               break;

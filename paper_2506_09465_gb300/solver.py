@@ -209,6 +209,11 @@ class Solver:
     def set_wall_T(self, Tw, stream=None):
         self._set(L.FIELD_WALL_T, Tw, stream)
 
+    def set_tau(self, tau, stream=None):
+        """Relaxation times [instance][band][cell] (rebuilds every tau-dependent part)."""
+        self._set(L.FIELD_TAU, tau, stream)
+        L.check(self.lib.iugkp_get_layout(self.ctx, ctypes.byref(self.layout), None, None), self.ctx)
+
     def set_wall_face_T(self, Tf, stream=None):
         """Temperature of every boundary face ([total_wall_faces], instance-major)."""
         self._set(L.FIELD_WALL_FACE_T, Tf, stream)
