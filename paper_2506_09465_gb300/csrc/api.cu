@@ -130,7 +130,7 @@ void free_all(Ctx* c) {
                   c->d_theta, c->d_theta_m, c->d_diag, c->d_cx, c->d_cy, c->d_cz, c->d_pcg, c->d_work, c->d_T2,
                   c->d_R, c->d_W, c->d_F, c->d_wall, c->d_red, c->d_counters, c->d_work_counter, c->d_err,
                   c->d_pcg_iters, c->d_scalar, c->d_adj, c->d_mg, c->d_mg_diag, c->d_mg_dinv, c->d_mg_cx,
-                  c->d_mg_cy, c->d_mg_cz, c->d_mg_cinv, c->d_mg_b, c->d_mg_x, c->d_mg_t, c->d_mg_r,
+                  c->d_mg_cy, c->d_mg_cz, c->d_mg_cinv, c->d_mg_b, c->d_mg_x, c->d_mg_t, c->d_mg_r, c->d_fd_q, c->d_fd_lam,
                   c->d_inst_beg, c->d_inst_end, c->d_inst_next, c->d_cost_prefix, c->d_window, c->d_wmax,
                   c->d_group_mag, c->d_mag, c->d_wall_unit, c->d_all_beg, c->d_all_end, c->d_all_cost_prefix,
                   c->d_all_group_mag, c->d_R32, c->d_W32, c->d_F32, c->d_m2, c->d_wallTf,
@@ -710,7 +710,7 @@ iugkp_status iugkp_create_batch(int n, const iugkp_grid* g, const double* const*
     return bail(IUGKP_ECUDA);
   }
   if ((s = dalloc(c, &c->d_pcg, 5 * (size_t)cell_off)) != IUGKP_OK) return bail(s);
-  if ((s = build_multigrid(c, diag, cx, cy, cz)) != IUGKP_OK) return bail(s);
+  if ((s = build_multigrid(c, diag, cx, cy, cz, kap, cvsum)) != IUGKP_OK) return bail(s);
   if ((s = dalloc(c, &c->d_work, cell_off)) != IUGKP_OK) return bail(s);
   if ((s = dalloc(c, &c->d_T2, cell_off)) != IUGKP_OK) return bail(s);
   if ((s = dalloc(c, &c->d_R, (size_t)nb * cell_off)) != IUGKP_OK) return bail(s);

@@ -158,6 +158,8 @@ struct Ctx {
   float* d_mg_x = nullptr;
   float* d_mg_t = nullptr;
   float* d_mg_r = nullptr;
+  float* d_fd_q = nullptr;       // fast diagonalization: eigenvector matrices (FP32)
+  double* d_fd_lam = nullptr;    // ... and eigenvalues
   long long mg_level_cells = 0;
   // staged sweep
   long long* d_inst_beg = nullptr;   // [n_inst] forward particle range per instance
@@ -218,7 +220,8 @@ cudaError_t launch_mgpcg(const Ctx* c, const double* rhs, cudaStream_t s);
 size_t mg_solo_smem_bytes(const std::vector<InstMG>& h_mg);
 cudaError_t configure_mgpcg(Ctx* c, size_t smem);
 iugkp_status build_multigrid(Ctx* c, const std::vector<double>& diag, const std::vector<double>& cx,
-                             const std::vector<double>& cy, const std::vector<double>& cz);
+                             const std::vector<double>& cy, const std::vector<double>& cz,
+                             const std::vector<double>& kap, double cvsum);
 cudaError_t launch_grad_source(const Ctx* c, const double* at, double* grad, cudaStream_t s);
 cudaError_t launch_persistent_init(Ctx* c, cudaStream_t s);
 cudaError_t launch_persistent_step(const Ctx* c, const double* T, unsigned it, double* R, double* W, double* wall,

@@ -20,6 +20,8 @@ namespace cg = cooperative_groups;
 
 namespace iugkp {
 
+constexpr int MG32_PASSES_FD = 6;  // refinement passes of the fast diagonalization solve at most
+
 struct MGArgs {
   const InstMG* mg;         // [n_inst]
   const double* diag;       // fine FP64 operator
@@ -32,6 +34,8 @@ struct MGArgs {
   const float* lcy;
   const float* lcz;
   const float* cinv;        // coarsest dense inverses
+  const float* fq;          // fast diagonalization: eigenvector matrices
+  const double* flam;       // ... and eigenvalues
   float* lb;                // level right-hand sides
   float* lx;                // level iterates
   float* lt;                // level scratch (ping-pong)
@@ -344,6 +348,140 @@ __device__ void vcycle(const MGArgs& A, const InstMG& m, cg::cluster_group& cl, 
   }
 }
 
+// ---- Fast diagonalization (Lynch, Rice and Thomas 1964) for separable operators ----
+// With A = Tx (x) I + I (x) Ty, Tx = Qx Lx Qx^T and Ty = Qy Ly Qy^T, and the right-hand side
+// as an ny x nx matrix S (row j = the cells of y-row j), A X = S is solved by
+//   X = Qy [(Qy^T S Qx) ./ (ly_j + lx_i)] Qx^T,
+// four dense products of FP32 matrices (nx, ny <= FD_MAX_N). The rows j are split over the
+// cluster's CTAs; each product reads what the other CTAs wrote through L2 after a cluster
+// barrier. The solve runs inside FP64 iterative refinement: the solution is accumulated in
+// FP64 and its residual S - A X is formed with the FP64 operator, until it meets rtol.
+
+// Tiles of the dense products: FD_TR rows x FD_TI columns of the output per step, FD_TK terms
+// of the sum staged in shared memory at a time (512 threads: each one column, four rows).
+constexpr int FD_TI = 128, FD_TK = 32, FD_TR = 16;
+
+// out(j, i) for rows j in [j0, j1) and columns i < N of sum_k L(j, k) R(k, i), with L and R
+// tiles staged in shared memory (R tile loads coalesce along i).
+template <int NT, class FL, class FR, class FE>
+__device__ __forceinline__ void rows_product(int j0, int j1, int N, int K, FL L, FR R, FE out,
+                                             float (*sl)[FD_TK + 1], float (*sr)[FD_TI]) {
+  static_assert(NT == 512, "four rows per thread: 512 threads = 4 groups of FD_TI columns");
+  const int tc = threadIdx.x % FD_TI, tg = threadIdx.x / FD_TI;
+  for (int jt = j0; jt < j1; jt += FD_TR) {
+    for (int it = 0; it < N; it += FD_TI) {
+      float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
+      for (int kt = 0; kt < K; kt += FD_TK) {
+        {
+          const int r = threadIdx.x / FD_TK, k = threadIdx.x % FD_TK;
+          sl[r][k] = (jt + r < j1 && kt + k < K) ? L(jt + r, kt + k) : 0.f;
+        }
+        for (int q = threadIdx.x; q < FD_TK * FD_TI; q += NT) {
+          const int k = q / FD_TI, i = q - k * FD_TI;
+          sr[k][i] = (kt + k < K && it + i < N) ? R(kt + k, it + i) : 0.f;
+        }
+        __syncthreads();
+#pragma unroll 8
+        for (int k = 0; k < FD_TK; ++k) {
+          const float r = sr[k][tc];
+          a0 = fmaf(sl[tg][k], r, a0);
+          a1 = fmaf(sl[tg + 4][k], r, a1);
+          a2 = fmaf(sl[tg + 8][k], r, a2);
+          a3 = fmaf(sl[tg + 12][k], r, a3);
+        }
+        __syncthreads();
+      }
+      const int i = it + tc;
+      if (i < N) {
+        if (jt + tg < j1) out(jt + tg, i, a0);
+        if (jt + tg + 4 < j1) out(jt + tg + 4, i, a1);
+        if (jt + tg + 8 < j1) out(jt + tg + 8, i, a2);
+        if (jt + tg + 12 < j1) out(jt + tg + 12, i, a3);
+      }
+    }
+  }
+}
+
+// Solves the instance's correction by fast diagonalization with FP64 refinement (at most
+// MG32_PASSES_FD passes); returns the passes taken, or -1 if rtol was not met.
+template <int NT, int CS>
+__device__ int fd_solve(const MGArgs& A, const InstMG& m, cg::cluster_group& cl, int rank, ClusterRed<NT, CS>& red,
+                        double* sh) {
+  const int nx = m.fnx, ny = m.fny;
+  const long long off = m.cell_off, n = m.nc[0];
+  const long long sy = m.n[0][0];
+  const int rows = (ny + CS - 1) / CS, j0 = min(ny, rank * rows), j1 = min(ny, j0 + rows);
+  const long long lo = (long long)j0 * nx, hi = (long long)j1 * nx;  // this CTA's cells
+  const float* Qx = A.fq + m.qx_off;
+  const float* Qy = A.fq + m.qy_off;
+  const double* lx = A.flam + m.lx_off;
+  const double* ly = A.flam + m.ly_off;
+  float* Sf = A.lt + m.off[0];  // scaled residual (FP32)
+  float* T1 = A.lb + m.off[0];  // Qy^T S, then Qy T2
+  float* T2 = A.lx + m.off[0];  // (Qy^T S Qx) ./ (ly + lx)
+  __shared__ float sl[FD_TR][FD_TK + 1];
+  __shared__ float sr[FD_TK][FD_TI];
+  double v[4];
+  v[0] = 0.0;
+  for (long long c = lo + threadIdx.x; c < hi; c += NT) {
+    const double b = A.rhs[off + c];
+    A.X[off + c] = 0.0;
+    A.Z[off + c] = b;  // FP64 residual
+    v[0] += b * b;
+  }
+  red.sum(cl, v, 1, sh);
+  const double bb = v[0];
+  if (bb == 0.0) return 0;
+  const double tol2 = A.rtol * A.rtol * bb;
+  double rr = bb;
+  for (int pass = 1; pass <= MG32_PASSES_FD && pass <= A.maxit; ++pass) {
+    const double rn = sqrt(rr), sc = 1.0 / rn;
+    for (long long c = lo + threadIdx.x; c < hi; c += NT) Sf[c] = (float)(__ldcg(&A.Z[off + c]) * sc);
+    cl.sync();
+    // T1 = Qy^T S (rows j of this CTA), then T2 = T1 Qx ./ (ly_j + lx_i) (same rows)
+    rows_product<NT>(
+        j0, j1, nx, ny, [&](int j, int k) { return __ldg(&Qy[(long long)k * ny + j]); },
+        [&](int k, int i) { return __ldcg(&Sf[(long long)k * nx + i]); },
+        [&](int j, int i, float x) { T1[(long long)j * nx + i] = x; }, sl, sr);
+    __syncthreads();
+    rows_product<NT>(
+        j0, j1, nx, nx, [&](int j, int k) { return __ldcg(&T1[(long long)j * nx + k]); },
+        [&](int k, int i) { return __ldg(&Qx[(long long)k * nx + i]); },
+        [&](int j, int i, float x) { T2[(long long)j * nx + i] = (float)((double)x / (ly[j] + lx[i])); }, sl, sr);
+    cl.sync();
+    // T1 = Qy T2, then the correction T1 Qx^T added to the FP64 solution (scaled back)
+    rows_product<NT>(
+        j0, j1, nx, ny, [&](int j, int k) { return __ldg(&Qy[(long long)j * ny + k]); },
+        [&](int k, int i) { return __ldcg(&T2[(long long)k * nx + i]); },
+        [&](int j, int i, float x) { T1[(long long)j * nx + i] = x; }, sl, sr);
+    __syncthreads();
+    rows_product<NT>(
+        j0, j1, nx, nx, [&](int j, int k) { return __ldcg(&T1[(long long)j * nx + k]); },
+        [&](int k, int i) { return __ldg(&Qx[(long long)i * nx + k]); },
+        [&](int j, int i, float x) { A.X[off + (long long)j * nx + i] += (double)x * rn; }, sl, sr);
+    cl.sync();
+    // FP64 residual of the FP64 solution
+    v[0] = 0.0;
+    for (long long c = lo + threadIdx.x; c < hi; c += NT) {
+      const long long g = off + c;
+      double q = A.diag[g] * __ldcg(&A.X[g]);
+      if (c + 1 < n) q -= A.cx[g] * __ldcg(&A.X[g + 1]);
+      if (c >= 1) q -= A.cx[g - 1] * __ldcg(&A.X[g - 1]);
+      if (m.dim >= 2) {
+        if (c + sy < n) q -= A.cy[g] * __ldcg(&A.X[g + sy]);
+        if (c >= sy) q -= A.cy[g - sy] * __ldcg(&A.X[g - sy]);
+      }
+      const double r = A.rhs[g] - q;
+      A.Z[g] = r;
+      v[0] += r * r;
+    }
+    red.sum(cl, v, 1, sh);  // also orders the residual's writes before the next pass
+    rr = v[0];
+    if (rr <= tol2) return pass;
+  }
+  return -1;
+}
+
 template <int NT, int CS>
 __global__ void __launch_bounds__(NT) mgpcg_kernel(MGArgs A) {
   __shared__ double sh[4 * 32];
@@ -357,6 +495,11 @@ __global__ void __launch_bounds__(NT) mgpcg_kernel(MGArgs A) {
   const long long chunk = (n + CS - 1) / CS, lo = rank * chunk, hi = min(n, lo + chunk);
   const long long sy = m.n[0][0], sz = (long long)m.n[0][0] * m.n[0][1];
   ClusterRed<NT, CS> red{slot, 0};
+  if (m.direct) {
+    const int passes = fd_solve<NT, CS>(A, m, cl, rank, red, sh);
+    if (rank == 0 && threadIdx.x == 0) A.iters_out[k] = passes;
+    return;
+  }
   double v[4];
   // x = 0, r = b
   v[0] = 0.0;
@@ -520,6 +663,11 @@ __global__ void __launch_bounds__(NT, 1) mgpcg32_kernel(MGArgs A, float* V32) {
   float* Q = P + n;
   const float *dg = A.ldiag + m.off[0], *cx = A.lcx + m.off[0], *cy = A.lcy + m.off[0], *cz = A.lcz + m.off[0];
   ClusterRed<NT, CS> red{slot, 0};
+  if (m.direct) {
+    const int passes = fd_solve<NT, CS>(A, m, cl, rank, red, sh);
+    if (rank == 0 && threadIdx.x == 0) A.iters_out[k] = passes;
+    return;
+  }
   double v[4];
   // x = 0, FP64 residual r = b
   v[0] = 0.0;
@@ -652,6 +800,8 @@ cudaError_t launch_mgpcg(const Ctx* c, const double* rhs, cudaStream_t s) {
   a.lcy = c->d_mg_cy;
   a.lcz = c->d_mg_cz;
   a.cinv = c->d_mg_cinv;
+  a.fq = c->d_fd_q;
+  a.flam = c->d_fd_lam;
   a.lb = c->d_mg_b;
   a.lx = c->d_mg_x;
   a.lt = c->d_mg_t;

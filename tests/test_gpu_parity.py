@@ -109,16 +109,21 @@ def test_newton_step_matches_direct_solve(orc, dim):
     assert ok, err
 
 
-@pytest.mark.parametrize("rtol", [1e-3, 1e-5, 9.9e-6])
-@pytest.mark.parametrize("dim,n", [(1, (30,)), (2, (14, 11)), (2, (160, 128)), (3, (6, 5, 4))])
-def test_correction_solve_meets_its_fp64_residual(orc, dim, n, rtol):
-    # From cg_rtol 1e-5 up (the default 1e-3 among them) the correction solve runs FP32 PCG
-    # iterates inside FP64 iterative refinement; below, FP64 iterates. Either way the returned
-    # correction x meets ||s - A x|| <= cg_rtol ||s|| with A the oracle's FP64 operator and s
-    # its right-hand side (s = A dT of the oracle's direct banded solve), and the solver reports its
-    # iterations.
+@pytest.mark.parametrize("rtol", [1e-3, 1e-5, 9.9e-6, 1e-11])
+@pytest.mark.parametrize("dim,n,uniform", [(1, (30,), False), (2, (14, 11), False), (2, (160, 128), False),
+                                           (3, (6, 5, 4), False), (1, (70,), True), (2, (48, 40), True),
+                                           (2, (200, 7), True)])
+def test_correction_solve_meets_its_fp64_residual(orc, dim, n, uniform, rtol):
+    # Separable operators (1D or 2D with uniform kappa) are solved by fast diagonalization;
+    # the others by multigrid-preconditioned CG, with FP32 iterates from cg_rtol 1e-5 up (the
+    # default 1e-3 among them) and FP64 iterates below. All of them refine in FP64: the
+    # returned correction x meets ||s - A x|| <= cg_rtol ||s|| with A the oracle's FP64
+    # operator and s its right-hand side (s = A dT of the oracle's direct banded solve), and
+    # the solver reports its iterations (refinement passes for the direct solve).
     rng = np.random.default_rng(60 + dim)
     inst = WL.random_instance(rng, dim, n, 2, (0.01, 0.4))
+    if uniform:  # the same tau in every cell of a band: uniform kappa
+        inst.tau = np.repeat(rng.uniform(0.02, 0.4, size=(2, 1)), inst.ncells, axis=1)
     C, v = [1.0, 0.5], [1.0, 1.5]
     N = 40 if inst.ncells < 1000 else 4
     p = oracle_problem(inst, C, v, N, N)
@@ -135,6 +140,8 @@ def test_correction_solve_meets_its_fp64_residual(orc, dim, n, rtol):
     rhs = orc.diffusion_apply(p, dT / theta)  # the oracle returns the damped correction theta dT
     res = np.linalg.norm(rhs - orc.diffusion_apply(p, x)) / np.linalg.norm(rhs)
     assert res <= rtol * 1.001, res
+    if uniform:
+        assert it <= 6, it  # direct solve: a few refinement passes
 
 
 @pytest.mark.parametrize("newton", [0, 1])
