@@ -289,6 +289,13 @@ iugkp_status iugkp_residual(iugkp_ctx *ctx, const double *T0_dev, const double *
 iugkp_status iugkp_replayed(iugkp_ctx *ctx, long long *n_out, void *cuda_stream);
 iugkp_status iugkp_check_fp32_walk(double *out6);
 
+/* Measurement aid (no counterpart in the paper): the rate of FP64 atomic additions to
+ * scattered addresses of an 8 MB (L2-resident) array on the current device, the access
+ * pattern of the deposit tallies, in additions per second (best of a warm-up and five
+ * timed launches). Allocates and frees its own buffer; synchronous; errors in
+ * iugkp_last_error(NULL). */
+iugkp_status iugkp_measure_atomics(double *ops_per_s);
+
 /* Steady driver: from the initial T_inout_dev, repeats sweep -> macro -> [Newton]
  * until res = ||T^{n+1} - T^n|| / max(||T^{n+1}||, dT_ref sqrt(ncells)) <= tol over
  * all instances (dT_ref = the wall-temperature span, or max |T_w|, or 1).

@@ -74,6 +74,7 @@ SIGNATURES = {
     "iugkp_adjoint": (_i, [_vp, _vp, _vp, _d, _i, _vp, _vp, _vp, _vp]),
     "iugkp_replayed": (_i, [_vp, ctypes.POINTER(_ll), _vp]),
     "iugkp_check_fp32_walk": (_i, [ctypes.POINTER(_d)]),
+    "iugkp_measure_atomics": (_i, [ctypes.POINTER(_d)]),
     "iugkp_diffusion_solve_noalloc": (_i, [ctypes.POINTER(Grid), _vp, _d, _vp, _vp, _d, _i, ctypes.POINTER(_i), _vp]),
 }
 

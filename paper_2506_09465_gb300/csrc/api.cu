@@ -1141,6 +1141,16 @@ iugkp_status iugkp_replayed(iugkp_ctx* ctx, long long* n_out, void* cuda_stream)
   return IUGKP_OK;
 }
 
+iugkp_status iugkp_measure_atomics(double* ops_per_s) {
+  Ctx* c = nullptr;
+  if (!ops_per_s) return fail(c, IUGKP_EINVAL, "NULL output");
+  int dev = 0, sms = 0;
+  CK(cudaGetDevice(&dev), "device");
+  CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev), "SM count");
+  CK(measure_atomic_rate(sms, ops_per_s), "atomic rate");
+  return IUGKP_OK;
+}
+
 iugkp_status iugkp_check_fp32_walk(double* out6) {
   Ctx* c = nullptr;
   if (!out6) return fail(c, IUGKP_EINVAL, "NULL output");

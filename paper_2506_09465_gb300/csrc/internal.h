@@ -216,6 +216,7 @@ cudaError_t launch_replay(const Ctx* c, const SweepArgs& a, const StagedArgs& S,
 cudaError_t launch_adjoint_replay(const Ctx* c, const SweepArgs& a, cudaStream_t s);
 cudaError_t launch_walk_bounds(unsigned long long* out, cudaStream_t s);
 double walk_bound_fraction(const double* measured);
+cudaError_t measure_atomic_rate(int sm_count, double* out_rate);
 cudaError_t launch_mgpcg(const Ctx* c, const double* rhs, cudaStream_t s);
 size_t mg_solo_smem_bytes(const std::vector<InstMG>& h_mg);
 cudaError_t configure_mgpcg(Ctx* c, size_t smem);

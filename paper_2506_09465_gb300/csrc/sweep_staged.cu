@@ -1837,6 +1837,41 @@ cudaError_t launch_walk_bounds(unsigned long long* out, cudaStream_t s) {
   return cudaGetLastError();
 }
 
+// FP64 atomic additions to scattered addresses of an L2-resident array (the deposit tallies'
+// access pattern): every thread adds to `per_thread` addresses spread by a multiplicative hash.
+__global__ void atomic_rate_kernel(double* buf, unsigned mask, int per_thread) {
+  const unsigned t = blockIdx.x * blockDim.x + threadIdx.x;
+  for (int k = 0; k < per_thread; ++k) {
+    const unsigned a = ((t * 32u + (unsigned)k) * 2654435761u) & mask;
+    atomicAdd(&buf[a], 1.0);
+  }
+}
+
+cudaError_t measure_atomic_rate(int sm_count, double* out_rate) {
+  const unsigned n = 1u << 20;  // 8 MB: L2-resident
+  double* buf = nullptr;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cudaError_t e = cudaMalloc((void**)&buf, n * sizeof(double));
+  if (e == cudaSuccess) e = cudaMemset(buf, 0, n * sizeof(double));
+  if (e == cudaSuccess) e = cudaEventCreate(&e0);
+  if (e == cudaSuccess) e = cudaEventCreate(&e1);
+  const int blocks = sm_count * 8, threads = 256, per = 256;
+  float ms = 0.f;
+  if (e == cudaSuccess) {
+    atomic_rate_kernel<<<blocks, threads>>>(buf, n - 1, per);  // warm-up
+    cudaEventRecord(e0);
+    for (int r = 0; r < 5; ++r) atomic_rate_kernel<<<blocks, threads>>>(buf, n - 1, per);
+    cudaEventRecord(e1);
+    e = cudaEventSynchronize(e1);
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+  }
+  if (e == cudaSuccess) *out_rate = 5.0 * blocks * threads * (double)per / (ms * 1e-3);
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  if (buf) cudaFree(buf);
+  return e;
+}
+
 // The relative bound the face-count decision needs, from the measured errors above (units of
 // 2^-23): direction s = product of a square root and a sine/cosine (one more rounding), cell
 // size h in FP32 (half an ulp), d = h / |s| (__fdividef), t = (1 - xi) d (one rounding), the
