@@ -309,12 +309,14 @@ def other_config_sweeps(WL, make_solver, reps=3):
     """Sweep throughput of the two other sweep workloads on the fast path: the 2D non-gray
     square (256^2, 40 bands x 2 branches, Gaussian source, 1024 particles per cell) and the
     batch of 16 two-material 3D boxes (16^3 .. 64^3, 256 particles per cell), T = 0.3 in every
-    cell plus the sources; best of reps after one warm-up, CUDA events around the sweep call."""
+    cell plus the sources; the staged sweep's parameters autotuned on that field first (untimed,
+    like the main workload's); best of reps after one warm-up, CUDA events around the sweep call."""
     import torch
     out = {}
     for name, wl in (("nongray_256x256_80bands", WL.nongray_square(256, 40, 1024)), ("box_batch_16", WL.box_batch(16))):
         s = make_solver(wl, seed=0)
         T = torch.full((s.total_cells,), 0.3, dtype=torch.float64, device="cuda")  # every emitter active
+        tuning = s.autotune(T, 0, allow_k32=False)
         R = torch.empty(s.nb * s.total_cells, dtype=torch.float64, device="cuda")
         W = torch.empty_like(R)
         F = torch.empty(s.total_faces, dtype=torch.float64, device="cuda")
@@ -332,7 +334,8 @@ def other_config_sweeps(WL, make_solver, reps=3):
         c = cnt.cpu().numpy()
         out[name] = {"cells": s.total_cells, "band_branches": s.nb, "flights": int(c[0]), "crossings": int(c[3]),
                      "candidates": int(c[1]), "sweep_ms": best, "crossings_per_s": c[3] / (best * 1e-3),
-                     "flights_per_s": c[0] / (best * 1e-3)}
+                     "flights_per_s": c[0] / (best * 1e-3),
+                     "autotuned": {k: tuning[k] for k in ("refill_lanes", "warp_grab", "walk_k")}}
         del s
     return out
 

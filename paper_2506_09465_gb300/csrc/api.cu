@@ -278,7 +278,8 @@ iugkp_status rebuild_forward_groups(Ctx* c) {
       continue;
     }
     c->all_two_group = false;
-    const long long len = std::min<long long>(X, c->staged_cap);
+    // 3D: no face window (the dynamic shared memory holds the warps' item tables)
+    const long long len = c->dim == 3 ? 0 : std::min<long long>(X, c->staged_cap);
     window[k] = make_int2((int)((X - len) / 2), (int)len);
     if (len < X) c->sync_partial = true;
   }
@@ -678,7 +679,8 @@ iugkp_status iugkp_create_batch(int n, const iugkp_grid* g, const double* const*
     // static shared memory of the staged kernel (the cooperative tallies' parameter table and
     // list starts, 36.2 KB, and a few words) stays below 37 KB
     const long long budget = ((long long)c->smem_optin - 37 * 1024) / (long long)sizeof(unsigned);
-    c->staged_cap = (int)std::max<long long>(1, std::min(maxX, budget));
+    c->staged_cap = c->dim == 3 ? COOP3_BYTES / (int)sizeof(unsigned)
+                                : (int)std::max<long long>(1, std::min(maxX, budget));
   }
   if ((s = rebuild_forward_groups(c)) != IUGKP_OK) return bail(s);
   {

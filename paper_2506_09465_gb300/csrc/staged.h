@@ -5,6 +5,14 @@ namespace iugkp {
 
 constexpr int STAGED_NT = 1024;                 // threads per persistent block
 
+// 3D face tallies: the warp tallies the items of the particles that ended together; per warp a
+// table of 64 item lists (the x- and y-faces of each lane's particle, 3 int4 of parameters
+// each) and their 65 start offsets, in the dynamic shared memory (3D instances keep no face
+// window there).
+constexpr int COOP3_LISTS = 64;
+constexpr int COOP3_INT4_PER_WARP = COOP3_LISTS * 3 + 17;  // parameters, then the starts (65 ints)
+constexpr int COOP3_BYTES = (STAGED_NT / 32) * COOP3_INT4_PER_WARP * 16;
+
 // Shared-memory x-face window: one 32-bit word per face holding the low word of a 64-bit
 // fixed-point sum in units of w_max 2^-26 (a contribution is below 2^26 units); words start
 // at 2^31, and a wrap of the word adds +-2^32 units (= 64 w_max) to the FP64 face at once.

@@ -608,6 +608,7 @@ __global__ void __launch_bounds__(STAGED_NT, 1) sweep_staged_kernel(SweepArgs A,
       // W tally, then acceptance with probability tau_maj / tau(x); a rejected candidate
       // draws the next flight length and the particle goes on in the same direction ----
       int nitem = 0;  // cooperative tallies: face items of the lane's particle ended in this pass
+      int nx3 = 0, ny3 = 0;  // 3D: x- and y-face items of the lane's particle ended in this pass
       if (alive && !tally) {
         bool ended = false, wall_exit = false, deferred = false;
         const bool all_real = A.all_real[(long long)k * A.nb + band] != 0;
@@ -774,6 +775,41 @@ __global__ void __launch_bounds__(STAGED_NT, 1) sweep_staged_kernel(SweepArgs A,
                 if (K32) tally_k32(&S.F32[fi], -w);
                 else atomicAdd(&A.F[fi], -w);
               }
+              if (DIM == 3) {
+                // Two item lists, tallied below by the whole warp: the x-faces crossed (the wall
+                // face too when the particle leaves through x) and the y-faces. Item k of the list
+                // along axis p is the face a0 + k sp + sq1 min(ceil(u1 + k r1), lim1) + sq2
+                // min(ceil(u2 + k r2), lim2): the k-th face normal to p, in the cell row and
+                // layer given by the faces of the other two axes crossed before it (ceil((t_p +
+                // k d_p - t_q) / d_q) = ceil(u + k r), u = (t_p - t_q) / d_q, r = d_p / d_q).
+                int4* tab = reinterpret_cast<int4*>(win) + (threadIdx.x >> 5) * COOP3_INT4_PER_WARP + 6 * lane;
+                auto ur = [](float tp, float dp, float tq, float dq, float& u, float& r) {
+                  const bool flat = !(dq < INFINITY);
+                  u = flat ? -1.f : __fdividef(tp - tq, dq);
+                  r = flat ? 0.f : __fdividef(dp, dq);
+                };
+                float u1, r1, u2, r2;
+                nx3 = c0 + (ex == 0 ? 1 : 0);
+                ny3 = c1 + (ex == 1 ? 1 : 0);
+                ur(f.t0, f.d0, f.t1, f.d1, u1, r1);
+                ur(f.t0, f.d0, f.t2, f.d2, u2, r2);
+                double ws = f.s0 > 0 ? w : -w;
+                tab[0] = make_int4((f.s0 > 0 ? f.i0 + 1 : f.i0) + sy_xf * f.i1 + sz_xf * f.i2, f.s0, f.s1 * sy_xf,
+                                   faces_to_wall(f.i1, f.s1, n1) - 1);
+                tab[1] = make_int4(f.s2 * sz_xf, faces_to_wall(f.i2, f.s2, n2) - 1, __float_as_int(u1),
+                                   __float_as_int(r1));
+                tab[2] = make_int4(__float_as_int(u2), __float_as_int(r2), __double2loint(ws), __double2hiint(ws));
+                ur(f.t1, f.d1, f.t0, f.d0, u1, r1);
+                ur(f.t1, f.d1, f.t2, f.d2, u2, r2);
+                ws = f.s1 > 0 ? w : -w;
+                const int sz_yf = n0 * (n1 + 1);  // y-face index step along z
+                tab[3] = make_int4((int)fax1 + f.i0 + n0 * (f.s1 > 0 ? f.i1 + 1 : f.i1) + sz_yf * f.i2, f.s1 * n0, f.s0,
+                                   m0 - 1);
+                tab[4] = make_int4(f.s2 * sz_yf, faces_to_wall(f.i2, f.s2, n2) - 1, __float_as_int(u1),
+                                   __float_as_int(r1));
+                tab[5] = make_int4(__float_as_int(u2), __float_as_int(r2), __double2loint(ws), __double2hiint(ws));
+                alive = false;
+              } else {
               // x-faces crossed (the wall face too when the particle leaves through x),
               // then in 3D the y-faces
               kcur = 0;
@@ -791,6 +827,7 @@ __global__ void __launch_bounds__(STAGED_NT, 1) sweep_staged_kernel(SweepArgs A,
               }
               tally = kend > 0;
               alive = tally;
+              }
             } else {
               alive = false;
             }
@@ -853,6 +890,57 @@ __global__ void __launch_bounds__(STAGED_NT, 1) sweep_staged_kernel(SweepArgs A,
                 const int carry = ((int)q >> 31) + (old + q < old ? 1 : 0);
                 if (carry) atomicAdd(&A.F[face_off + face], (double)carry * S.wmax[k] * WIN_CARRY);
               }
+            }
+          }
+          __syncwarp();
+        }
+      }
+      // ---- 3D: the warp tallies the x- and y-face items of the particles that ended in this
+      // pass together (lists 2 lane and 2 lane + 1, concatenated in order and cut into 32
+      // equal contiguous chunks, one per lane), with global atomics ----
+      if (DIM == 3 && !ADJ && useF) {
+        int incl = nx3 + ny3;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+          const int t = __shfl_up_sync(0xffffffffu, incl, o);
+          if (lane >= o) incl += t;
+        }
+        const int total = __shfl_sync(0xffffffffu, incl, 31);
+        if (total > 0) {
+          const int4* tab = reinterpret_cast<const int4*>(win) + (threadIdx.x >> 5) * COOP3_INT4_PER_WARP;
+          int* lst = reinterpret_cast<int*>(reinterpret_cast<int4*>(win) + (threadIdx.x >> 5) * COOP3_INT4_PER_WARP +
+                                            3 * COOP3_LISTS);
+          const int excl = incl - nx3 - ny3;
+          lst[2 * lane] = excl;
+          lst[2 * lane + 1] = excl + nx3;
+          if (lane == 31) lst[COOP3_LISTS] = total;
+          __syncwarp();
+          const int k0 = (lane * total) >> 5, k1 = ((lane + 1) * total) >> 5;
+          if (k0 < k1) {
+            int l = 0;  // the last list starting at or before k0
+#pragma unroll
+            for (int st = 32; st > 0; st >>= 1)
+              if (lst[l + st] <= k0) l += st;
+            int lend = lst[l + 1];
+            int4 pa = tab[3 * l], pb = tab[3 * l + 1], pc = tab[3 * l + 2];
+#pragma unroll 1
+            for (int kk = k0; kk < k1; ++kk) {
+              if (kk >= lend) {  // the next non-empty list
+                do {
+                  ++l;
+                  lend = lst[l + 1];
+                } while (lend <= kk);
+                pa = tab[3 * l];
+                pb = tab[3 * l + 1];
+                pc = tab[3 * l + 2];
+              }
+              const float fk = small_int_float(kk - lst[l]);
+              const int face = pa.x + (kk - lst[l]) * pa.y +
+                               pa.z * min(ceil_count(fmaf(fk, __int_as_float(pb.w), __int_as_float(pb.z))), pa.w) +
+                               pb.x * min(ceil_count(fmaf(fk, __int_as_float(pc.y), __int_as_float(pc.x))), pb.y);
+              const double val = __hiloint2double(pc.w, pc.z);
+              if (K32) tally_k32(&S.F32[face_off + face], val);
+              else atomicAdd(&A.F[face_off + face], val);
             }
           }
           __syncwarp();
