@@ -159,7 +159,7 @@ struct Ctx {
   float* d_mg_t = nullptr;
   float* d_mg_r = nullptr;
   float* d_fd_q = nullptr;       // fast diagonalization: eigenvector matrices (FP32)
-  double* d_fd_lam = nullptr;    // ... and eigenvalues
+  float* d_fd_lam = nullptr;     // ... and eigenvalues
   long long mg_level_cells = 0;
   // staged sweep
   long long* d_inst_beg = nullptr;   // [n_inst] forward particle range per instance

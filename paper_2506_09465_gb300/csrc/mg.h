@@ -17,7 +17,7 @@ struct InstMG {
   int direct;
   int fnx, fny;            // sizes of Tx and Ty (fny = 1 in 1D)
   long long qx_off, qy_off;  // offsets of Qx, Qy (row-major, eigenvectors in columns) in the FP32 array
-  long long lx_off, ly_off;  // offsets of the eigenvalues in the FP64 array
+  long long lx_off, ly_off;  // offsets of the eigenvalues in the FP32 array
   int n[MG_MAXL][3];
   long long nc[MG_MAXL];
   long long off[MG_MAXL];  // offset of each level in the FP32 level arrays

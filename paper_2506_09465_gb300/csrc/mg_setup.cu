@@ -197,8 +197,7 @@ iugkp_status build_multigrid(Ctx* c, const std::vector<double>& diag, const std:
                              const std::vector<double>& cy, const std::vector<double>& cz,
                              const std::vector<double>& kap, double cvsum) {
   std::vector<InstMG> mgs;
-  std::vector<float> ldiag, ldinv, lcx, lcy, lcz, cinv, fq;
-  std::vector<double> flam;
+  std::vector<float> ldiag, ldinv, lcx, lcy, lcz, cinv, fq, flam;
   long long level_off = 0;
   for (int k = 0; k < c->n_inst; ++k) {
     const InstDesc& in = c->h_inst[k];
@@ -221,12 +220,12 @@ iugkp_status build_multigrid(Ctx* c, const std::vector<double>& diag, const std:
         m.qx_off = (long long)fq.size();
         m.lx_off = (long long)flam.size();
         for (double x : Q) fq.push_back((float)x);
-        flam.insert(flam.end(), lam.begin(), lam.end());
+        for (double x : lam) flam.push_back((float)x);
         tridiag_eigen(part[1][0], part[1][1], lam, Q);
         m.qy_off = (long long)fq.size();
         m.ly_off = (long long)flam.size();
         for (double x : Q) fq.push_back((float)x);
-        flam.insert(flam.end(), lam.begin(), lam.end());
+        for (double x : lam) flam.push_back((float)x);
       }
     }
     std::vector<Level> lv(1);

@@ -35,7 +35,7 @@ struct MGArgs {
   const float* lcz;
   const float* cinv;        // coarsest dense inverses
   const float* fq;          // fast diagonalization: eigenvector matrices
-  const double* flam;       // ... and eigenvalues
+  const float* flam;        // ... and eigenvalues
   float* lb;                // level right-hand sides
   float* lx;                // level iterates
   float* lt;                // level scratch (ping-pong)
@@ -414,8 +414,8 @@ __device__ int fd_solve(const MGArgs& A, const InstMG& m, cg::cluster_group& cl,
   const long long lo = (long long)j0 * nx, hi = (long long)j1 * nx;  // this CTA's cells
   const float* Qx = A.fq + m.qx_off;
   const float* Qy = A.fq + m.qy_off;
-  const double* lx = A.flam + m.lx_off;
-  const double* ly = A.flam + m.ly_off;
+  const float* lx = A.flam + m.lx_off;
+  const float* ly = A.flam + m.ly_off;
   float* Sf = A.lt + m.off[0];  // scaled residual (FP32)
   float* T1 = A.lb + m.off[0];  // Qy^T S, then Qy T2
   float* T2 = A.lx + m.off[0];  // (Qy^T S Qx) ./ (ly + lx)
@@ -447,7 +447,7 @@ __device__ int fd_solve(const MGArgs& A, const InstMG& m, cg::cluster_group& cl,
     rows_product<NT>(
         j0, j1, nx, nx, [&](int j, int k) { return __ldcg(&T1[(long long)j * nx + k]); },
         [&](int k, int i) { return __ldg(&Qx[(long long)k * nx + i]); },
-        [&](int j, int i, float x) { T2[(long long)j * nx + i] = (float)((double)x / (ly[j] + lx[i])); }, sl, sr);
+        [&](int j, int i, float x) { T2[(long long)j * nx + i] = x / (ly[j] + lx[i]); }, sl, sr);
     cl.sync();
     // T1 = Qy T2, then the correction T1 Qx^T added to the FP64 solution (scaled back)
     rows_product<NT>(
