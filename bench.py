@@ -46,6 +46,8 @@ def parse():
     ap.add_argument("--profile", default=None, choices=["sweep", "step", "persistent"],
                     help="run --warmup then --steps sweeps (or full steps) of the workload and exit; for ncu")
     ap.add_argument("--kn", type=float, default=None, help="profile one Knudsen number only")
+    ap.add_argument("--workload", default="cavity", choices=["cavity", "box32"],
+                    help="profiled workload: the bench batch, or one 32^3 box of the 3D box batch")
     ap.add_argument("--mode", default="fast", choices=["fast", "plain64", "plain32"], help="profiled path")
     ap.add_argument("--no-flux", action="store_true", help="profile the sweep without face tallies (F = NULL)")
     ap.add_argument("--refill", type=int, default=0, help="staged sweep refill threshold (0 = auto)")
@@ -78,6 +80,9 @@ def run_profile(args):
               ev0.elapsed_time(ev1) / max(1, args.steps))
         return
     wl = WL.cavity_sweep(NGRID, kns, NPART)
+    if args.workload == "box32":  # one box of the 3D two-material batch (32^3, 256 particles per cell)
+        wl = WL.box_batch(16)
+        wl.instances = [WL.two_material_box(32)]
     opt = {"fast": {"refill_lanes": args.refill}, "plain64": {"precision": 0, "tally": 0, "schedule": 0},
            "plain32": {"precision": 1, "tally": 0, "schedule": 0}}[args.mode]
     s = make_solver(wl, seed=0, **opt)
