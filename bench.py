@@ -350,7 +350,7 @@ def persistent_scheme_time(wl, make_solver, steps=10, warmup=3):
     same batch, with FP32 and with FP64 tracking: the state of every slot is read and written
     once per iteration. Time per iteration (CUDA events), flights/s, and the algorithmic
     state traffic against the measured HBM bandwidth (2D: position and direction (4 words),
-    weight and 3 ints read; the same words and 2 ints written per slot)."""
+    weight, band and home read; the same words but the band written per slot)."""
     import torch
     out = {}
     for prec in ("fp32", "fp64"):
@@ -376,7 +376,7 @@ def _persistent_time(wl, make_solver, prec, steps, warmup):
     slots = g["slots"]
     flights = int(g["counters"][0].item())
     rb = 4 if prec == "fp32" else 8   # position and direction words
-    bytes_per_step = slots * (4 * rb + 8 + 3 * 4 + 4 * rb + 8 + 2 * 4)
+    bytes_per_step = slots * (4 * rb + 8 + 2 * 4 + 4 * rb + 8 + 4)
     peak = 6783.5
     try:
         peak = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["hbm_gbs"]

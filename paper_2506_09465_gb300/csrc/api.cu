@@ -135,7 +135,7 @@ void free_all(Ctx* c) {
                   c->d_group_mag, c->d_mag, c->d_wall_unit, c->d_all_beg, c->d_all_end, c->d_all_cost_prefix,
                   c->d_all_group_mag, c->d_R32, c->d_W32, c->d_F32, c->d_m2, c->d_wallTf,
                   c->d_pslot_off, c->d_phome_off, c->d_pnband, c->d_pnwall, c->d_px, c->d_pband, c->d_phome,
-                  c->d_pdue, c->d_pcount, c->d_phome_w, c->d_wemit, c->d_DY, c->d_EY, c->d_GX, c->d_Fd,
+                  c->d_pcount, c->d_pfcount, c->d_phome_w, c->d_wemit, c->d_DY, c->d_EY, c->d_GX, c->d_Fd,
                   c->d_all_real, c->d_defer, c->d_defer_n};
   for (void* p : ptrs)
     if (p) cudaFree(p);
@@ -1290,6 +1290,9 @@ iugkp_status iugkp_solve_steady(iugkp_ctx* ctx, double* T_inout_dev, double tol,
   return IUGKP_OK;
 }
 
+// Boundary-face homes of the persistent population over all instances and bands.
+static long long pers_face_homes(const Ctx* c) { return c->pers_homes - (long long)c->nb * c->total_cells; }
+
 iugkp_status iugkp_persistent_reset(iugkp_ctx* ctx, void* cuda_stream) {
   if (!ctx) return IUGKP_EINVAL;
   Ctx* c = &ctx->c;
@@ -1307,13 +1310,13 @@ iugkp_status iugkp_persistent_reset(iugkp_ctx* ctx, void* cuda_stream) {
   if (slot_off[c->n_inst] >= (1ll << 31)) return fail(c, IUGKP_EINVAL, "persistent population above 2^31 slots");
   if (c->pers_n != slot_off[c->n_inst] || !c->d_px) {
     void* olds[] = {c->d_pslot_off, c->d_phome_off, c->d_pnband, c->d_pnwall, c->d_px, c->d_pband, c->d_phome,
-                    c->d_pdue, c->d_pcount, c->d_phome_w};
+                    c->d_pcount, c->d_pfcount, c->d_phome_w};
     for (void* p : olds)
       if (p) cudaFree(p);
     c->d_pslot_off = c->d_phome_off = c->d_pnband = c->d_pnwall = nullptr;
     c->d_px = nullptr;
-    c->d_pband = c->d_phome = c->d_pdue = nullptr;
-    c->d_pcount = nullptr;
+    c->d_pband = c->d_phome = nullptr;
+    c->d_pcount = c->d_pfcount = nullptr;
     c->d_phome_w = nullptr;
     c->pers_n = slot_off[c->n_inst];
     c->pers_homes = home_off[c->n_inst];
@@ -1325,11 +1328,13 @@ iugkp_status iugkp_persistent_reset(iugkp_ctx* ctx, void* cuda_stream) {
     if ((st = dalloc(c, &c->d_px, (size_t)7 * c->pers_n)) != IUGKP_OK) return st;
     if ((st = dalloc(c, &c->d_pband, (size_t)c->pers_n)) != IUGKP_OK) return st;
     if ((st = dalloc(c, &c->d_phome, (size_t)c->pers_n)) != IUGKP_OK) return st;
-    if ((st = dalloc(c, &c->d_pdue, (size_t)c->pers_n)) != IUGKP_OK) return st;
     if ((st = dalloc(c, &c->d_pcount, (size_t)2 * c->pers_homes)) != IUGKP_OK) return st;
+    if ((st = dalloc(c, &c->d_pfcount, (size_t)2 * PERS_FACE_REPLICAS * pers_face_homes(c))) != IUGKP_OK) return st;
     if ((st = dalloc(c, &c->d_phome_w, (size_t)c->pers_homes)) != IUGKP_OK) return st;
   }
   c->pers_parity = 0;
+  CK(cudaMemsetAsync(c->d_pfcount, 0, (size_t)2 * PERS_FACE_REPLICAS * pers_face_homes(c) * sizeof(unsigned), s),
+     "clear face counts");
   CK(launch_persistent_init(c, s), "persistent init");
   return check_device(c, s);
 }
@@ -1350,6 +1355,10 @@ iugkp_status iugkp_persistent_step(iugkp_ctx* ctx, const double* T_dev, unsigned
   CK(cudaMemsetAsync(W, 0, bc * sizeof(double), s), "clear W");
   CK(cudaMemsetAsync(wall, 0, (size_t)c->total_walls * sizeof(double), s), "clear wall");
   CK(cudaMemsetAsync(cnt, 0, CNT_N * sizeof(unsigned long long), s), "clear counters");
+  {
+    const size_t fr = (size_t)PERS_FACE_REPLICAS * pers_face_homes(c);
+    CK(cudaMemsetAsync(c->d_pfcount + (c->pers_parity ? 0 : fr), 0, fr * sizeof(unsigned), s), "clear face counts");
+  }
   CK(cudaMemsetAsync(c->d_pcount + (c->pers_parity ? 0 : c->pers_homes), 0, (size_t)c->pers_homes * sizeof(unsigned), s),
      "clear counts");
   CK(launch_persistent_step(c, T_dev, iteration, R_dev, W, wall, cnt, s), "persistent step");

@@ -64,6 +64,13 @@ struct Stream {
     buf = philox4x32_10(ctr, key);  // block 0 holds the first emission draws
     j = 0;
   }
+  // The same stream with no block computed yet (the first next_pair or load_block does it).
+  __device__ __forceinline__ void init_lazy(unsigned long long seed, uint32_t inst_id, uint32_t band,
+                                            uint32_t epoch, uint32_t emitter, uint32_t particle) {
+    key = make_uint2((uint32_t)seed, (uint32_t)(seed >> 32) ^ inst_id);
+    ctr = make_uint4(0u, particle, emitter, (band << 24) | (epoch & 0xFFFFFFu));
+    j = 0;
+  }
   __device__ __forceinline__ void load_block(uint32_t blk) {
     uint4 c = ctr;
     c.x = blk;
@@ -90,6 +97,15 @@ struct Stream {
 // phi (dim >= 2); wall tangential positions, mu_n, phi (dim >= 2).
 __host__ __device__ constexpr int thermal_uniforms(int dim) { return dim == 1 ? 2 : (dim == 2 ? 4 : 6); }
 __host__ __device__ constexpr int wall_uniforms(int dim) { return dim == 1 ? 2 : 4; }
+
+// Exact n / d for n < 2^31 and d >= 1 with M = floor((2^32 - 1) / d) from the host: since
+// 2^32/d - 1 <= M < 2^32/d, umulhi(n, M) is floor(n/d) or one less, and one comparison of
+// the remainder fixes it. Integer operations only (conversions issue at a low rate here).
+__device__ __forceinline__ unsigned udiv(unsigned n, unsigned d, unsigned M) {
+  unsigned q = __umulhi(n, M);
+  q += (n - q * d >= d) ? 1u : 0u;
+  return q;
+}
 
 template <typename Real>
 struct RealTraits;

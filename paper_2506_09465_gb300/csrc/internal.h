@@ -13,6 +13,12 @@
 
 namespace iugkp {
 
+// Counts of particles absorbed through one boundary face are spread over this many copies
+// (by lane), summed when the face's power is shared out: a wall face receives far more
+// absorptions per iteration than a cell receives real collisions, and same-address atomics
+// serialise at the L2.
+constexpr int PERS_FACE_REPLICAS = 32;
+
 struct InstMG;
 
 // Arguments of the forward and adjoint sweep kernels (all device pointers).
@@ -142,8 +148,8 @@ struct Ctx {
   double* d_phome_w = nullptr;    // [pers_homes] power per re-emitted particle of each home
   int* d_pband = nullptr;
   int* d_phome = nullptr;
-  int* d_pdue = nullptr;
-  unsigned* d_pcount = nullptr;   // [2 * pers_homes]
+  unsigned* d_pcount = nullptr;   // [2 * pers_homes] (cell homes; the entries of face homes stay 0)
+  unsigned* d_pfcount = nullptr;  // [2 * PERS_FACE_REPLICAS * face homes] face-home counts, replicated
   double* h_pinned = nullptr;    // [8 + n_inst] host readback
   // multigrid preconditioner of the Newton correction (mg_setup.cu, mgpcg.cu)
   struct InstMG* d_mg = nullptr;

@@ -10,7 +10,10 @@
 // w = S_{b,c} / N(b, c) in a cell (S = C_b T_emit V / tau_b, T_emit = T + Q/m), and
 // w = (C_b v_b T_face A / 4) / N(b, face) on a face. A null candidate keeps its position,
 // direction and weight and flies again. One thread per particle; state in structure-of-
-// arrays form, read and written once per iteration (coalesced).
+// arrays form, read and written once per iteration (coalesced, streaming: the state does not
+// displace the descriptors and the home powers from the caches). A slot's home word carries
+// its due flag in the top bit. The face-home index of face bf of instance k, band b is
+// home_off[k] - nb cell_off[k] + b nbf_k + bf (the homes less the cell homes before it).
 //
 // Slots of an instance: per band, N_b per cell in q-major order (slot q * ncells + cell, so
 // neighbouring slots start in different cells and their tallies rarely meet at one
@@ -43,6 +46,7 @@ struct PArgs {
   const float* ratio32;        // [bc] tau_maj / tau in FP32
   const float* vtm32;          // [inst * nb] v_b tau_maj in FP32
   const int* all_real;         // [inst * nb] 1 where tau = tau_maj in every cell
+  const unsigned* mag;         // [5 n_inst] division magics of n_x, n_y, and n((a+1)%3) per wall axis a
   const double* taumaj;        // [inst * nb]
   const double* v;             // [nb]
   const double* wcoef;         // [inst * nb * 6] C_b v_b A / (4 N_w)
@@ -51,10 +55,11 @@ struct PArgs {
   double* pw;                  // [n_slots] weights
   const double* home_w;        // [homes] power per particle re-emitted from each home
   const int* band;
-  int* home;
-  int* due;
+  unsigned* home;              // home index | DUE_BIT when due for re-emission
   const unsigned* n_prev;
-  unsigned* n_new;
+  unsigned* n_new;             // [homes] counts of cell homes
+  unsigned* f_new;             // [PERS_FACE_REPLICAS][face homes] counts of boundary-face homes
+  long long n_fhomes;          // face homes of all instances and bands
   double* R;
   double* W;
   double* wall;
@@ -119,53 +124,128 @@ __device__ __forceinline__ double accept_ratio<double>(const PArgs& A, long long
 template <>
 __device__ __forceinline__ float accept_ratio<float>(const PArgs& A, long long jb) { return A.ratio32[jb]; }
 
-// Wall power is accumulated per block in shared memory and flushed once: every absorption
-// adding to one of 2 dim addresses per instance in global memory would serialise at the L2.
+// Quotients of the flight geometry (distance to a wall, position over cell size): IEEE
+// division in FP64 tracking; in FP32 tracking the reciprocal approximation (2 ulp), well inside
+// the FP32 rounding the positions carry anyway.
+template <typename Real>
+__device__ __forceinline__ Real quot(Real a, Real b) { return a / b; }
+template <>
+__device__ __forceinline__ float quot<float>(float a, float b) { return __fdividef(a, b); }
+
+// Wall power: each thread sums its absorptions per wall of the instance it is in (one FP64
+// add per absorption); a warp adds its sums, grouped by wall, to the block's shared copy when
+// the instance of one of its lanes changes and at the end, and the block adds its copy to
+// global memory once (every absorption adding to one of 2 dim addresses per instance in global
+// memory would serialise at the L2).
 constexpr int PERS_SHARED_WALLS = 384;
 
+constexpr int PERS_NT = 256;            // threads per block of the step kernel
+constexpr int PERS_SHARED_INST = 32;    // instance descriptors copied to shared memory
+constexpr unsigned DUE_BIT = 0x80000000u;
+
+// acc: the block's per-thread sums, [wall of the instance][thread] in shared memory.
+template <int NW>
+__device__ __forceinline__ void flush_wall_sums(double* acc, int k_acc, bool to_shared, double* swall, double* wall,
+                                                int lane) {
+#pragma unroll
+  for (int q = 0; q < NW; ++q) {
+    const double v = acc[q * PERS_NT + threadIdx.x];
+    const int key = NW * k_acc + q;  // wall index: 2 dim per instance, in instance order
+    unsigned pending = __ballot_sync(0xffffffffu, v != 0.0);
+    while (pending) {
+      const int lead = __shfl_sync(0xffffffffu, key, __ffs(pending) - 1);
+      const bool mine = key == lead && v != 0.0;
+      double x = mine ? v : 0.0;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+      if (lane == 0) {
+        if (to_shared) atomicAdd(&swall[lead], x);
+        else atomicAdd(&wall[lead], x);
+      }
+      pending &= ~__ballot_sync(0xffffffffu, mine);
+    }
+    acc[q * PERS_NT + threadIdx.x] = 0.0;
+  }
+}
+
 template <int DIM, typename Real>
-__global__ void __launch_bounds__(256, 4) persistent_step_kernel(PArgs A) {
+__global__ void __launch_bounds__(PERS_NT, 4) persistent_step_kernel(PArgs A) {
+  constexpr int NW = 2 * DIM;
   __shared__ double swall[PERS_SHARED_WALLS];
+  __shared__ double wacc[NW * PERS_NT];  // this thread's absorbed power per wall of instance k_acc
+  __shared__ InstDesc sinst[PERS_SHARED_INST];
   const int n_walls = 2 * DIM * A.n_inst;
   const bool wall_shared = n_walls <= PERS_SHARED_WALLS;
+  const bool inst_shared = A.n_inst <= PERS_SHARED_INST;
   for (int j = threadIdx.x; j < PERS_SHARED_WALLS; j += blockDim.x) swall[j] = 0.0;
+  if (inst_shared) {
+    const int words = A.n_inst * (int)(sizeof(InstDesc) / sizeof(int));
+    for (int j = threadIdx.x; j < words; j += blockDim.x)
+      reinterpret_cast<int*>(sinst)[j] = reinterpret_cast<const int*>(A.inst)[j];
+  }
+#pragma unroll
+  for (int q = 0; q < NW; ++q) wacc[q * PERS_NT + threadIdx.x] = 0.0;
   __syncthreads();
+  const InstDesc* INS = inst_shared ? sinst : A.inst;
   Real* px = reinterpret_cast<Real*>(A.state);
-  Real* py = px + A.n_slots;
-  Real* pz = px + 2 * A.n_slots;
-  Real* sx = px + 3 * A.n_slots;
-  Real* sy = px + 4 * A.n_slots;
-  Real* sz = px + 5 * A.n_slots;
+  const long long ns = A.n_slots;
   unsigned c_flights = 0, c_cand = 0, c_real = 0, c_exit = 0;
   const int lane = threadIdx.x & 31;
+  int k = 0, k_acc = 0;
+  long long k_beg = 0, k_end = A.slot_off[1];  // slots of instance k (slots only grow below)
+  // per (instance, band): reloaded when either changes (bands change rarely along a thread's
+  // slots, instances more rarely still)
+  int kb = -1;
+  double tm = 0.0;
+  Real vtm = (Real)0;
+  bool all_real = false;
+  long long hbase = 0;  // offset of the (instance, band)'s homes
+  long long fbase = 0;  // offset of its face homes among all face homes
   // every thread of a block runs the same number of passes, so warps are converged at the
-  // end of each pass (for the warp reduction of the wall tallies)
-  for (long long base = (long long)blockIdx.x * blockDim.x; base < A.n_slots;
-       base += (long long)gridDim.x * blockDim.x) {
+  // start and end of each pass (for the warp sums of the wall tallies)
+  for (long long base = (long long)blockIdx.x * blockDim.x; base < ns; base += (long long)gridDim.x * blockDim.x) {
     const long long i = base + threadIdx.x;
-    int exit_key = -1;  // global wall index of this pass's absorption, if any
-    double exit_w = 0.0;
-    if (i < A.n_slots) {
-    int k = 0;
-    while (k + 1 < A.n_inst && A.slot_off[k + 1] <= i) ++k;
-    const InstDesc& in = A.inst[k];
-    const long long local = i - A.slot_off[k];
-    const int b = A.band[i];
-    const int n0 = in.n[0], n1 = in.n[1], n2 = in.n[2];
-    const int nbf = in.wface_off[2 * DIM - 1] + in.n[((2 * DIM - 1) / 2 + 1) % 3] * in.n[((2 * DIM - 1) / 2 + 2) % 3];
-    const long long nh = (long long)in.ncells + nbf;  // homes per band
-    Stream st;
-    st.init(A.seed, in.inst_id, (uint32_t)b, A.it, 0x80000000u, (uint32_t)local);
-    Real x[3] = {px[i], DIM >= 2 ? py[i] : (Real)0, DIM >= 3 ? pz[i] : (Real)0};
-    Real s[3] = {sx[i], DIM >= 2 ? sy[i] : (Real)0, DIM >= 3 ? sz[i] : (Real)0};
-    double w = A.pw[i];
-    int h = A.home[i];
-    st.j = 0;
-    if (A.due[i]) {
-      w = A.home_w[A.home_off[k] + (long long)b * nh + h];
+    if (i < ns)
+      while (k + 1 < A.n_inst && k_end <= i) {
+        k_beg = k_end;
+        k_end = A.slot_off[++k + 1];
+      }
+    if (__any_sync(0xffffffffu, k != k_acc)) {
+      flush_wall_sums<NW>(wacc, k_acc, wall_shared, swall, A.wall, lane);
+      k_acc = k;
+    }
+    if (i >= ns) continue;
+    const InstDesc& in = INS[k];
+    const int b = __ldcs(A.band + i);
+    const unsigned hw = __ldcs(A.home + i);
+    Real x[3], s[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      x[a] = a < DIM ? __ldcs(px + a * ns + i) : (Real)0;
+      s[a] = a < DIM ? __ldcs(px + (3 + a) * ns + i) : (Real)0;
+    }
+    double w = __ldcs(A.pw + i);
+    int h = (int)(hw & ~DUE_BIT);
+    const int n0 = in.n[0], n1 = in.n[1];
+    if (k * A.nb + b != kb) {
+      kb = k * A.nb + b;
+      tm = A.taumaj[kb];
+      vtm = mean_path<Real>(A, k, b, tm);
+      all_real = A.all_real[kb] != 0;
+      const int nbf = in.wface_off[2 * DIM - 1] + in.n[((2 * DIM - 1) / 2 + 1) % 3] * in.n[((2 * DIM - 1) / 2 + 2) % 3];
+      hbase = A.home_off[k] + (long long)b * ((long long)in.ncells + nbf);
+      fbase = A.home_off[k] - (long long)A.nb * in.cell_off + (long long)b * nbf;
+    }
+    Stream st;  // block 0 is computed by the emission, or else by the flight's draw
+    st.init_lazy(A.seed, in.inst_id, (uint32_t)b, A.it, 0x80000000u, (uint32_t)(i - k_beg));
+    if (hw & DUE_BIT) {
+      w = A.home_w[hbase + h];
+      st.load_block(0);
       if (h < in.ncells) {
         // re-emission in the cell of the real collision (Sec. 3.2 step (2))
-        const int ci[3] = {h % n0, (h / n0) % n1, h / (n0 * n1)};
+        const unsigned r0 = udiv((unsigned)h, (unsigned)n0, A.mag[k]);
+        const unsigned r1 = DIM == 3 ? udiv(r0, (unsigned)n1, A.mag[A.n_inst + k]) : 0u;
+        const int ci[3] = {h - (int)r0 * n0, (int)(r0 - r1 * (unsigned)n1), (int)r1};
         const Real hx = cell_h<Real>(in, 0), hy = cell_h<Real>(in, 1), hz = cell_h<Real>(in, 2);
         Real u_mu, u_phi = (Real)0.5;
         if (DIM == 1) {
@@ -202,10 +282,11 @@ __global__ void __launch_bounds__(256, 4) persistent_step_kernel(PArgs A) {
         const int a = wl >> 1, side = wl & 1, o1 = (a + 1) % 3, o2 = (a + 2) % 3;
         const int j = bf - in.wface_off[wl];
         const int no1 = in.n[o1];
+        const int jq = (int)udiv((unsigned)j, (unsigned)no1, A.mag[2 * A.n_inst + 3 * k + a]);
         int f[3] = {0, 0, 0};
         put(f, a, side ? in.n[a] : 0);
-        put(f, o1, j % no1);
-        put(f, o2, j / no1);
+        put(f, o1, j - jq * no1);
+        put(f, o2, jq);
         Real u_n, u_phi = (Real)0.5;
         if (DIM == 1) {
           u_n = word_uniform<Real>(st.buf.x);
@@ -241,79 +322,64 @@ __global__ void __launch_bounds__(256, 4) persistent_step_kernel(PArgs A) {
     c_flights += 1;
     uint32_t ua, ub;
     st.next_pair(ua, ub);
-    const double tm = A.taumaj[(long long)k * A.nb + b];
-    const Real ell = -RealTraits<Real>::log_(word_uniform<Real>(ua)) * mean_path<Real>(A, k, b, tm);
+    const Real ell = -RealTraits<Real>::log_(word_uniform<Real>(ua)) * vtm;
     Real tw = RealTraits<Real>::inf();
     int wl = -1;
 #pragma unroll
     for (int a = 0; a < DIM; ++a) {
       if (s[a] == (Real)0) continue;
       const Real L = cell_h<Real>(in, a) * int_to_real<Real>(in.n[a]);
-      const Real t = s[a] > (Real)0 ? (L - x[a]) / s[a] : -x[a] / s[a];
+      const Real t = quot<Real>(s[a] > (Real)0 ? L - x[a] : -x[a], s[a]);
       if (t < tw) {
         tw = t;
         wl = 2 * a + (s[a] > (Real)0 ? 1 : 0);
       }
     }
-    int due = 1;
+    unsigned due = DUE_BIT;
     if (wl >= 0 && tw < ell) {
       // absorbed by the wall it reaches first; its home is the face it crossed
       c_exit += 1;
-      exit_key = in.wall_off + wl;
-      exit_w = w;
+      wacc[wl * PERS_NT + threadIdx.x] += w;
       const int a = wl >> 1, o1 = (a + 1) % 3, o2 = (a + 2) % 3;
       int j1 = 0, j2 = 0;
-      if (o1 < DIM) j1 = min(floor_nonneg<Real>((pick(x, o1) + tw * pick(s, o1)) / cell_h<Real>(in, o1)), in.n[o1] - 1);
-      if (o2 < DIM) j2 = min(floor_nonneg<Real>((pick(x, o2) + tw * pick(s, o2)) / cell_h<Real>(in, o2)), in.n[o2] - 1);
-      h = in.ncells + in.wface_off[wl] + j2 * in.n[o1] + j1;
-      atomicAdd(&A.n_new[A.home_off[k] + (long long)b * nh + h], 1u);
+      if (o1 < DIM) j1 = min(floor_nonneg<Real>(quot<Real>(pick(x, o1) + tw * pick(s, o1), cell_h<Real>(in, o1))), in.n[o1] - 1);
+      if (o2 < DIM) j2 = min(floor_nonneg<Real>(quot<Real>(pick(x, o2) + tw * pick(s, o2), cell_h<Real>(in, o2))), in.n[o2] - 1);
+      const int bf = in.wface_off[wl] + j2 * in.n[o1] + j1;
+      h = in.ncells + bf;
+      atomicAdd(&A.f_new[(long long)lane * A.n_fhomes + fbase + bf], 1u);
     } else {
       int ci[3] = {0, 0, 0};
 #pragma unroll
       for (int a = 0; a < DIM; ++a) {
         x[a] += ell * s[a];
-        ci[a] = min(floor_nonneg<Real>(x[a] / cell_h<Real>(in, a)), in.n[a] - 1);
+        ci[a] = min(floor_nonneg<Real>(quot<Real>(x[a], cell_h<Real>(in, a))), in.n[a] - 1);
       }
       const int c = ci[0] + n0 * (ci[1] + n1 * ci[2]);
-      // candidate (steps (4)-(5)): W from every candidate, R and the count from real ones
+      // candidate (steps (4)-(5)): W from every candidate, R and the count from real ones;
+      // W collects w here and is scaled by tau_maj afterwards, and a band with tau = tau_maj
+      // in every cell accepts every candidate (the uniform is below 1), so its W is tau_maj R
       c_cand += 1;
       const long long jb = in.bc_off + (long long)b * in.ncells + c;
-      atomicAdd(&A.W[jb], w * tm);
-      // (a band with tau = tau_maj everywhere accepts every candidate: the uniform is below 1)
-      if (A.all_real[(long long)k * A.nb + b] || word_uniform<Real>(ub) < accept_ratio<Real>(A, jb)) {
+      if (all_real || word_uniform<Real>(ub) < accept_ratio<Real>(A, jb)) {
         c_real += 1;
+        if (!all_real) atomicAdd(&A.W[jb], w);
         atomicAdd(&A.R[jb], w);
         h = c;
-        atomicAdd(&A.n_new[A.home_off[k] + (long long)b * nh + h], 1u);
+        atomicAdd(&A.n_new[hbase + h], 1u);
       } else {
-        due = 0;  // step (6): same direction and weight, a new path next iteration
+        atomicAdd(&A.W[jb], w);
+        due = 0u;  // step (6): same direction and weight, a new path next iteration
       }
     }
-    px[i] = x[0];
-    if (DIM >= 2) py[i] = x[1];
-    if (DIM >= 3) pz[i] = x[2];
-    sx[i] = s[0];
-    if (DIM >= 2) sy[i] = s[1];
-    if (DIM >= 3) sz[i] = s[2];
-    A.pw[i] = w;
-    A.home[i] = h;
-    A.due[i] = due;
-    (void)n2;
-    }
-    // wall tallies: the lanes that hit one wall are summed first, one atomic per wall
-    unsigned pending = __ballot_sync(0xffffffffu, exit_key >= 0);
-    while (pending) {
-      const int key = __shfl_sync(0xffffffffu, exit_key, __ffs(pending) - 1);
-      double v = exit_key == key ? exit_w : 0.0;
 #pragma unroll
-      for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-      if (lane == 0) {
-        if (wall_shared) atomicAdd(&swall[key], v);
-        else atomicAdd(&A.wall[key], v);
-      }
-      pending &= ~__ballot_sync(0xffffffffu, exit_key == key);
+    for (int a = 0; a < DIM; ++a) {
+      __stcs(px + a * ns + i, x[a]);
+      __stcs(px + (3 + a) * ns + i, s[a]);
     }
+    __stcs(A.pw + i, w);
+    __stcs(A.home + i, (unsigned)h | due);
   }
+  flush_wall_sums<NW>(wacc, k_acc, wall_shared, swall, A.wall, lane);
   __syncthreads();
   if (wall_shared)
     for (int j = threadIdx.x; j < n_walls; j += blockDim.x)
@@ -329,14 +395,26 @@ __global__ void __launch_bounds__(256, 4) persistent_step_kernel(PArgs A) {
   }
 }
 
+// W of the step: the kernel summed w per candidate, or nothing for bands whose every
+// candidate is real (there W = tau_maj R); both are scaled by the instance's tau_maj here.
+__global__ void persistent_finish_W_kernel(const InstDesc* inst, int n_inst, int nb, const double* taumaj,
+                                           const int* all_real, const double* R, double* W, long long total) {
+  for (long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x; j < total; j += (long long)gridDim.x * blockDim.x) {
+    int k = 0;
+    while (k + 1 < n_inst && inst[k + 1].bc_off <= j) ++k;
+    const int kb = k * nb + (int)((j - inst[k].bc_off) / inst[k].ncells);
+    W[j] = (all_real[kb] ? R[j] : W[j]) * taumaj[kb];
+  }
+}
+
 // Power per particle re-emitted from each (band, home) this iteration: the home's power
 // (C_b T_emit V / tau_b for a cell, C_b v_b T_face A / 4 for a boundary face) over the
 // particles that ended there in the previous iteration (0 where none did).
 __global__ void persistent_home_power_kernel(const InstDesc* inst, int n_inst, int nb, const long long* home_off,
                                              const long long* nband, const long long* nwall, const double* T,
                                              const double* srcshift, const double* coef, const double* wcoef,
-                                             const double* wallTf, const unsigned* n_prev, double* home_w,
-                                             long long n_homes) {
+                                             const double* wallTf, const unsigned* n_prev, const unsigned* f_prev,
+                                             long long n_fhomes, double* home_w, long long n_homes) {
   for (long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x; j < n_homes;
        j += (long long)gridDim.x * blockDim.x) {
     int k = 0;
@@ -346,7 +424,14 @@ __global__ void persistent_home_power_kernel(const InstDesc* inst, int n_inst, i
     const long long r = j - home_off[k];
     const int b = (int)(r / nh);
     const long long h = r - (long long)b * nh;
-    const unsigned n = n_prev[j];
+    unsigned n = 0;
+    if (h < in.ncells) {
+      n = n_prev[j];
+    } else {
+      const long long f = home_off[k] - (long long)nb * in.cell_off + (long long)b * (nh - in.ncells) + (h - in.ncells);
+#pragma unroll 8
+      for (int q = 0; q < PERS_FACE_REPLICAS; ++q) n += f_prev[(long long)q * n_fhomes + f];
+    }
     double pw = 0.0;
     if (n > 0) {
       if (h < in.ncells) {
@@ -384,6 +469,7 @@ cudaError_t launch_persistent_step(const Ctx* c, const double* T, unsigned it, d
   a.ratio32 = c->d_ratio32;
   a.vtm32 = c->d_vtm32;
   a.all_real = c->d_all_real;
+  a.mag = c->d_mag;
   a.taumaj = c->d_taumaj;
   a.v = c->d_v;
   a.wcoef = c->d_wcoef;
@@ -392,10 +478,13 @@ cudaError_t launch_persistent_step(const Ctx* c, const double* T, unsigned it, d
   a.pw = reinterpret_cast<double*>(c->d_px) + 6 * c->pers_n;  // after 6 arrays of FP64 or FP32
   a.home_w = c->d_phome_w;
   a.band = c->d_pband;
-  a.home = c->d_phome;
-  a.due = c->d_pdue;
+  a.home = reinterpret_cast<unsigned*>(c->d_phome);
   a.n_prev = c->d_pcount + (c->pers_parity ? c->pers_homes : 0);
   a.n_new = c->d_pcount + (c->pers_parity ? 0 : c->pers_homes);
+  a.n_fhomes = c->pers_homes - (long long)c->nb * c->total_cells;
+  const long long fr = (long long)PERS_FACE_REPLICAS * a.n_fhomes;
+  const unsigned* f_prev = c->d_pfcount + (c->pers_parity ? fr : 0);
+  a.f_new = c->d_pfcount + (c->pers_parity ? 0 : fr);
   a.R = R;
   a.W = W;
   a.wall = wall;
@@ -407,21 +496,25 @@ cudaError_t launch_persistent_step(const Ctx* c, const double* T, unsigned it, d
     const unsigned hb = (unsigned)std::min<long long>((c->pers_homes + 255) / 256 + 1, (long long)c->sm_count * 16);
     persistent_home_power_kernel<<<hb, 256, 0, s>>>(c->d_inst, c->n_inst, c->nb, c->d_phome_off, c->d_pnband,
                                                     c->d_pnwall, T, c->d_srcshift, c->d_coef, c->d_wcoef, c->d_wallTf,
-                                                    a.n_prev, c->d_phome_w, c->pers_homes);
+                                                    a.n_prev, f_prev, a.n_fhomes, c->d_phome_w, c->pers_homes);
     const cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }
-  const long long want = (c->pers_n + 255) / 256;
+  const long long want = (c->pers_n + PERS_NT - 1) / PERS_NT;
   const unsigned blocks = (unsigned)std::min<long long>(std::max<long long>(want, 1), (long long)c->sm_count * 16);
   const bool f32 = c->opt.precision == IUGKP_TRACK_FP32;
   switch (c->dim * 2 + (f32 ? 1 : 0)) {
-    case 2: persistent_step_kernel<1, double><<<blocks, 256, 0, s>>>(a); break;
-    case 3: persistent_step_kernel<1, float><<<blocks, 256, 0, s>>>(a); break;
-    case 4: persistent_step_kernel<2, double><<<blocks, 256, 0, s>>>(a); break;
-    case 5: persistent_step_kernel<2, float><<<blocks, 256, 0, s>>>(a); break;
-    case 6: persistent_step_kernel<3, double><<<blocks, 256, 0, s>>>(a); break;
-    default: persistent_step_kernel<3, float><<<blocks, 256, 0, s>>>(a); break;
+    case 2: persistent_step_kernel<1, double><<<blocks, PERS_NT, 0, s>>>(a); break;
+    case 3: persistent_step_kernel<1, float><<<blocks, PERS_NT, 0, s>>>(a); break;
+    case 4: persistent_step_kernel<2, double><<<blocks, PERS_NT, 0, s>>>(a); break;
+    case 5: persistent_step_kernel<2, float><<<blocks, PERS_NT, 0, s>>>(a); break;
+    case 6: persistent_step_kernel<3, double><<<blocks, PERS_NT, 0, s>>>(a); break;
+    default: persistent_step_kernel<3, float><<<blocks, PERS_NT, 0, s>>>(a); break;
   }
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess || !W) return e;
+  persistent_finish_W_kernel<<<c->sm_count * 4, 256, 0, s>>>(c->d_inst, c->n_inst, c->nb, c->d_taumaj, c->d_all_real,
+                                                             R, W, (long long)c->nb * c->total_cells);
   return cudaGetLastError();
 }
 
@@ -435,8 +528,8 @@ namespace {
 // every home counted with its own number of slots.
 __global__ void persistent_init_kernel(const InstDesc* inst, int n_inst, int nb, const long long* slot_off,
                                        const long long* home_off, const long long* nband, const long long* nwall,
-                                       long long n_slots, long long n_homes, double* state, int* band, int* home,
-                                       int* due, unsigned* count_prev) {
+                                       long long n_slots, long long n_homes, double* state, int* band, unsigned* home,
+                                       unsigned* count_prev, unsigned* fcount_prev) {
   const long long stride = (long long)gridDim.x * blockDim.x;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n_slots; i += stride) {
     int k = 0;
@@ -456,8 +549,7 @@ __global__ void persistent_init_kernel(const InstDesc* inst, int n_inst, int nb,
       h = in.ncells + (int)(r % nbf);
     }
     band[i] = b;
-    home[i] = h;
-    due[i] = 1;
+    home[i] = (unsigned)h | DUE_BIT;
     for (int q = 0; q < 7; ++q) state[q * n_slots + i] = 0.0;
   }
   for (long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x; j < n_homes; j += stride) {
@@ -468,7 +560,9 @@ __global__ void persistent_init_kernel(const InstDesc* inst, int n_inst, int nb,
     const long long r = j - home_off[k];
     const int b = (int)(r / nh);
     const long long h = r - (long long)b * nh;
-    count_prev[j] = (unsigned)(h < in.ncells ? nband[(long long)k * nb + b] : nwall[b]);
+    if (h < in.ncells) count_prev[j] = (unsigned)nband[(long long)k * nb + b];
+    else fcount_prev[home_off[k] - (long long)nb * in.cell_off + (long long)b * (nh - in.ncells) + (h - in.ncells)] =
+        (unsigned)nwall[b];  // copy 0 of the face's counts (the others are cleared)
   }
 }
 
@@ -477,8 +571,8 @@ __global__ void persistent_init_kernel(const InstDesc* inst, int n_inst, int nb,
 cudaError_t launch_persistent_init(Ctx* c, cudaStream_t s) {
   const unsigned blocks = (unsigned)std::min<long long>((c->pers_n + 255) / 256 + 1, (long long)c->sm_count * 16);
   persistent_init_kernel<<<blocks, 256, 0, s>>>(c->d_inst, c->n_inst, c->nb, c->d_pslot_off, c->d_phome_off, c->d_pnband,
-                                                c->d_pnwall, c->pers_n, c->pers_homes, c->d_px, c->d_pband, c->d_phome,
-                                                c->d_pdue, c->d_pcount);
+                                                c->d_pnwall, c->pers_n, c->pers_homes, c->d_px, c->d_pband,
+                                                reinterpret_cast<unsigned*>(c->d_phome), c->d_pcount, c->d_pfcount);
   return cudaGetLastError();
 }
 

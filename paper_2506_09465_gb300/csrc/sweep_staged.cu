@@ -53,15 +53,6 @@ __device__ __forceinline__ void flush_lcounts(LCounts& c, unsigned long long* ou
   }
 }
 
-// Exact n / d for n < 2^31 and d >= 1 with M = floor((2^32 - 1) / d) from the host: since
-// 2^32/d - 1 <= M < 2^32/d, umulhi(n, M) is floor(n/d) or one less, and one comparison of
-// the remainder fixes it. Integer operations only (conversions issue at a low rate here).
-__device__ __forceinline__ unsigned udiv(unsigned n, unsigned d, unsigned M) {
-  unsigned q = __umulhi(n, M);
-  q += (n - q * d >= d) ? 1u : 0u;
-  return q;
-}
-
 // Register-resident path state. The direction does not change at null collisions, so the
 // path from emission to the end (real collision or wall) is one straight segment: i_a is
 // the emission cell, t_a the path length at which the first face normal to axis a is
