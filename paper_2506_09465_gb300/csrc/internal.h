@@ -226,6 +226,8 @@ cudaError_t measure_atomic_rate(int sm_count, double* out_rate);
 cudaError_t launch_mgpcg(const Ctx* c, const double* rhs, cudaStream_t s);
 size_t mg_solo_smem_bytes(const std::vector<InstMG>& h_mg);
 cudaError_t configure_mgpcg(Ctx* c, size_t smem);
+size_t fd_small_smem_bytes();  // dynamic shared memory of the in-shared-memory fast diagonalization
+int fd_small_max_n();          // its largest axis size
 iugkp_status build_multigrid(Ctx* c, const std::vector<double>& diag, const std::vector<double>& cx,
                              const std::vector<double>& cy, const std::vector<double>& cz,
                              const std::vector<double>& kap, double cvsum);

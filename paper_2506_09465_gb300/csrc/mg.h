@@ -14,7 +14,7 @@ struct InstMG {
   // Separable operator (1D, or 2D with uniform kappa): A = Tx (x) I + I (x) Ty with
   // Tx = Qx diag(lx) Qx^T and Ty = Qy diag(ly) Qy^T; solved by fast diagonalization
   // (mgpcg.cu) instead of the multigrid PCG when direct != 0.
-  int direct;
+  int direct;               // 0: multigrid PCG; 1: fast diagonalization; 2: the same in shared memory
   int fnx, fny;            // sizes of Tx and Ty (fny = 1 in 1D)
   long long qx_off, qy_off;  // offsets of Qx, Qy (row-major, eigenvectors in columns) in the FP32 array
   long long lx_off, ly_off;  // offsets of the eigenvalues in the FP32 array

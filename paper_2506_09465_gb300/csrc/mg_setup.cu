@@ -212,7 +212,8 @@ iugkp_status build_multigrid(Ctx* c, const std::vector<double>& diag, const std:
       if (nx <= FD_MAX_N && ny <= FD_MAX_N &&
           separable_parts(in, kap.data() + in.cell_off, cvsum, diag.data() + in.cell_off, cx.data() + in.cell_off,
                           cy.data() + in.cell_off, part)) {
-        m.direct = 1;
+        // 2: every operand in shared memory (small axes), 1: tiles through L2
+        m.direct = (nx <= fd_small_max_n() && ny <= fd_small_max_n()) ? 2 : 1;
         m.fnx = nx;
         m.fny = ny;
         std::vector<double> lam, Q;
@@ -321,7 +322,10 @@ iugkp_status build_multigrid(Ctx* c, const std::vector<double>& diag, const std:
   if ((s = up(&c->d_mg_x, zeros)) != IUGKP_OK) return s;
   if ((s = up(&c->d_mg_t, zeros)) != IUGKP_OK) return s;
   if ((s = up(&c->d_mg_r, zeros)) != IUGKP_OK) return s;
-  const cudaError_t e = configure_mgpcg(c, mg_solo_smem_bytes(mgs));
+  size_t smem = mg_solo_smem_bytes(mgs);
+  for (const InstMG& m : mgs)
+    if (m.direct == 2) smem = std::max(smem, fd_small_smem_bytes());
+  const cudaError_t e = configure_mgpcg(c, smem);
   if (e != cudaSuccess) return fail(c, IUGKP_ECUDA, std::string("multigrid kernel set-up: ") + cudaGetErrorString(e));
   return IUGKP_OK;
 }

@@ -482,6 +482,167 @@ __device__ int fd_solve(const MGArgs& A, const InstMG& m, cg::cluster_group& cl,
   return -1;
 }
 
+// The same solve for nx, ny <= FD_SMALL_N with every operand in shared memory: Qx (rows
+// padded to FD_SMALL_N + 1 words, so that both Qx and its transpose are read without bank
+// conflicts), this CTA's rows and columns of Qy, and the full ny x nx right operand of the
+// products that need every row (S, then T2), gathered from the cluster's CTAs through
+// distributed shared memory. Each CTA keeps its rows of S, T1 and T2 in its own memory.
+constexpr int FD_SMALL_N = 128;
+constexpr int FD_SMALL_R = 16;  // rows per CTA (ny <= FD_SMALL_R * cluster size)
+constexpr int FDS_QX = 0;                                                   // [N][N + 1]
+constexpr int FDS_QYC = FDS_QX + FD_SMALL_N * (FD_SMALL_N + 1);             // [R][N]: Qy(k, j0 + r)
+constexpr int FDS_QYR = FDS_QYC + FD_SMALL_R * FD_SMALL_N;                  // [R][N]: Qy(j0 + r, k)
+constexpr int FDS_FULL = FDS_QYR + FD_SMALL_R * FD_SMALL_N;                 // [N][N]
+constexpr int FDS_S = FDS_FULL + FD_SMALL_N * FD_SMALL_N;                   // [R][N] rows of S
+constexpr int FDS_T2 = FDS_S + FD_SMALL_R * FD_SMALL_N;                     // [R][N] rows of T2
+constexpr int FDS_T1 = FDS_T2 + FD_SMALL_R * FD_SMALL_N;                    // [R][N] rows of T1
+constexpr int FDS_LX = FDS_T1 + FD_SMALL_R * FD_SMALL_N;                    // [N]
+constexpr int FDS_LY = FDS_LX + FD_SMALL_N;                                 // [R]
+constexpr int FDS_FLOATS = FDS_LY + FD_SMALL_R;
+constexpr size_t FD_SMALL_SMEM = (size_t)FDS_FLOATS * sizeof(float);
+
+// acc[q] = sum over k < K4 of L[(tg + 4 q) * N + k] R(k), for the four rows of this thread
+// (L rows N words apart, 16-byte aligned, zero beyond the true K).
+template <class FR>
+__device__ __forceinline__ void fds_rows4(const float* L, int tg, int K4, FR R, float (&acc)[4]) {
+  acc[0] = acc[1] = acc[2] = acc[3] = 0.f;
+  for (int k = 0; k < K4; k += 4) {
+    const float r0 = R(k), r1 = R(k + 1), r2 = R(k + 2), r3 = R(k + 3);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const float4 l = *reinterpret_cast<const float4*>(L + (tg + 4 * q) * FD_SMALL_N + k);
+      acc[q] = fmaf(l.x, r0, fmaf(l.y, r1, fmaf(l.z, r2, fmaf(l.w, r3, acc[q]))));
+    }
+  }
+}
+
+// full (rows < ny) <- every CTA's rows of strip, through distributed shared memory.
+template <int NT, int CS>
+__device__ __forceinline__ void fds_gather(cg::cluster_group& cl, float* full, float* strip, int ny, int rows) {
+  const int n4 = ny * (FD_SMALL_N / 4);
+  for (int e = threadIdx.x; e < n4; e += NT) {
+    const int k = e / (FD_SMALL_N / 4), c4 = e - k * (FD_SMALL_N / 4);
+    const int q = k / rows;
+    const float4* src = reinterpret_cast<const float4*>(cl.map_shared_rank(strip, q) + (k - q * rows) * FD_SMALL_N);
+    reinterpret_cast<float4*>(full + k * FD_SMALL_N)[c4] = src[c4];
+  }
+}
+
+template <int NT, int CS>
+__device__ int fd_solve_small(const MGArgs& A, const InstMG& m, cg::cluster_group& cl, int rank,
+                              ClusterRed<NT, CS>& red, double* sh, float* smem) {
+  static_assert(NT == 4 * FD_SMALL_N, "one column and four rows per thread");
+  static_assert(FD_SMALL_R * CS >= FD_SMALL_N, "rows per CTA");
+  const int nx = m.fnx, ny = m.fny;
+  const long long off = m.cell_off, n = m.nc[0];
+  const long long sy = m.n[0][0];
+  const int rows = (ny + CS - 1) / CS, j0 = min(ny, rank * rows), j1 = min(ny, j0 + rows);
+  const long long lo = (long long)j0 * nx, hi = (long long)j1 * nx;  // this CTA's cells
+  const int tc = threadIdx.x % FD_SMALL_N, tg = threadIdx.x / FD_SMALL_N;
+  const int kx4 = (nx + 3) & ~3, ky4 = (ny + 3) & ~3;
+  float* qx = smem + FDS_QX;
+  float* qyc = smem + FDS_QYC;
+  float* qyr = smem + FDS_QYR;
+  float* full = smem + FDS_FULL;
+  float* sS = smem + FDS_S;
+  float* sT2 = smem + FDS_T2;
+  float* sT1 = smem + FDS_T1;
+  float* slx = smem + FDS_LX;
+  float* sly = smem + FDS_LY;
+  {
+    // operands, zero outside the true sizes (the products run over multiples of 4 terms)
+    const float* Qx = A.fq + m.qx_off;
+    const float* Qy = A.fq + m.qy_off;
+    for (int e = threadIdx.x; e < FD_SMALL_N * (FD_SMALL_N + 1); e += NT) {
+      const int k = e / (FD_SMALL_N + 1), i = e - k * (FD_SMALL_N + 1);
+      qx[e] = (k < nx && i < nx) ? __ldg(&Qx[(long long)k * nx + i]) : 0.f;
+    }
+    for (int e = threadIdx.x; e < FD_SMALL_R * FD_SMALL_N; e += NT) {
+      const int r = e / FD_SMALL_N, k = e - r * FD_SMALL_N, j = j0 + r;
+      const bool in = j < j1 && k < ny;
+      qyc[e] = in ? __ldg(&Qy[(long long)k * ny + j]) : 0.f;
+      qyr[e] = in ? __ldg(&Qy[(long long)j * ny + k]) : 0.f;
+      sS[e] = 0.f;
+      sT2[e] = 0.f;
+      sT1[e] = 0.f;
+    }
+    for (int e = threadIdx.x; e < FD_SMALL_N * FD_SMALL_N; e += NT) full[e] = 0.f;
+    for (int i = threadIdx.x; i < FD_SMALL_N; i += NT) slx[i] = i < nx ? A.flam[m.lx_off + i] : 1.f;
+    for (int r = threadIdx.x; r < FD_SMALL_R; r += NT) sly[r] = j0 + r < j1 ? A.flam[m.ly_off + j0 + r] : 1.f;
+  }
+  double v[4];
+  v[0] = 0.0;
+  for (long long c = lo + threadIdx.x; c < hi; c += NT) {
+    const double b = A.rhs[off + c];
+    A.X[off + c] = 0.0;
+    A.Z[off + c] = b;  // FP64 residual
+    v[0] += b * b;
+  }
+  red.sum(cl, v, 1, sh);  // also orders the operand set-up before first use
+  const double bb = v[0];
+  if (bb == 0.0) return 0;
+  const double tol2 = A.rtol * A.rtol * bb;
+  double rr = bb;
+  float acc[4];
+  for (int pass = 1; pass <= MG32_PASSES_FD && pass <= A.maxit; ++pass) {
+    const double rn = sqrt(rr), sc = 1.0 / rn;
+    for (long long c = lo + threadIdx.x; c < hi; c += NT) {
+      const int r = (int)(c / nx), i = (int)(c - (long long)r * nx);
+      sS[(r - j0) * FD_SMALL_N + i] = (float)(__ldcg(&A.Z[off + c]) * sc);
+    }
+    cl.sync();
+    fds_gather<NT, CS>(cl, full, sS, ny, rows);
+    __syncthreads();
+    // T1 = Qy^T S (this CTA's rows), then T2 = T1 Qx ./ (ly_j + lx_i)
+    fds_rows4(qyc, tg, ky4, [&](int k) { return full[k * FD_SMALL_N + tc]; }, acc);
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+      if (tc < nx) sT1[(tg + 4 * q) * FD_SMALL_N + tc] = acc[q];
+    __syncthreads();
+    fds_rows4(sT1, tg, kx4, [&](int k) { return qx[k * (FD_SMALL_N + 1) + tc]; }, acc);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int r = tg + 4 * q;
+      if (tc < nx && j0 + r < j1) sT2[r * FD_SMALL_N + tc] = acc[q] / (sly[r] + slx[tc]);
+    }
+    cl.sync();
+    fds_gather<NT, CS>(cl, full, sT2, ny, rows);
+    __syncthreads();
+    // T1 = Qy T2, then the correction T1 Qx^T added to the FP64 solution (scaled back)
+    fds_rows4(qyr, tg, ky4, [&](int k) { return full[k * FD_SMALL_N + tc]; }, acc);
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+      if (tc < nx) sT1[(tg + 4 * q) * FD_SMALL_N + tc] = acc[q];
+    __syncthreads();
+    fds_rows4(sT1, tg, kx4, [&](int k) { return qx[tc * (FD_SMALL_N + 1) + k]; }, acc);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int j = j0 + tg + 4 * q;
+      if (tc < nx && j < j1) A.X[off + (long long)j * nx + tc] += (double)acc[q] * rn;
+    }
+    cl.sync();
+    // FP64 residual of the FP64 solution
+    v[0] = 0.0;
+    for (long long c = lo + threadIdx.x; c < hi; c += NT) {
+      const long long g = off + c;
+      double q = A.diag[g] * __ldcg(&A.X[g]);
+      if (c + 1 < n) q -= A.cx[g] * __ldcg(&A.X[g + 1]);
+      if (c >= 1) q -= A.cx[g - 1] * __ldcg(&A.X[g - 1]);
+      if (m.dim >= 2) {
+        if (c + sy < n) q -= A.cy[g] * __ldcg(&A.X[g + sy]);
+        if (c >= sy) q -= A.cy[g - sy] * __ldcg(&A.X[g - sy]);
+      }
+      const double r = A.rhs[g] - q;
+      A.Z[g] = r;
+      v[0] += r * r;
+    }
+    red.sum(cl, v, 1, sh);  // also orders the residual's writes before the next pass
+    rr = v[0];
+    if (rr <= tol2) return pass;
+  }
+  return -1;
+}
+
 template <int NT, int CS>
 __global__ void __launch_bounds__(NT) mgpcg_kernel(MGArgs A) {
   __shared__ double sh[4 * 32];
@@ -496,8 +657,10 @@ __global__ void __launch_bounds__(NT) mgpcg_kernel(MGArgs A) {
   const long long sy = m.n[0][0], sz = (long long)m.n[0][0] * m.n[0][1];
   ClusterRed<NT, CS> red{slot, 0};
   if (m.direct) {
-    const int passes = fd_solve<NT, CS>(A, m, cl, rank, red, sh);
+    const int passes = m.direct == 2 ? fd_solve_small<NT, CS>(A, m, cl, rank, red, sh, mg_smem)
+                                     : fd_solve<NT, CS>(A, m, cl, rank, red, sh);
     if (rank == 0 && threadIdx.x == 0) A.iters_out[k] = passes;
+    cl.sync();  // no CTA leaves while another may still read its shared memory
     return;
   }
   double v[4];
@@ -513,6 +676,7 @@ __global__ void __launch_bounds__(NT) mgpcg_kernel(MGArgs A) {
   const double bb = v[0];
   if (bb == 0.0) {
     if (rank == 0 && threadIdx.x == 0) A.iters_out[k] = 0;
+    cl.sync();
     return;
   }
   const double tol2 = A.rtol * A.rtol * bb;
@@ -578,6 +742,7 @@ __global__ void __launch_bounds__(NT) mgpcg_kernel(MGArgs A) {
     cl.sync();
   }
   if (rank == 0 && threadIdx.x == 0) A.iters_out[k] = done ? it : -1;
+  cl.sync();
 }
 
 // The same V-cycle for the FP32 iterates of mgpcg32_kernel: the finest level's right-hand
@@ -664,8 +829,10 @@ __global__ void __launch_bounds__(NT, 1) mgpcg32_kernel(MGArgs A, float* V32) {
   const float *dg = A.ldiag + m.off[0], *cx = A.lcx + m.off[0], *cy = A.lcy + m.off[0], *cz = A.lcz + m.off[0];
   ClusterRed<NT, CS> red{slot, 0};
   if (m.direct) {
-    const int passes = fd_solve<NT, CS>(A, m, cl, rank, red, sh);
+    const int passes = m.direct == 2 ? fd_solve_small<NT, CS>(A, m, cl, rank, red, sh, mg_smem)
+                                     : fd_solve<NT, CS>(A, m, cl, rank, red, sh);
     if (rank == 0 && threadIdx.x == 0) A.iters_out[k] = passes;
+    cl.sync();  // no CTA leaves while another may still read its shared memory
     return;
   }
   double v[4];
@@ -681,6 +848,7 @@ __global__ void __launch_bounds__(NT, 1) mgpcg32_kernel(MGArgs A, float* V32) {
   const double bb = v[0];
   if (bb == 0.0) {
     if (rank == 0 && threadIdx.x == 0) A.iters_out[k] = 0;
+    cl.sync();
     return;
   }
   const double tol2 = A.rtol * A.rtol * bb;
@@ -760,6 +928,7 @@ __global__ void __launch_bounds__(NT, 1) mgpcg32_kernel(MGArgs A, float* V32) {
     }
   }
   if (rank == 0 && threadIdx.x == 0) A.iters_out[k] = done ? it : -1;
+  cl.sync();  // no CTA leaves while another may still read its shared memory
 }
 
 // Tolerances from here up run the FP32 iterates.
@@ -778,6 +947,9 @@ size_t mg_solo_smem_bytes(const std::vector<InstMG>& h_mg) {
   }
   return best;
 }
+
+size_t fd_small_smem_bytes() { return FD_SMALL_SMEM; }
+int fd_small_max_n() { return FD_SMALL_N; }
 
 cudaError_t configure_mgpcg(Ctx* c, size_t smem) {
   c->mg_smem_bytes = smem;
