@@ -153,7 +153,8 @@ __global__ void __launch_bounds__(128) adjoint_replay_kernel(SweepArgs A, const 
     const InstDesc& in = A.inst[G.inst];
     const unsigned local = pid - (unsigned)G.first_particle;
     const int q = (int)(local / (unsigned)G.n_emitters);
-    const int e0 = (int)(local - (unsigned)q * (unsigned)G.n_emitters);
+    int e0 = (int)(local - (unsigned)q * (unsigned)G.n_emitters);
+    if (G.perm_off >= 0) e0 = A.perm[G.perm_off + e0];  // the staged visiting order
     Walk<double, DIM> wk;
     Stream st;
     double coefp;

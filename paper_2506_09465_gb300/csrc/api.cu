@@ -125,7 +125,7 @@ iugkp_status upload(Ctx* c, T** p, const std::vector<T>& h) {
 }
 
 void free_all(Ctx* c) {
-  void* ptrs[] = {c->d_vtm32, c->d_inst, c->d_groups_all, c->d_groups_fwd, c->d_coef, c->d_ratio64, c->d_ratio32, c->d_ratio_nb32, c->d_taumaj,
+  void* ptrs[] = {c->d_vtm32, c->d_perm, c->d_inst, c->d_groups_all, c->d_groups_fwd, c->d_coef, c->d_ratio64, c->d_ratio32, c->d_ratio_nb32, c->d_taumaj,
                   c->d_v, c->d_wcoef, c->d_wallT, c->d_srcshift, c->d_source, c->d_m, c->d_Vm, c->d_invVm, c->d_VC,
                   c->d_theta, c->d_theta_m, c->d_diag, c->d_cx, c->d_cy, c->d_cz, c->d_pcg, c->d_work, c->d_T2,
                   c->d_R, c->d_W, c->d_F, c->d_wall, c->d_red, c->d_counters, c->d_work_counter, c->d_err,
@@ -210,6 +210,46 @@ void staged_tables(const Ctx* c, const std::vector<Group>& groups, std::vector<l
     prefix[k] = total;
     total += cost[k];
   }
+}
+
+// Visiting order of each group's emitters in the staged sweep: stable-sorted by the class
+// floor(2 log2(tau / tau_maj)) of the emitter's cell (a wall face: the cell behind it), from
+// the expected number of candidates per real collision, so that a warp's lanes (consecutive
+// emitters) walk chains of similar length. Groups whose emitters share one class keep the
+// emitter order (perm_off = -1). Draws are keyed by (emitter, particle): the order changes
+// which lane traces a particle, not the particle. Sets perm_off of h_groups_all; returns the
+// concatenated orders (one entry at least).
+std::vector<int> emitter_orders(Ctx* c, const std::vector<float>& r32) {
+  std::vector<int> perm;
+  for (Group& g : c->h_groups_all) {
+    g.perm_off = -1;
+    const InstDesc& in = c->h_inst[g.inst];
+    const float* r = r32.data() + in.bc_off + (long long)g.band * in.ncells;
+    std::vector<int> cls(g.n_emitters);
+    for (int e = 0; e < g.n_emitters; ++e) {
+      long long cell = e;
+      if (g.kind > 0) {
+        const int wl = g.kind - 1, a = wl >> 1, side = wl & 1;
+        const int o1 = (a + 1) % 3, o2 = (a + 2) % 3;
+        int idx[3];
+        idx[a] = side ? in.n[a] - 1 : 0;
+        idx[o1] = e % in.n[o1];
+        idx[o2] = e / in.n[o1];
+        cell = idx[0] + (long long)in.n[0] * (idx[1] + (long long)in.n[1] * idx[2]);
+      }
+      // r = tau_maj / tau <= 1 is the acceptance probability: 1 / r candidates per real one
+      cls[e] = (int)std::floor(-2.0 * std::log2(std::min(1.0, std::max(1e-30, (double)r[cell]))));
+    }
+    if (std::all_of(cls.begin(), cls.end(), [&](int x) { return x == cls[0]; })) continue;
+    if ((long long)perm.size() + g.n_emitters > 0x7fffffffll) continue;
+    std::vector<int> order(g.n_emitters);
+    for (int e = 0; e < g.n_emitters; ++e) order[e] = e;
+    std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return cls[x] < cls[y]; });
+    g.perm_off = (int)perm.size();
+    perm.insert(perm.end(), order.begin(), order.end());
+  }
+  if (perm.empty()) perm.push_back(0);
+  return perm;
 }
 
 // Per-face wall temperatures from the per-wall values (every face of a wall alike).
@@ -620,6 +660,10 @@ iugkp_status iugkp_create_batch(int n, const iugkp_grid* g, const double* const*
   iugkp_status s;
 #define UP(ptr, vec)                                 \
   if ((s = upload(c, &(ptr), (vec))) != IUGKP_OK) return bail(s);
+  {
+    std::vector<int> perm = emitter_orders(c, r32);
+    UP(c->d_perm, perm);
+  }
   UP(c->d_inst, c->h_inst);
   UP(c->d_groups_all, c->h_groups_all);
   UP(c->d_coef, coef);
@@ -808,6 +852,7 @@ SweepArgs base_args(Ctx* c) {
   a.ratio32 = c->d_ratio32;
   a.ratio_nb32 = c->d_ratio_nb32;
   a.all_real = c->d_all_real;
+  a.perm = c->d_perm;
   a.taumaj = c->d_taumaj;
   a.vtm32 = c->d_vtm32;
   a.v = c->d_v;

@@ -35,6 +35,7 @@ struct SweepArgs {
   const float* ratio32;
   const float* ratio_nb32; // [bc] largest ratio32 over the cell and its neighbours
   const int* all_real;     // [inst * nb] 1 where tau = tau_maj in every cell (every candidate real)
+  const int* perm;         // staged visiting order of the emitters of groups with perm_off >= 0
   const double* taumaj;    // [inst * nb] majorant tau per instance and band
   const double* v;         // [nb] group speed
   const float* vtm32;      // [inst * nb] v_b tau_maj in FP32
@@ -87,6 +88,7 @@ struct Ctx {
   double* d_ratio64 = nullptr;
   float* d_ratio32 = nullptr;
   float* d_ratio_nb32 = nullptr; // [nb * cells] largest FP32 ratio over each cell's neighbourhood
+  int* d_perm = nullptr;         // emitter visiting orders of the groups (Group::perm_off)
   int* d_all_real = nullptr;     // [inst * nb] tau = tau_maj in every cell of the band
   bool all_real_all = false;     // ... in every instance and band
   double* d_taumaj = nullptr;

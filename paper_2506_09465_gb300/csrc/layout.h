@@ -30,12 +30,15 @@ struct InstDesc {
 // A run of emitters sharing (instance, band, kind). kind 0 = the instance's cells;
 // kind 1 + w = the boundary faces of wall w. Particles of the run are numbered
 // emitter-major: local = e * per_emitter + q.
+// The staged sweep visits them q-major in the order perm[perm_off + r], r = 0 .. n_emitters-1,
+// of emitter ranks (emitters sorted by their cell's majorant ratio class, so that the lanes of
+// a warp walk candidate chains of similar length); perm_off = -1: emitter order.
 struct Group {
   long long first_particle;
   int inst, band, kind;
   int n_emitters;
   int per_emitter;
-  int pad0;
+  int perm_off;
 };
 
 // Counter slots (u64) written by a sweep.

@@ -249,7 +249,8 @@ __global__ void __launch_bounds__(256) replay_kernel(SweepArgs A, StagedArgs S) 
       const InstDesc& in = A.inst[G.inst];
       const unsigned local = ent.x - (unsigned)G.first_particle;
       const int q = (int)(local / (unsigned)G.n_emitters);
-      const int e = (int)(local - (unsigned)q * (unsigned)G.n_emitters);
+      int e = (int)(local - (unsigned)q * (unsigned)G.n_emitters);
+      if (G.perm_off >= 0) e = A.perm[G.perm_off + e];  // the staged visiting order
       int gj;
       Walk<double, DIM> wk;
       Stream st;

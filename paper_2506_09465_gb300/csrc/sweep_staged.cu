@@ -256,6 +256,7 @@ __global__ void group_wmax_kernel(SweepArgs A, unsigned long long* wmax_bits) {
 struct EmitCache {
   unsigned g_first, g_end;  // forward particle range of the cached group
   int g_idx, g_ne, g_kind, g_band;
+  int g_perm;               // perm_off of the group
   unsigned g_mag;           // division magic of n_emitters
   int e;
   double w;
@@ -280,17 +281,20 @@ __device__ __forceinline__ bool staged_emit(const SweepArgs& A, const StagedArgs
     ec.g_kind = G.kind;
     ec.g_band = G.band;
     ec.g_mag = S.group_mag[gi];
+    ec.g_perm = G.perm_off;
     ec.e = -1;
   }
   band = ec.g_band;
   const int b = ec.g_band;
   // The staged sweep visits a group's particles q-major (particle q of every emitter,
   // then q + 1), so the lanes of a warp start in different cells: their face and deposit
-  // tallies rarely hit the same address at the same time. Draws are keyed by (emitter,
-  // particle), so the order changes nothing else.
+  // tallies rarely hit the same address at the same time; within a q the emitters come in
+  // the group's visiting order. Draws are keyed by (emitter, particle), so the order changes
+  // nothing else.
   const unsigned local = pid - ec.g_first;
   const int q = (int)udiv(local, (unsigned)ec.g_ne, ec.g_mag);
-  const int e = (int)(local - (unsigned)q * (unsigned)ec.g_ne);
+  int e = (int)(local - (unsigned)q * (unsigned)ec.g_ne);
+  if (ec.g_perm >= 0) e = A.perm[ec.g_perm + e];
   const int n0 = in.n[0], n1 = in.n[1], n2 = in.n[2];
   const int kind = ec.g_kind;
   float xi0 = 0.5f, xi1 = 0.5f, xi2 = 0.5f, sx = 0.f, sy = 0.f, sz = 0.f;
