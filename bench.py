@@ -24,8 +24,10 @@ sys.path.insert(0, ROOT)
 
 METRIC = "cell-crossings/s and time-to-steady (res 1e-8) vs plain FP64 sweep, same GPU"
 KNS = (0.01, 0.1, 1.0, 10.0)
-SWEEP_DRAM_BYTES = 3.21e6  # ncu dram bytes per launch of the staged sweep on this workload
-SWEEP_ISSUE_UTIL = 0.790   # ncu sm__issue_active of the same launch
+# From one ncu capture of the current sweep kernel on this workload (the command and the
+# figures are in profiles/sweep_cavity128_4kn.md); retaken whenever the kernel changes.
+SWEEP_DRAM_BYTES = 3.25e6  # dram__bytes_read.sum + dram__bytes_write.sum per launch
+SWEEP_ISSUE_UTIL = 0.780   # smsp__issue_active of the same launch
 NGRID = 128
 NPART = 1024
 
