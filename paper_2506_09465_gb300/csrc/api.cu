@@ -125,7 +125,7 @@ iugkp_status upload(Ctx* c, T** p, const std::vector<T>& h) {
 }
 
 void free_all(Ctx* c) {
-  void* ptrs[] = {c->d_vtm32, c->d_perm, c->d_inst, c->d_groups_all, c->d_groups_fwd, c->d_coef, c->d_ratio64, c->d_ratio32, c->d_ratio_nb32, c->d_taumaj,
+  void* ptrs[] = {c->d_vtm32, c->d_perm, c->d_wmax_bpre, c->d_inst, c->d_groups_all, c->d_groups_fwd, c->d_coef, c->d_ratio64, c->d_ratio32, c->d_ratio_nb32, c->d_taumaj,
                   c->d_v, c->d_wcoef, c->d_wallT, c->d_srcshift, c->d_source, c->d_m, c->d_Vm, c->d_invVm, c->d_VC,
                   c->d_theta, c->d_theta_m, c->d_diag, c->d_cx, c->d_cy, c->d_cz, c->d_pcg, c->d_work, c->d_T2,
                   c->d_R, c->d_W, c->d_F, c->d_wall, c->d_red, c->d_counters, c->d_work_counter, c->d_err,
@@ -293,6 +293,15 @@ iugkp_status rebuild_forward_groups(Ctx* c) {
   c->d_groups_fwd = nullptr;
   iugkp_status s = upload(c, &c->d_groups_fwd, c->h_groups_fwd);
   if (s != IUGKP_OK) return s;
+  {
+    // w_max pre-pass: one block per WMAX_CHUNK emitters of each group (at least one)
+    std::vector<int> bpre(1, 0);
+    for (const Group& g : c->h_groups_fwd) bpre.push_back(bpre.back() + (int)((g.n_emitters + WMAX_CHUNK - 1) / WMAX_CHUNK));
+    c->wmax_blocks = bpre.back();
+    if (c->d_wmax_bpre) cudaFree(c->d_wmax_bpre);
+    c->d_wmax_bpre = nullptr;
+    if ((s = upload(c, &c->d_wmax_bpre, bpre)) != IUGKP_OK) return s;
+  }
   // Staged sweep: each instance's forward particles are contiguous (groups are ordered
   // by instance); blocks start on instances in proportion to the estimated cost.
   std::vector<long long> beg, end;

@@ -357,46 +357,88 @@ __device__ void vcycle(const MGArgs& A, const InstMG& m, cg::cluster_group& cl, 
 // barrier. The solve runs inside FP64 iterative refinement: the solution is accumulated in
 // FP64 and its residual S - A X is formed with the FP64 operator, until it meets rtol.
 
-// Tiles of the dense products: FD_TR rows x FD_TI columns of the output per step, FD_TK terms
-// of the sum staged in shared memory at a time (512 threads: each one column, four rows).
-constexpr int FD_TI = 128, FD_TK = 32, FD_TR = 16;
+// Tiles of the dense products: FDT_BM rows x FDT_BN columns of the output per tile (each of
+// the 512 threads 4 rows x 4 columns, from one float4 of each operand per term), FDT_BK terms
+// per stage; the next stage's operands are loaded into registers while the current stage is
+// multiplied from shared memory. Shared rows are padded by 4 words (16-byte aligned float4
+// reads, at most 2-way conflicts on the transposing stores).
+constexpr int FDT_BM = 64, FDT_BN = 128, FDT_BK = 16;
+constexpr int FDT_AS = FDT_BM + 4, FDT_BS = FDT_BN + 4;
 
-// out(j, i) for rows j in [j0, j1) and columns i < N of sum_k L(j, k) R(k, i), with L and R
-// tiles staged in shared memory (R tile loads coalesce along i).
-template <int NT, class FL, class FR, class FE>
-__device__ __forceinline__ void rows_product(int j0, int j1, int N, int K, FL L, FR R, FE out,
-                                             float (*sl)[FD_TK + 1], float (*sr)[FD_TI]) {
-  static_assert(NT == 512, "four rows per thread: 512 threads = 4 groups of FD_TI columns");
-  const int tc = threadIdx.x % FD_TI, tg = threadIdx.x / FD_TI;
-  for (int jt = j0; jt < j1; jt += FD_TR) {
-    for (int it = 0; it < N; it += FD_TI) {
-      float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
-      for (int kt = 0; kt < K; kt += FD_TK) {
-        {
-          const int r = threadIdx.x / FD_TK, k = threadIdx.x % FD_TK;
-          sl[r][k] = (jt + r < j1 && kt + k < K) ? L(jt + r, kt + k) : 0.f;
+// out(j, i) for rows j in [j0, j1) and columns i < N of sum over k < K of L(j, k) R(k, i).
+// L_KC: L is contiguous along k (else along j); R_IC: R is contiguous along i (else along
+// k); the tile loads run along the contiguous index.
+template <int NT, bool L_KC, bool R_IC, class FL, class FR, class FE>
+__device__ __forceinline__ void tile_product(int j0, int j1, int N, int K, FL L, FR R, FE out, float* As,
+                                             float* Bs) {
+  static_assert(NT == 512, "4 x 4 outputs per thread: 512 threads = 16 x 32 groups");
+  constexpr int NA = FDT_BK * FDT_BM / NT, NB = FDT_BK * FDT_BN / NT;  // loads per thread and stage
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  for (int jt = j0; jt < j1; jt += FDT_BM) {
+    for (int it = 0; it < N; it += FDT_BN) {
+      float acc[4][4];
+#pragma unroll
+      for (int r = 0; r < 4; ++r)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) acc[r][c] = 0.f;
+      float ra[NA], rb[NB];
+      auto load = [&](int kt) {
+#pragma unroll
+        for (int q = 0; q < NA; ++q) {
+          const int e = threadIdx.x + q * NT;
+          const int kk = L_KC ? e % FDT_BK : e / FDT_BM, jj = L_KC ? e / FDT_BK : e % FDT_BM;
+          ra[q] = (jt + jj < j1 && kt + kk < K) ? L(jt + jj, kt + kk) : 0.f;
         }
-        for (int q = threadIdx.x; q < FD_TK * FD_TI; q += NT) {
-          const int k = q / FD_TI, i = q - k * FD_TI;
-          sr[k][i] = (kt + k < K && it + i < N) ? R(kt + k, it + i) : 0.f;
+#pragma unroll
+        for (int q = 0; q < NB; ++q) {
+          const int e = threadIdx.x + q * NT;
+          const int kk = R_IC ? e / FDT_BN : e % FDT_BK, ii = R_IC ? e % FDT_BN : e / FDT_BK;
+          rb[q] = (kt + kk < K && it + ii < N) ? R(kt + kk, it + ii) : 0.f;
         }
+      };
+      auto store = [&](int buf) {
+#pragma unroll
+        for (int q = 0; q < NA; ++q) {
+          const int e = threadIdx.x + q * NT;
+          const int kk = L_KC ? e % FDT_BK : e / FDT_BM, jj = L_KC ? e / FDT_BK : e % FDT_BM;
+          As[(buf * FDT_BK + kk) * FDT_AS + jj] = ra[q];
+        }
+#pragma unroll
+        for (int q = 0; q < NB; ++q) {
+          const int e = threadIdx.x + q * NT;
+          const int kk = R_IC ? e / FDT_BN : e % FDT_BK, ii = R_IC ? e % FDT_BN : e / FDT_BK;
+          Bs[(buf * FDT_BK + kk) * FDT_BS + ii] = rb[q];
+        }
+      };
+      load(0);
+      store(0);
+      __syncthreads();
+      int buf = 0;
+      for (int kt = 0; kt < K; kt += FDT_BK) {
+        const bool more = kt + FDT_BK < K;
+        if (more) load(kt + FDT_BK);
+#pragma unroll
+        for (int k = 0; k < FDT_BK; ++k) {
+          const float4 a = *reinterpret_cast<const float4*>(&As[(buf * FDT_BK + k) * FDT_AS + 4 * ty]);
+          const float4 b = *reinterpret_cast<const float4*>(&Bs[(buf * FDT_BK + k) * FDT_BS + 4 * tx]);
+          const float av[4] = {a.x, a.y, a.z, a.w}, bv[4] = {b.x, b.y, b.z, b.w};
+#pragma unroll
+          for (int r = 0; r < 4; ++r)
+#pragma unroll
+            for (int c = 0; c < 4; ++c) acc[r][c] = fmaf(av[r], bv[c], acc[r][c]);
+        }
+        if (more) store(buf ^ 1);
         __syncthreads();
-#pragma unroll 8
-        for (int k = 0; k < FD_TK; ++k) {
-          const float r = sr[k][tc];
-          a0 = fmaf(sl[tg][k], r, a0);
-          a1 = fmaf(sl[tg + 4][k], r, a1);
-          a2 = fmaf(sl[tg + 8][k], r, a2);
-          a3 = fmaf(sl[tg + 12][k], r, a3);
-        }
-        __syncthreads();
+        buf ^= 1;
       }
-      const int i = it + tc;
-      if (i < N) {
-        if (jt + tg < j1) out(jt + tg, i, a0);
-        if (jt + tg + 4 < j1) out(jt + tg + 4, i, a1);
-        if (jt + tg + 8 < j1) out(jt + tg + 8, i, a2);
-        if (jt + tg + 12 < j1) out(jt + tg + 12, i, a3);
+#pragma unroll
+      for (int r = 0; r < 4; ++r) {
+        const int j = jt + 4 * ty + r;
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+          const int i = it + 4 * tx + c;
+          if (j < j1 && i < N) out(j, i, acc[r][c]);
+        }
       }
     }
   }
@@ -419,8 +461,8 @@ __device__ int fd_solve(const MGArgs& A, const InstMG& m, cg::cluster_group& cl,
   float* Sf = A.lt + m.off[0];  // scaled residual (FP32)
   float* T1 = A.lb + m.off[0];  // Qy^T S, then Qy T2
   float* T2 = A.lx + m.off[0];  // (Qy^T S Qx) ./ (ly + lx)
-  __shared__ float sl[FD_TR][FD_TK + 1];
-  __shared__ float sr[FD_TK][FD_TI];
+  __shared__ __align__(16) float As[2 * FDT_BK * FDT_AS];
+  __shared__ __align__(16) float Bs[2 * FDT_BK * FDT_BS];
   double v[4];
   v[0] = 0.0;
   for (long long c = lo + threadIdx.x; c < hi; c += NT) {
@@ -439,26 +481,26 @@ __device__ int fd_solve(const MGArgs& A, const InstMG& m, cg::cluster_group& cl,
     for (long long c = lo + threadIdx.x; c < hi; c += NT) Sf[c] = (float)(__ldcg(&A.Z[off + c]) * sc);
     cl.sync();
     // T1 = Qy^T S (rows j of this CTA), then T2 = T1 Qx ./ (ly_j + lx_i) (same rows)
-    rows_product<NT>(
+    tile_product<NT, false, true>(
         j0, j1, nx, ny, [&](int j, int k) { return __ldg(&Qy[(long long)k * ny + j]); },
         [&](int k, int i) { return __ldcg(&Sf[(long long)k * nx + i]); },
-        [&](int j, int i, float x) { T1[(long long)j * nx + i] = x; }, sl, sr);
+        [&](int j, int i, float x) { T1[(long long)j * nx + i] = x; }, As, Bs);
     __syncthreads();
-    rows_product<NT>(
+    tile_product<NT, true, true>(
         j0, j1, nx, nx, [&](int j, int k) { return __ldcg(&T1[(long long)j * nx + k]); },
         [&](int k, int i) { return __ldg(&Qx[(long long)k * nx + i]); },
-        [&](int j, int i, float x) { T2[(long long)j * nx + i] = x / (ly[j] + lx[i]); }, sl, sr);
+        [&](int j, int i, float x) { T2[(long long)j * nx + i] = x / (ly[j] + lx[i]); }, As, Bs);
     cl.sync();
     // T1 = Qy T2, then the correction T1 Qx^T added to the FP64 solution (scaled back)
-    rows_product<NT>(
+    tile_product<NT, true, true>(
         j0, j1, nx, ny, [&](int j, int k) { return __ldg(&Qy[(long long)j * ny + k]); },
         [&](int k, int i) { return __ldcg(&T2[(long long)k * nx + i]); },
-        [&](int j, int i, float x) { T1[(long long)j * nx + i] = x; }, sl, sr);
+        [&](int j, int i, float x) { T1[(long long)j * nx + i] = x; }, As, Bs);
     __syncthreads();
-    rows_product<NT>(
+    tile_product<NT, true, false>(
         j0, j1, nx, nx, [&](int j, int k) { return __ldcg(&T1[(long long)j * nx + k]); },
         [&](int k, int i) { return __ldg(&Qx[(long long)i * nx + k]); },
-        [&](int j, int i, float x) { A.X[off + (long long)j * nx + i] += (double)x * rn; }, sl, sr);
+        [&](int j, int i, float x) { A.X[off + (long long)j * nx + i] += (double)x * rn; }, As, Bs);
     cl.sync();
     // FP64 residual of the FP64 solution
     v[0] = 0.0;

@@ -184,8 +184,9 @@ __device__ __forceinline__ void run_particle(const SweepArgs& A, long long pid, 
 }
 
 // Deposit tallies of a replayed particle: W as w (the staged sweep scales it by tau_maj
-// afterwards), from candidate k_done on (the earlier ones were tallied by the staged sweep); R,
-// and the y-group balance DY for a y-group particle of a two-group instance.
+// afterwards, or sets it to tau_maj R in bands whose every candidate is real: all_real), from
+// candidate k_done on (the earlier ones were tallied by the staged sweep); R, and the y-group
+// balance DY for a y-group particle of a two-group instance.
 struct ReplayDeposits {
   const SweepArgs& A;
   const StagedArgs& S;
@@ -193,11 +194,12 @@ struct ReplayDeposits {
   double w;
   int k_done;
   bool ydy;
+  bool all_real;
   Counts& cnt;
   __device__ void candidate(int k, long long ci, int) {
     if (k < k_done) return;
     cnt.v[CNT_CANDIDATES] += 1;
-    if (A.W) atomicAdd(&A.W[ci], w);
+    if (A.W && !all_real) atomicAdd(&A.W[ci], w);
   }
   __device__ void real(long long ci, int cell) {
     cnt.v[CNT_REAL] += 1;
@@ -259,7 +261,8 @@ __global__ void __launch_bounds__(256) replay_kernel(SweepArgs A, StagedArgs S) 
         sg.init(wk, in);
         const bool two = DIM == 2 && A.F && S.window[G.inst].x == 0 && (long long)S.window[G.inst].y == in.nfaces;
         const bool yg = two && (ent.y & 1u);
-        ReplayDeposits pol{A, S, in, w, (int)(ent.y >> 1), yg, cnt};
+        ReplayDeposits pol{A, S, in, w, (int)(ent.y >> 1), yg,
+                           A.all_real[(long long)G.inst * A.nb + G.band] != 0, cnt};
         int fb[DIM];
         const int res = replay_candidates<DIM>(A, in, G.inst, G.band, wk, sg, st, fb, pol);
         if (res < 0) {

@@ -216,17 +216,28 @@ __device__ __forceinline__ int candidate_outcome(const SweepArgs& A, long long b
 
 }  // namespace
 
-// gridDim.y blocks per forward group (blockIdx.x): the largest |weight| of the group's
-// emitters, max-reduced into its instance's slot (non-negative doubles order like their bit
-// patterns). Several blocks per group spread the FP64 weight arithmetic over the SMs.
-__global__ void group_wmax_kernel(SweepArgs A, unsigned long long* wmax_bits) {
+// The largest |weight| of each forward group's emitters, max-reduced into its instance's slot
+// (non-negative doubles order like their bit patterns). Group g has blocks [bpre[g],
+// bpre[g + 1]) of the grid, about one per WMAX_CHUNK emitters, so the FP64 weight arithmetic
+// is spread over the SMs in proportion to the work.
+__global__ void group_wmax_kernel(SweepArgs A, const int* bpre, unsigned long long* wmax_bits) {
   __shared__ double sh[32];
-  const Group G = A.groups[blockIdx.x];
+  int gi = 0;
+  {
+    int hi = A.n_groups - 1;  // the last group whose first block is at or before this one
+    while (gi < hi) {
+      const int mid = (gi + hi + 1) >> 1;
+      if (bpre[mid] <= (int)blockIdx.x) gi = mid;
+      else hi = mid - 1;
+    }
+  }
+  const Group G = A.groups[gi];
+  const int by = (int)blockIdx.x - bpre[gi], ny = bpre[gi + 1] - bpre[gi];
   const InstDesc& in = A.inst[G.inst];
   double m = 0.0;
   if (G.kind == 0) {
     const long long base = in.bc_off + (long long)G.band * in.ncells;
-    for (int e = blockIdx.y * blockDim.x + threadIdx.x; e < in.ncells; e += gridDim.y * blockDim.x) {
+    for (int e = by * blockDim.x + threadIdx.x; e < in.ncells; e += ny * blockDim.x) {
       double Te = A.T[in.cell_off + e];
       if (A.srcshift) Te += A.srcshift[in.cell_off + e];
       const double w = A.coef[base + e] * Te;
@@ -237,7 +248,7 @@ __global__ void group_wmax_kernel(SweepArgs A, unsigned long long* wmax_bits) {
     const int wl = G.kind - 1;
     const double wc = A.wcoef[((long long)G.inst * A.nb + G.band) * 6 + wl];
     const double* tf = A.wallTf + in.bface_off + in.wface_off[wl];
-    for (int j = blockIdx.y * blockDim.x + threadIdx.x; j < G.n_emitters; j += gridDim.y * blockDim.x)
+    for (int j = by * blockDim.x + threadIdx.x; j < G.n_emitters; j += ny * blockDim.x)
       m = fmax(m, fabs(wc * tf[j]));
   }
 #pragma unroll
@@ -467,15 +478,27 @@ __device__ __forceinline__ void tally_k32(float2* p, double x) {
   if (lo != 0.f) atomicAdd(&p->y, lo);
 }
 
+// Instance holding entry j of a [band][cell] array: the last one whose bc_off is at or before j.
+__device__ __forceinline__ int bc_instance(const InstDesc* inst, int n_inst, long long j) {
+  int lo = 0, hi = n_inst - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (inst[mid].bc_off <= j) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+
 // The candidate estimator W = sum of w tau_maj over candidates (Sec. 3.2): the staged sweep
-// sums w per (band, cell) and multiplies by the instance's tau_maj of the band here.
-__global__ void scale_by_taumaj_kernel(const InstDesc* inst, int n_inst, int nb, const double* taumaj, double* W,
-                                       long long total) {
+// sums w per (band, cell) and multiplies by the instance's tau_maj of the band here; in a band
+// with tau = tau_maj in every cell every candidate is real, so there W = tau_maj R (the sweep
+// leaves W alone).
+__global__ void scale_by_taumaj_kernel(const InstDesc* inst, int n_inst, int nb, const double* taumaj,
+                                       const int* all_real, const double* R, double* W, long long total) {
   for (long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x; j < total; j += (long long)gridDim.x * blockDim.x) {
-    int k = 0;
-    while (k + 1 < n_inst && inst[k + 1].bc_off <= j) ++k;
-    const int b = (int)((j - inst[k].bc_off) / inst[k].ncells);
-    W[j] *= taumaj[(long long)k * nb + b];
+    const int k = bc_instance(inst, n_inst, j);
+    const long long kb = (long long)k * nb + (j - inst[k].bc_off) / inst[k].ncells;
+    W[j] = (all_real[kb] ? R[j] : W[j]) * taumaj[kb];
   }
 }
 
@@ -645,9 +668,10 @@ __global__ void __launch_bounds__(STAGED_NT, 1) sweep_staged_kernel(SweepArgs A,
           }
           cnt.v[CNT_CANDIDATES] += 1;
           ++kc;
-          // W collects w here; the sweep scales it by tau_maj afterwards (scale_by_taumaj)
-          if (!ADJ && K32 && S.W32) tally_k32(&S.W32[ci], w);
-          else if (!ADJ && !K32 && A.W) atomicAdd(&A.W[ci], w);
+          // W collects w here; the sweep scales it by tau_maj afterwards (scale_by_taumaj), and
+          // a band whose every candidate is real takes W = tau_maj R there instead
+          if (!ADJ && K32 && S.W32 && !all_real) tally_k32(&S.W32[ci], w);
+          else if (!ADJ && !K32 && A.W && !all_real) atomicAdd(&A.W[ci], w);
           if (oc == CAND_REAL) {
             cnt.v[CNT_REAL] += 1;
             if (ADJ) {
@@ -1134,8 +1158,10 @@ __global__ void __launch_bounds__(STAGED_NT, 1) sweep_sync_kernel(SweepArgs A, S
             }
             cnt.v[CNT_CANDIDATES] += 1;
             ++kc;
-            if (K32 && S.W32) tally_k32(&S.W32[ci], w);
-            else if (!K32 && A.W) atomicAdd(&A.W[ci], w);
+            if (!all_real) {  // else W = tau_maj R after the sweep
+              if (K32 && S.W32) tally_k32(&S.W32[ci], w);
+              else if (!K32 && A.W) atomicAdd(&A.W[ci], w);
+            }
             if (oc == CAND_REAL) {
               cnt.v[CNT_REAL] += 1;
               if (K32) tally_k32(&S.R32[ci], w);
@@ -1722,13 +1748,7 @@ cudaError_t launch_sweep_staged(const Ctx* c, const SweepArgs& a, cudaStream_t s
   if (e != cudaSuccess) return e;
   if ((e = cudaMemsetAsync(c->d_wmax, 0, c->n_inst * sizeof(double), s)) != cudaSuccess) return e;
   if ((e = cudaMemsetAsync(c->d_defer_n, 0, sizeof(unsigned), s)) != cudaSuccess) return e;
-  {
-    // about four emitters per thread, at most 64 blocks per group
-    long long most = 1;
-    for (const Group& g : c->h_groups_fwd) most = std::max<long long>(most, g.n_emitters);
-    const unsigned split = (unsigned)std::min<long long>(64, (most + 1023) / 1024);
-    group_wmax_kernel<<<dim3(a.n_groups, split), 256, 0, s>>>(a, c->d_wmax);
-  }
+  group_wmax_kernel<<<c->wmax_blocks, 256, 0, s>>>(a, c->d_wmax_bpre, c->d_wmax);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   const size_t smem = (size_t)c->staged_cap * sizeof(unsigned);
   const int blocks = c->sm_count * c->staged_blocks_per_sm;
@@ -1783,8 +1803,8 @@ cudaError_t launch_sweep_staged(const Ctx* c, const SweepArgs& a, cudaStream_t s
   }
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   if (a.W) {
-    scale_by_taumaj_kernel<<<c->sm_count * 4, 256, 0, s>>>(c->d_inst, c->n_inst, c->nb, c->d_taumaj, a.W,
-                                                          (long long)c->nb * c->total_cells);
+    scale_by_taumaj_kernel<<<c->sm_count * 4, 256, 0, s>>>(c->d_inst, c->n_inst, c->nb, c->d_taumaj, c->d_all_real,
+                                                          a.R, a.W, (long long)c->nb * c->total_cells);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
   if (a.F) {

@@ -112,7 +112,7 @@ def test_newton_step_matches_direct_solve(orc, dim):
 @pytest.mark.parametrize("rtol", [1e-3, 1e-5, 9.9e-6, 1e-11])
 @pytest.mark.parametrize("dim,n,uniform", [(1, (30,), False), (2, (14, 11), False), (2, (160, 128), False),
                                            (3, (6, 5, 4), False), (1, (70,), True), (2, (48, 40), True),
-                                           (2, (200, 7), True)])
+                                           (2, (200, 7), True), (2, (150, 260), True)])
 def test_correction_solve_meets_its_fp64_residual(orc, dim, n, uniform, rtol):
     # Separable operators (1D or 2D with uniform kappa) are solved by fast diagonalization;
     # the others by multigrid-preconditioned CG, with FP32 iterates from cg_rtol 1e-5 up (the
