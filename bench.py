@@ -146,6 +146,49 @@ def oracle_rate(n_particles: int, budget_s: float):
                 return crossings / dt, dt, crossings, sample
 
 
+def oracle_config_sweeps():
+    """The oracle's sweep rate on one instance of each of the other sweep workloads, at a
+    particle count small enough for a few seconds of one core (the rate is intensive), and the
+    time of one full sweep of the GPU workload at that rate (flights of the GPU sweep over the
+    oracle's flights/s), labelled extrapolated: the non-gray 256^2 square (80 band-branches,
+    sampled at 128 particles per cell of the 1024), one 32^3 box of the 3D box batch (16 of the
+    256 particles per cell; the batch holds 1.44 M cells) and the square of the adjoint batch
+    closest to 256^2 (40 band-branches, 48 of the 128 particles per cell; the batch holds
+    2.06 M cells)."""
+    import numpy as np
+    from oracle import oracle as O
+    from paper_2506_09465_gb300 import workloads as WL
+    out = {}
+    box = WL.box_batch(16)
+    adj = WL.nongray_batch(32, 64, 512, 20, 128)
+    sq = min(adj.instances, key=lambda i: abs(i.n[0] - 256))
+    cases = (("nongray_256x256_80bands", WL.nongray_square(256, 40, 1024), 128),
+             ("box32_of_box_batch_16", WL.Workload("box", box.C, box.v, [WL.two_material_box(32)],
+                                                   box.particles_per_cell, box.particles_per_wall_face), 16),
+             (f"square{sq.n[0]}_of_adjoint_batch", WL.Workload("sq", adj.C, adj.v, [sq], adj.particles_per_cell,
+                                                               adj.particles_per_wall_face), 48))
+    for name, wl, n_s in cases:
+        inst = wl.instances[0]
+        C = np.asarray(wl.C, dtype=np.float64)
+        v = np.asarray(wl.v, dtype=np.float64)
+        r = C * (1.0 / inst.tau).mean(axis=1)
+        nb = O.band_split(n_s, r) if len(C) > 1 else np.array([n_s])
+        nw = O.band_split(n_s, C * v) if len(C) > 1 else np.array([n_s])
+        p = O.Problem(inst.dim, inst.n, inst.L, C, v, inst.tau, inst.wall_T, nb, nw, source=inst.source, seed=0)
+        T = np.full(inst.ncells, 0.3)
+        t0 = time.perf_counter()
+        res = O.sweep(p, T, 0)
+        dt = time.perf_counter() - t0
+        fl, cr = float(res.counters[0]), float(res.counters[3])
+        full_flights = fl * wl.particles_per_cell / n_s  # the same instance at the GPU's particle count
+        out[name] = {"cells": int(inst.ncells), "band_branches": int(len(C)), "particles_per_cell_sample": n_s,
+                     "particles_per_cell_gpu": int(wl.particles_per_cell), "s_at_sample": dt,
+                     "flights_per_s": fl / dt, "crossings_per_s": cr / dt,
+                     "s_per_sweep_of_this_instance_extrapolated": full_flights / (fl / dt), "cores": 1,
+                     "extrapolated": True}
+    return out
+
+
 # the workload both arms report (the reference arm times a bounded sample of it)
 WORKLOAD = ("2D gray cavity 128x128 unit square, Kn {0.01,0.1,1,10} batched (4 instances), top wall T=1, "
             "1024 particles/cell (2^24 per instance) + 1024 per wall face; one step = sweep + macro + "
@@ -757,6 +800,7 @@ def run_ours(args):
                                           "cavity instances (Kn cycling) at 64 particles per cell and wall face for "
                                           "8 s"}
             oracle_steady = oracle_cavity_steady(64)
+            oracle_steady["other_configs_sweep"] = oracle_config_sweeps()
         # Roofline of the dominant kernel (the sweep): ALU issue bound. Algorithmic
         # lane-operations per event of a cell-by-cell walk (10 per crossing, 50 per
         # candidate, 200 per flight) x events / kernel time, against the device's FP32/INT32

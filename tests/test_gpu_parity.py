@@ -144,6 +144,41 @@ def test_correction_solve_meets_its_fp64_residual(orc, dim, n, uniform, rtol):
         assert it <= 6, it  # direct solve: a few refinement passes
 
 
+def test_correction_solve_batch_mixes_solvers(orc):
+    # One context whose instances take the three correction solvers in one launch: fast
+    # diagonalization with every operand in shared memory (axes up to 128), the register-tiled
+    # one (larger axes) and the multigrid PCG (varying kappa). Each instance's correction meets
+    # its FP64 residual against the oracle's operator.
+    rng = np.random.default_rng(64)
+    insts = [WL.random_instance(rng, 2, n, 1, (0.02, 0.4)) for n in [(40, 30), (140, 135), (20, 18)]]
+    for inst in insts[:2]:
+        inst.tau = np.full_like(inst.tau, rng.uniform(0.05, 0.3))
+    rtol = 1e-5
+    N = 4
+    s = gpu_solver(insts, [1.0], [1.0], N, N, precision=0, cg_rtol=rtol)
+    ps = [oracle_problem(inst, [1.0], [1.0], N, N, instance=k) for k, inst in enumerate(insts)]
+    Ts, Ths, Rs, dTs, thetas = [], [], [], [], []
+    for k, (inst, p) in enumerate(zip(insts, ps)):
+        T = rng.uniform(0, 1, inst.ncells)
+        r = orc.sweep(p, T, 0)
+        Th, _ = orc.macro(p, r.R, r.W)
+        _, dT = orc.newton(p, T, Th, r.R)
+        Ts.append(T)
+        Ths.append(Th)
+        Rs.append(r.R.ravel())
+        dTs.append(dT)
+        thetas.append(orc.newton_theta(p))
+    gT = cuda_T(np.concatenate(Ths))
+    s.newton_step(cuda_T(np.concatenate(Ts)), gT, cuda_T(np.concatenate(Rs)))
+    got = gT.cpu().numpy()
+    co = s.cell_off
+    for k, p in enumerate(ps):
+        x = (got[co[k]:co[k + 1]] - Ths[k]) / thetas[k]
+        rhs = orc.diffusion_apply(p, dTs[k] / thetas[k])
+        res = np.linalg.norm(rhs - orc.diffusion_apply(p, x)) / np.linalg.norm(rhs)
+        assert res <= rtol * 1.001, (k, res)
+
+
 @pytest.mark.parametrize("newton", [0, 1])
 def test_steady_fp64_matches_oracle(orc, newton):
     inst = WL.slab(40, 0.1, 1.0, -1.0).instances[0]
