@@ -630,9 +630,10 @@ __global__ void __launch_bounds__(STAGED_NT, 1) sweep_staged_kernel(SweepArgs A,
       // draws the next flight length and the particle goes on in the same direction ----
       int nitem = 0;  // cooperative tallies: face items of the lane's particle ended in this pass
       int nx3 = 0, ny3 = 0;  // 3D: x- and y-face items of the lane's particle ended in this pass
-      if (alive && !tally) {
-        bool ended = false, wall_exit = false, deferred = false;
-        const bool all_real = A.all_real[(long long)k * A.nb + band] != 0;
+      bool ended = false, wall_exit = false, deferred = false;
+      const bool walking = alive && !tally;
+      const bool all_real = A.all_real[(long long)k * A.nb + band] != 0;
+      if (walking) {
 #pragma unroll 1
         for (int it = 0; it < S.walk_k; ++it) {
           // a decision within rounding of the FP64 walk's defers the particle to the FP64 replay
@@ -694,6 +695,8 @@ __global__ void __launch_bounds__(STAGED_NT, 1) sweep_staged_kernel(SweepArgs A,
           f.D = __fadd_rn(f.D, ell);
           eD = fmaf(f.D, TIE_SUM, fmaf(ell, TIE_LOG_REL, eD + vtm * TIE_LOG_ABS));
         }
+      }
+      if (walking) {
         if (deferred) {
           defer_particle(S, pid, ADJ ? 0u : (((unsigned)kc << 1) | ((two && f.d0 < f.d1) ? 1u : 0u)));
           ended = false;

@@ -76,6 +76,32 @@ def test_staged_sweep_takes_the_fp64_decisions(orc, dim, n, tau, tally):
                 assert np.mean(d > 1e-6 * np.abs(ora).max()) < 0.02, key
 
 
+@pytest.mark.parametrize("walk_k", [1, 3, 16])
+@pytest.mark.parametrize("tally", [1, 2])
+def test_long_chains_across_passes_take_the_fp64_decisions(orc, walk_k, tally):
+    # A 3D box with a factor-100 tau jump: in the tau = 2 half about a hundred null candidates
+    # per real one, so most chains outlast a pass of walk_k candidates and go on in later passes
+    # (the path length, its bound and the stream carried across refills of other lanes); the
+    # counters equal the oracle's and R agrees to summation order, whatever walk_k is.
+    inst = WL.two_material_box(8)
+    T = np.random.default_rng(5).uniform(0.0, 1.0, inst.ncells)
+    N = 24
+    p = oracle_problem(inst, [1.0], [1.0], N, N, seed=11)
+    s = gpu_solver(inst, [1.0], [1.0], N, N, precision=1, tally=tally, seed=11, walk_k=walk_k, refill_lanes=8)
+    for epoch in (0, 3):
+        r = orc.sweep(p, T, epoch)
+        g = s.sweep(cuda_T(T), epoch)
+        assert g["counters"].cpu().numpy().tolist() == r.counters.astype(np.int64).tolist()
+        ok, err = normwise_close(g["R"].cpu().numpy(), r.R, 1e-10 if tally == 1 else 1e-9)
+        assert ok, ("R", err)
+        # W may differ where a null candidate lay within rounding of a face but every cell it may
+        # lie in rejects it (its W then sits in the FP32 cell): a few particle weights
+        Wg, Wo = g["W"].cpu().numpy().ravel(), np.asarray(r.W).ravel()
+        ok, err = normwise_close(Wg, Wo, 2e-3)
+        assert ok, ("W", err)
+        assert np.mean(np.abs(Wg - Wo) > 1e-6 * np.abs(Wo).max()) < 0.02
+
+
 @pytest.fixture(scope="module")
 def cavity_pair():
     # The benchmark batch (128^2, Kn 0.01 / 0.1 / 1 / 10, 1024 particles per cell and wall face)
