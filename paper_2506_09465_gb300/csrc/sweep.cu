@@ -229,6 +229,8 @@ __device__ __forceinline__ double shfl_d(double x, int src) {
 // an exit through the low wall of an untallied axis goes to that wall's face (one-group
 // instances) or to the group's exit tally GX (two-group). Emission needs nothing: the staged
 // sweep and its post-passes account for it.
+constexpr unsigned REPLAY_PER_WARP = 32;  // queue entries per warp and round
+
 template <int DIM>
 __global__ void __launch_bounds__(256) replay_kernel(SweepArgs A, StagedArgs S) {
   Counts cnt;
@@ -236,10 +238,17 @@ __global__ void __launch_bounds__(256) replay_kernel(SweepArgs A, StagedArgs S) 
   for (int k = 0; k < CNT_N; ++k) cnt.v[k] = 0;
   const int lane = threadIdx.x & 31;
   const unsigned n = min(*S.defer_n, S.defer_cap);
-  const unsigned stride = gridDim.x * blockDim.x;
+  // Warps are numbered block-major (warp j of block b is warp j G + b, G blocks), and warp a
+  // takes entries E a .. E a + E - 1 (E = REPLAY_PER_WARP; then E (a + W) .., W warps in the
+  // grid): the queue is
+  // short, and numbering the warps block by block put all its work on a few SMs (measured: the
+  // busiest SM active 3.6 times as long as the average); this way the first warps to get work
+  // are the first warp of every block.
+  const unsigned W = gridDim.x * blockDim.x >> 5;
+  const unsigned wid = (threadIdx.x >> 5) * gridDim.x + blockIdx.x;
   // all lanes of a warp run the same rounds (the face items are tallied by the whole warp)
-  for (unsigned i0 = blockIdx.x * blockDim.x + threadIdx.x - lane; i0 < n; i0 += stride) {
-    const unsigned i = i0 + lane;
+  for (unsigned i0 = REPLAY_PER_WARP * wid; i0 < n; i0 += REPLAY_PER_WARP * W) {
+    const unsigned i = lane < (int)REPLAY_PER_WARP ? i0 + lane : n;
     // the lane's particle, kept for the face items
     int kinst = 0, ex = 0, tall = 0;  // instance, exit axis (-1: real collision), tallied axes (bits)
     double w = 0.0;
