@@ -93,7 +93,11 @@ double word_to_uniform(uint32_t a) {
 
 // The uniform stream of one particle. Uniform j of the stream is word (j mod 4) of
 // Philox block (j / 4), block k having counter (k, particle, emitter, band<<24|epoch)
-// and key (lo32(seed), hi32(seed) ^ instance).
+// and key (lo32(seed), hi32(seed) ^ instance). A flight's draws: the emission takes
+// uniforms 0 .. j0 - 1 (j0 even); the first candidate's path uniform is made of bits the
+// emission leaves unused (first_path_uniform), its acceptance uniform is uniform j0;
+// uniform j0 + 1 is not used; candidate k >= 2 takes uniforms j0 + 2k - 2 (path) and
+// j0 + 2k - 1 (acceptance).
 struct Stream {
   uint32_t ctr[4];
   uint32_t key[2];
@@ -124,6 +128,16 @@ struct Stream {
     return word_to_uniform(words[word]);
   }
   void skip_to(long long j) { next = j; }
+  // The first candidate's path uniform: 23 bits that the emission leaves unused in block 0,
+  // the low 9 bits of words 0 and 1 and bits 4..8 of word 2 (uniforms take the top 23 bits),
+  // m = (w0 mod 2^9) 2^14 + (w1 mod 2^9) 2^5 + floor((w2 mod 2^9) / 2^4), u = (2m + 1) / 2^24.
+  double first_path_uniform() const {
+    uint32_t c[4] = {0u, ctr[1], ctr[2], ctr[3]};
+    uint32_t w[4];
+    philox4x32_10(c, key, w);
+    const uint32_t m = ((w[0] & 511u) << 14) | ((w[1] & 511u) << 5) | ((w[2] & 511u) >> 4);
+    return (double)(2u * m + 1u) * (1.0 / 16777216.0);
+  }
 };
 
 // ---------------------------------------------------------------------------
@@ -214,7 +228,8 @@ double trace_particle(const OrcProblem& p, const Geo& g, int b, double tau_maj,
   const long long nc = g.ncells;
   double speed = p.v[b];
   long long steps = 0;
-  double d = -std::log(st.uniform()) * speed * tau_maj;  // path to the first candidate
+  double d = -std::log(st.first_path_uniform()) * speed * tau_maj;  // path to the first candidate
+  bool first = true;
   for (;;) {
     // Distance along s to the next face on each axis.
     double tmin = INFINITY;
@@ -239,6 +254,10 @@ double trace_particle(const OrcProblem& p, const Geo& g, int b, double tau_maj,
         t->W[(long long)b * nc + c] += w * tau_maj;
       }
       double u_acc = st.uniform();
+      if (first) {  // the first candidate's acceptance is uniform j0; j0 + 1 is not used
+        st.skip_to(st.next + 1);
+        first = false;
+      }
       if (u_acc < tau_maj / tau_here) {
         if (t) {
           t->counters[2] += 1;
@@ -722,7 +741,7 @@ int orc_emit(const OrcProblem* p, int kind, int band, long long emitter, uint32_
                         x_out[3 * k + a] = x[a];
                         s_out[3 * k + a] = s[a];
                       }
-                      d_out[k] = -std::log(st.uniform()) * p->v[b] * tmaj[b];
+                      d_out[k] = -std::log(st.first_path_uniform()) * p->v[b] * tmaj[b];
                       ++k;
                     });
   return (int)k;

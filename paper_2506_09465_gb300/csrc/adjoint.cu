@@ -81,7 +81,7 @@ __device__ __forceinline__ void adjoint_particle(const SweepArgs& A, long long p
   const long long bcbase = in.bc_off + (long long)b * in.ncells;
   const int stride[3] = {1, in.n[0], in.n[0] * in.n[1]};
   uint32_t ua, ub;
-  st.next_pair(ua, ub);
+  st.first_pair(ua, ub);
   wk.D = adj_path<Real>(ua, vb, tm, vtm_f);
   long long steps = 0;
   double val = 0.0;

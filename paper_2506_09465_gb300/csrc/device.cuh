@@ -49,19 +49,31 @@ __device__ __forceinline__ float word_uniform<float>(uint32_t a) {
 
 // The uniform stream of one particle: uniform j is word (j mod 4) of block j / 4,
 // block k = Philox(counter (k, particle, emitter, band<<24 | epoch), key). Emission
-// consumes an even number of uniforms, so every later (path, accept) pair of a
-// candidate lies in one block: one Philox call serves two candidates.
+// consumes j0 uniforms (j0 even). The first candidate's path word is made of bits the
+// emission leaves unused in block 0 (first), its acceptance word is uniform j0; uniform
+// j0 + 1 is not used, and candidate k >= 2 takes the pair (j0 + 2k - 2, j0 + 2k - 1), so
+// every later pair lies in one block: one Philox call serves two candidates, and a flight
+// whose first candidate needs no acceptance draw needs block 0 alone (2D: thermal and wall
+// emission both).
 struct Stream {
   uint4 ctr;
   uint2 key;
   uint4 buf;
-  uint32_t j;  // index of the next uniform
+  uint32_t j;      // index of the next uniform
+  uint32_t first;  // the first candidate's path word (init)
+
+  // 23 bits of block 0 that no uniform uses (uniforms take the top 23 bits of a word): the
+  // low 9 bits of words x and y and bits 4..8 of word z, placed where word_uniform reads.
+  __device__ __forceinline__ static uint32_t spare_word(uint4 b) {
+    return (((b.x & 511u) << 14) | ((b.y & 511u) << 5) | ((b.z & 511u) >> 4)) << 9;
+  }
 
   __device__ __forceinline__ void init(unsigned long long seed, uint32_t inst_id, uint32_t band,
                                        uint32_t epoch, uint32_t emitter, uint32_t particle) {
     key = make_uint2((uint32_t)seed, (uint32_t)(seed >> 32) ^ inst_id);
     ctr = make_uint4(0u, particle, emitter, (band << 24) | (epoch & 0xFFFFFFu));
     buf = philox4x32_10(ctr, key);  // block 0 holds the first emission draws
+    first = spare_word(buf);
     j = 0;
   }
   // The same stream with no block computed yet (the first next_pair or load_block does it).
@@ -78,6 +90,21 @@ struct Stream {
   }
   __device__ __forceinline__ uint32_t word(uint32_t k) const {
     return k == 0 ? buf.x : (k == 1 ? buf.y : (k == 2 ? buf.z : buf.w));
+  }
+  // Uniform j (even) of the stream: word x of block j / 4, loaded here, or word z of the
+  // block already loaded.
+  __device__ __forceinline__ uint32_t even_word() {
+    if ((j & 3u) == 0u) {
+      load_block(j >> 2);
+      return buf.x;
+    }
+    return buf.z;
+  }
+  // After the emission (j = j0): the first candidate's path and acceptance words.
+  __device__ __forceinline__ void first_pair(uint32_t& a, uint32_t& b) {
+    a = first;
+    b = even_word();
+    j += 2;
   }
   // Next (path, accept) pair; j is even.
   __device__ __forceinline__ void next_pair(uint32_t& a, uint32_t& b) {

@@ -66,7 +66,7 @@ __device__ __forceinline__ int replay_candidates(const SweepArgs& A, const InstD
   const double vb = A.v[b];
   const long long bcbase = in.bc_off + (long long)b * in.ncells;
   uint32_t ua, ub;
-  st.next_pair(ua, ub);
+  st.first_pair(ua, ub);
   double D = path64(ua, vb, tm);
   for (long long k = 0;; ++k) {
     if (k >= A.budget) return -1;

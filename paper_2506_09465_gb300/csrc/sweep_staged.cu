@@ -448,9 +448,12 @@ __device__ __forceinline__ bool staged_emit(const SweepArgs& A, const StagedArgs
       atomicAdd(&S.EY[in.bface_off + in.wface_off[wl] + e], (wl & 1) ? -w : w);
     }
   }
-  uint32_t ua;
-  st.next_pair(ua, ub);
-  f.D = __fmul_rn(-__logf(word_uniform<float>(ua)), A.vtm32[(long long)k * A.nb + b]);
+  // the first candidate: its path word from block 0's unused bits; its acceptance word only
+  // where some cell of the band may reject (else every candidate is real and the particle ends
+  // at its first candidate, so no later draw is taken)
+  ub = A.all_real[(long long)k * A.nb + b] ? 0u : st.even_word();
+  st.j += 2;
+  f.D = __fmul_rn(-__logf(word_uniform<float>(st.first)), A.vtm32[(long long)k * A.nb + b]);
   return true;
 }
 

@@ -54,6 +54,13 @@ def test_thermal_sampler_moments(orc):
     # Path to the first candidate: exponential with mean v tau_maj = 0.5 (Sec. 3.1).
     assert abs(d.mean() - 0.5) < 5 * 0.5 / np.sqrt(N)
     assert abs(np.median(d) - 0.5 * np.log(2.0)) < 0.02
+    # Its uniform comes from bits of the emission's Philox block that the position and
+    # direction uniforms leave unused: uniform on (0, 1) and uncorrelated with them.
+    u = np.exp(-d / 0.5)
+    counts, _ = np.histogram(u, bins=32, range=(0.0, 1.0))
+    assert ((counts - N / 32) ** 2 / (N / 32)).sum() < 70.0  # 31 dof: p ~ 1e-4
+    for v in (frac[:, 0], frac[:, 1], frac[:, 2], s[:, 0]):
+        assert abs(np.corrcoef(u, v)[0, 1]) < 5 / np.sqrt(N)
 
 
 def test_wall_sampler_cosine_law(orc):
