@@ -788,7 +788,7 @@ iugkp_status iugkp_create_batch(int n, const iugkp_grid* g, const double* const*
   if (c->dim == 2) {
     if ((s = dalloc(c, &c->d_DY, cell_off)) != IUGKP_OK) return bail(s);
     if ((s = dalloc(c, &c->d_EY, (size_t)c->total_bfaces)) != IUGKP_OK) return bail(s);
-    if ((s = dalloc(c, &c->d_GX, (size_t)c->total_bfaces)) != IUGKP_OK) return bail(s);
+    if ((s = dalloc(c, &c->d_GX, (size_t)GX_COPIES * c->total_bfaces)) != IUGKP_OK) return bail(s);
     if ((s = dalloc(c, &c->d_Fd, face_off)) != IUGKP_OK) return bail(s);
   }
   if ((s = dalloc(c, &c->d_wall, c->total_walls)) != IUGKP_OK) return bail(s);

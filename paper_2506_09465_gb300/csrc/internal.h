@@ -106,7 +106,7 @@ struct Ctx {
   // two-group face tallies of the staged sweep (2D): group balances and derived faces
   double* d_DY = nullptr;        // [cells]
   double* d_EY = nullptr;        // [total_bfaces]
-  double* d_GX = nullptr;        // [total_bfaces]
+  double* d_GX = nullptr;        // [GX_COPIES * total_bfaces]
   double* d_Fd = nullptr;        // [total_faces] faces derived from the group balances
   bool any_two_group = false;    // some instance of the context uses the two-group tallies
   bool all_two_group = false;    // ... every instance does (no face follows from a column walk)

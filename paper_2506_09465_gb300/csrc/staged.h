@@ -20,6 +20,13 @@ constexpr double WIN_SCALE = 0x1p26;
 constexpr double WIN_CARRY = 0x1p6;             // 2^32 units in multiples of w_max
 constexpr unsigned WIN_BIAS = 0x80000000u;
 
+// Copies of the two-group exit tally GX (one per block, by block index modulo the count),
+// summed when the untallied faces are derived. Exits through one wall pile onto a few hundred
+// faces (a single 128 x 128 instance at Kn 10 sends ~4e6 exits to 256 of them); FP64
+// atomics to one address serialise at its L2 slice, so one copy made the sweep's time
+// depend on which slices those lines landed in.
+constexpr int GX_COPIES = 16;
+
 struct StagedArgs {
   int n_inst;
   unsigned long long* inst_next;  // [n_inst] next unclaimed forward particle of each instance
@@ -47,8 +54,9 @@ struct StagedArgs {
   double* DY;                     // [total_cells] y-group: absorbed minus emitted power per cell
   double* EY;                     // [total_bfaces] y-group wall emission per boundary face (signed
                                   // flux: + on the low walls, - on the high walls)
-  double* GX;                     // [total_bfaces] exits of the x-group through the low y-wall and
-                                  // of the y-group through the low x-wall (signed flux)
+  double* GX;                     // [GX_COPIES][total_bfaces] exits of the x-group through the low
+                                  // y-wall and of the y-group through the low x-wall (signed flux)
+  long long gx_stride;            // total_bfaces: entries per copy of GX
   // Particles whose FP32 walk lies within rounding of a decision of the FP64 walk are left
   // untallied and replayed by the FP64 walk after the sweep (replay_kernel): entry
   // {forward index, (candidates already tallied << 1) | y-group}.
@@ -56,6 +64,12 @@ struct StagedArgs {
   unsigned* defer_n;              // entries pushed by this sweep (beyond defer_cap: overflow)
   unsigned defer_cap;
   int* err;                       // device error word (ERR_DEFER on overflow)
+#ifdef __CUDACC__
+  // this block's copy of GX
+  __device__ __forceinline__ double* gx() const {
+    return GX + (long long)(blockIdx.x % (unsigned)GX_COPIES) * gx_stride;
+  }
+#endif
 };
 
 }  // namespace iugkp

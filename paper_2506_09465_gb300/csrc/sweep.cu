@@ -312,7 +312,7 @@ __global__ void __launch_bounds__(256) replay_kernel(SweepArgs A, StagedArgs S) 
               for (int a = 0; a < DIM; ++a) cc[a] = wk.idx[a] + wk.step[a] * c[a];
               if (two) {
                 const int j = sg.ex == 1 ? cc[0] : cc[1];  // the low y-wall's column or the low x-wall's row
-                atomicAdd(&S.GX[in.bface_off + in.wface_off[sg.ex == 1 ? 2 : 0] + j], -w);
+                atomicAdd(&S.gx()[in.bface_off + in.wface_off[sg.ex == 1 ? 2 : 0] + j], -w);
               } else {
                 atomicAdd(&A.F[in.face_off + face_at(in, sg.ex, 0, cc)], -w);
               }

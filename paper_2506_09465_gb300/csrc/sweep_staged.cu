@@ -760,7 +760,7 @@ __global__ void __launch_bounds__(STAGED_NT, 1) sweep_staged_kernel(SweepArgs A,
                 // exit through the low y-wall: the one face normal to y this group tallies
                 if (ex == 1 && f.s1 < 0) {
                   const int col = f.i0 + f.s0 * c0;
-                  if (two) atomicAdd(&S.GX[in.bface_off + in.wface_off[2] + col], -w);
+                  if (two) atomicAdd(&S.gx()[in.bface_off + in.wface_off[2] + col], -w);
                   else if (K32) tally_k32(&S.F32[face_off + fax1 + col], -w);
                   else atomicAdd(&A.F[face_off + fax1 + col], -w);
                 }
@@ -774,7 +774,7 @@ __global__ void __launch_bounds__(STAGED_NT, 1) sweep_staged_kernel(SweepArgs A,
                 sq = f.s1 * sy_xf;
               } else {
                 // exit through the low x-wall: the one face normal to x this group tallies
-                if (ex == 0 && f.s0 < 0) atomicAdd(&S.GX[in.bface_off + in.wface_off[0] + (f.i1 + f.s1 * c1)], -w);
+                if (ex == 0 && f.s0 < 0) atomicAdd(&S.gx()[in.bface_off + in.wface_off[0] + (f.i1 + f.s1 * c1)], -w);
                 kend = c1 + (ex == 1 ? 1 : 0);
                 u0 = __fdividef(f.t1 - f.t0, f.d0);
                 r = __fdividef(f.d1, f.d0);
@@ -1211,7 +1211,7 @@ __global__ void __launch_bounds__(STAGED_NT, 1) sweep_sync_kernel(SweepArgs A, S
             if (ex == 1 - axp && (yg ? f.s0 : f.s1) < 0) {  // exit through the low q-wall
               if (two) {
                 const int j = yg ? in.wface_off[0] + f.i1 + f.s1 * c1 : in.wface_off[2] + f.i0 + f.s0 * c0;
-                atomicAdd(&S.GX[in.bface_off + j], -w);
+                atomicAdd(&S.gx()[in.bface_off + j], -w);
               } else {
                 const int col = f.i0 + f.s0 * c0;
                 if (K32) tally_k32(&S.F32[face_off + fax1 + col], -w);
@@ -1583,7 +1583,7 @@ __global__ void __launch_bounds__(256) derive_two_group_kernel(const InstDesc* i
                                                                const double* Vm, const double* R,
                                                                const double* wall_unit, const double* wallTf,
                                                                const double* DY, const double* EY, const double* GX,
-                                                               const double* F, double* Fd) {
+                                                               long long gx_stride, const double* F, double* Fd) {
   const int k = blockIdx.y;
   const InstDesc& in = inst[k];
   if (!two_group(in, window, k)) return;
@@ -1594,7 +1594,12 @@ __global__ void __launch_bounds__(256) derive_two_group_kernel(const InstDesc* i
   double* Fo = Fd + in.face_off;
   const long long fax1 = in.fax_off[1];
   const double* ey = EY + in.bface_off;
-  const double* gx = GX + in.bface_off;
+  // the exit tally of boundary face j, summed over the copies of GX
+  auto gx = [&](long long j) {
+    double t = 0.0;
+    for (int r = 0; r < GX_COPIES; ++r) t += GX[r * gx_stride + in.bface_off + j];
+    return t;
+  };
   const double* tf = wallTf + in.bface_off;
   const double* dy = DY + in.cell_off;
   // signed flux of the whole emission of wall wl through its face j
@@ -1604,7 +1609,7 @@ __global__ void __launch_bounds__(256) derive_two_group_kernel(const InstDesc* i
   };
   if (line < n0) {
     const int i = line;
-    double acc = gx[in.wface_off[2] + i] + etot(2, i) - ey[in.wface_off[2] + i];
+    double acc = gx(in.wface_off[2] + i) + etot(2, i) - ey[in.wface_off[2] + i];
     if (lane == 0) Fo[fax1 + i] = acc;
     for (int j0 = 0; j0 < n1; j0 += 32) {
       const int j = j0 + lane;
@@ -1631,7 +1636,7 @@ __global__ void __launch_bounds__(256) derive_two_group_kernel(const InstDesc* i
     }
   } else {
     const int j = line - n0;
-    double acc = gx[in.wface_off[0] + j] + ey[in.wface_off[0] + j];
+    double acc = gx(in.wface_off[0] + j) + ey[in.wface_off[0] + j];
     if (lane == 0) Fo[(long long)(n0 + 1) * j] = acc;
     for (int ib = 0; ib < n0; ib += 32) {
       const int i = ib + lane;
@@ -1762,10 +1767,11 @@ cudaError_t launch_sweep_staged(const Ctx* c, const SweepArgs& a, cudaStream_t s
   S.DY = c->d_DY;
   S.EY = c->d_EY;
   S.GX = c->d_GX;
+  S.gx_stride = c->total_bfaces;
   if (two) {
     if ((e = cudaMemsetAsync(c->d_DY, 0, (size_t)c->total_cells * sizeof(double), s)) != cudaSuccess) return e;
     if ((e = cudaMemsetAsync(c->d_EY, 0, (size_t)c->total_bfaces * sizeof(double), s)) != cudaSuccess) return e;
-    if ((e = cudaMemsetAsync(c->d_GX, 0, (size_t)c->total_bfaces * sizeof(double), s)) != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(c->d_GX, 0, (size_t)GX_COPIES * c->total_bfaces * sizeof(double), s)) != cudaSuccess) return e;
   }
   const bool k32 = c->opt.tally == IUGKP_TALLY_STAGED_K32;
   // pass-synchronous schedule: refill only when all 32 lanes are idle (the default where it
@@ -1843,7 +1849,7 @@ cudaError_t launch_sweep_staged(const Ctx* c, const SweepArgs& a, cudaStream_t s
     }
     derive_two_group_kernel<<<dim3((unsigned)((lines + 7) / 8), (unsigned)c->n_inst), 256, 0, s>>>(
         c->d_inst, c->nb, c->d_window, a.T, a.srcshift, c->d_Vm, a.R, c->d_wall_unit, c->d_wallTf, c->d_DY, c->d_EY,
-        c->d_GX, a.F, c->d_Fd);
+        c->d_GX, c->total_bfaces, a.F, c->d_Fd);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     assemble_two_group_kernel<<<dim3((unsigned)std::min<long long>((faces + 255) / 256, 1024), (unsigned)c->n_inst), 256,
                                 0, s>>>(c->d_inst, c->d_window, c->d_wall_unit, c->d_wallTf, c->d_EY, c->d_Fd, a.F);
@@ -1884,6 +1890,7 @@ cudaError_t launch_adjoint_staged(const Ctx* c, const SweepArgs& a, cudaStream_t
   if ((e = cudaMemsetAsync(c->d_defer_n, 0, sizeof(unsigned), s)) != cudaSuccess) return e;
   S.R32 = S.W32 = S.F32 = nullptr;
   S.DY = S.EY = S.GX = nullptr;
+  S.gx_stride = 0;
   const int blocks = c->sm_count * c->adj_blocks_per_sm;
   if (c->dim == 2 && (c->opt.refill_lanes == 0 || c->opt.refill_lanes == 32)) {
     // pass-synchronous re-trace (refill only when all 32 lanes are idle)
