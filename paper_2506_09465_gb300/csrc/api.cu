@@ -294,9 +294,14 @@ iugkp_status rebuild_forward_groups(Ctx* c) {
   iugkp_status s = upload(c, &c->d_groups_fwd, c->h_groups_fwd);
   if (s != IUGKP_OK) return s;
   {
-    // w_max pre-pass: one block per WMAX_CHUNK emitters of each group (at least one)
+    // w_max pre-pass: each group's blocks in proportion to its emitters, about two blocks per
+    // SM in all, at least WMAX_MIN_CHUNK emitters per block
+    long long total = 0;
+    for (const Group& g : c->h_groups_fwd) total += g.n_emitters;
+    const long long nblk = 2 * (long long)std::max(1, c->sm_count);
+    const long long chunk = std::max<long long>(WMAX_MIN_CHUNK, (total + nblk - 1) / nblk);
     std::vector<int> bpre(1, 0);
-    for (const Group& g : c->h_groups_fwd) bpre.push_back(bpre.back() + (int)((g.n_emitters + WMAX_CHUNK - 1) / WMAX_CHUNK));
+    for (const Group& g : c->h_groups_fwd) bpre.push_back(bpre.back() + (int)((g.n_emitters + chunk - 1) / chunk));
     c->wmax_blocks = bpre.back();
     if (c->d_wmax_bpre) cudaFree(c->d_wmax_bpre);
     c->d_wmax_bpre = nullptr;

@@ -17,8 +17,9 @@ namespace iugkp {
 // (by lane), summed when the face's power is shared out: a wall face receives far more
 // absorptions per iteration than a cell receives real collisions, and same-address atomics
 // serialise at the L2.
-// Emitters per block of the w_max pre-pass of the staged sweep (16 per thread).
-constexpr int WMAX_CHUNK = 4096;
+// Fewest emitters per block of the w_max pre-pass of the staged sweep (4 per thread); above
+// that the pass takes about two blocks per SM.
+constexpr int WMAX_MIN_CHUNK = 1024;
 
 constexpr int PERS_FACE_REPLICAS = 32;
 
@@ -93,7 +94,7 @@ struct Ctx {
   float* d_ratio_nb32 = nullptr; // [nb * cells] largest FP32 ratio over each cell's neighbourhood
   int* d_perm = nullptr;         // emitter visiting orders of the groups (Group::perm_off)
   int* d_wmax_bpre = nullptr;    // [forward groups + 1] first block of each group in the w_max pre-pass
-                                 // (one block per WMAX_CHUNK emitters)
+                                 // (in proportion to its emitters)
   int wmax_blocks = 0;           // blocks of that pass
   int* d_all_real = nullptr;     // [inst * nb] tau = tau_maj in every cell of the band
   bool all_real_all = false;     // ... in every instance and band

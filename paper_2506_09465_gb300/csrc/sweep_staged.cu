@@ -218,8 +218,8 @@ __device__ __forceinline__ int candidate_outcome(const SweepArgs& A, long long b
 
 // The largest |weight| of each forward group's emitters, max-reduced into its instance's slot
 // (non-negative doubles order like their bit patterns). Group g has blocks [bpre[g],
-// bpre[g + 1]) of the grid, about one per WMAX_CHUNK emitters, so the FP64 weight arithmetic
-// is spread over the SMs in proportion to the work.
+// bpre[g + 1]) of the grid, in proportion to its emitters (about two blocks per SM in all), so
+// the FP64 weight arithmetic is spread over the SMs in proportion to the work.
 __global__ void group_wmax_kernel(SweepArgs A, const int* bpre, unsigned long long* wmax_bits) {
   __shared__ double sh[32];
   int gi = 0;
@@ -1234,11 +1234,14 @@ __global__ void __launch_bounds__(STAGED_NT, 1) sweep_sync_kernel(SweepArgs A, S
       }
       rbeg += take;
       // ---- the pass's face items: each lane's list is cut into segments of SEG items, the
-      // segments are numbered in lane order and dealt to the lanes round-robin; a lane finds
-      // its segment's list by a binary search of the segment starts and runs SEG steps with the
-      // list's parameters (no per-item list check). Against contiguous chunks of the pass's
-      // items (a list change inside a chunk at a different step on every lane): 2.46 -> 2.40
-      // ms per bench-batch sweep (Kn 10: -6 %, Kn 0.01, short lists: +3 %) ----
+      // segments are numbered in lane order and dealt to the lanes round-robin, 32 to a
+      // round; a lane runs SEG steps of its segment with its list's parameters (no per-item
+      // list check). Against contiguous chunks of the pass's items (a list change inside a
+      // chunk at a different step on every lane): 2.46 -> 2.40 ms per bench-batch sweep (Kn
+      // 10: -6 %, Kn 0.01, short lists: +3 %). The non-empty lists are stored in lane order
+      // without gaps; segment g belongs to list (number of lists starting at or before g) - 1,
+      // counted from a ballot of the lists starting before the round and an OR-reduction of
+      // the start bits within it (no search through the starts in shared memory). ----
       constexpr int SEG = 8;
       const int nseg = (nitem + SEG - 1) / SEG;
       int incl = nseg;
@@ -1249,18 +1252,22 @@ __global__ void __launch_bounds__(STAGED_NT, 1) sweep_sync_kernel(SweepArgs A, S
       }
       const int total = __shfl_sync(0xffffffffu, incl, 31);
       if (total > 0) {
-        lst[lane] = incl - nseg;
-        par[2 * lane] = pa_own;
-        par[2 * lane + 1] = make_int4(pb_own.x, pb_own.y, pb_own.z, nitem);
-        if (lane == 0) lst[32] = total;
+        const int first = incl - nseg;  // this lane's first segment
+        const unsigned nonempty = __ballot_sync(0xffffffffu, nseg > 0);
+        if (nseg > 0) {
+          const int pos = __popc(nonempty & ((1u << lane) - 1u));
+          lst[pos] = first;
+          par[2 * pos] = pa_own;
+          par[2 * pos + 1] = make_int4(pb_own.x, pb_own.y, pb_own.z, nitem);
+        }
         __syncwarp();
-        for (int g = lane; g < total; g += 32) {
-          // the list of segment g: the last start at or before it (a start followed by a
-          // larger one, so the list is not empty)
-          int l = 0;
-#pragma unroll
-          for (int st = 16; st > 0; st >>= 1)
-            if (lst[l + st] <= g) l += st;
+        for (int r0 = 0; r0 < total; r0 += 32) {
+          const bool starts_here = nseg > 0 && first >= r0 && first < r0 + 32;
+          const unsigned bits = __reduce_or_sync(0xffffffffu, starts_here ? 1u << (first - r0) : 0u);
+          const int before = __popc(__ballot_sync(0xffffffffu, nseg > 0 && first < r0));
+          const int g = r0 + lane;
+          if (g >= total) continue;
+          const int l = before + __popc(bits & (0xffffffffu >> (31 - lane))) - 1;
           const int4 pa = par[2 * l], pb = par[2 * l + 1];
           const int kl0 = (g - lst[l]) * SEG;
           const int kn = min(SEG, pb.w - kl0);
