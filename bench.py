@@ -26,8 +26,8 @@ METRIC = "cell-crossings/s and time-to-steady (res 1e-8) vs plain FP64 sweep, sa
 KNS = (0.01, 0.1, 1.0, 10.0)
 # From one ncu capture of the current sweep kernel on this workload (the command and the
 # figures are in profiles/sweep_cavity128_4kn.md); retaken whenever the kernel changes.
-SWEEP_DRAM_BYTES = 3.25e6  # dram__bytes_read.sum + dram__bytes_write.sum per launch
-SWEEP_ISSUE_UTIL = 0.780   # smsp__issue_active of the same launch
+SWEEP_DRAM_BYTES = 2.81e6  # dram__bytes_read.sum + dram__bytes_write.sum per launch
+SWEEP_ISSUE_UTIL = 0.792   # smsp__issue_active of the same launch
 NGRID = 128
 NPART = 1024
 
