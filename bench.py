@@ -27,7 +27,7 @@ KNS = (0.01, 0.1, 1.0, 10.0)
 # From one ncu capture of the current sweep kernel on this workload (the command and the
 # figures are in profiles/sweep_cavity128_4kn.md); retaken whenever the kernel changes.
 SWEEP_DRAM_BYTES = 2.81e6  # dram__bytes_read.sum + dram__bytes_write.sum per launch
-SWEEP_ISSUE_UTIL = 0.792   # smsp__issue_active of the same launch
+SWEEP_ISSUE_UTIL = 0.808   # smsp__issue_active of the same launch
 NGRID = 128
 NPART = 1024
 
