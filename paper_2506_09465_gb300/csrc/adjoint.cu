@@ -147,8 +147,8 @@ template <int DIM>
 __global__ void __launch_bounds__(128) adjoint_replay_kernel(SweepArgs A, const uint2* defer, const unsigned* defer_n,
                                                              unsigned defer_cap) {
   const unsigned n = min(*defer_n, defer_cap);
-  // warps numbered block-major, 32 entries each (see replay_kernel): the short queue's work
-  // is spread over the SMs
+  // warp j of every block numbered before warp j + 1 of any, 32 entries each (as in
+  // replay_kernel): the short queue's work is spread over the SMs
   const unsigned wid = (threadIdx.x >> 5) * gridDim.x + blockIdx.x;
   for (unsigned i = 32u * wid + (threadIdx.x & 31); i < n; i += gridDim.x * blockDim.x) {
     const unsigned pid = defer[i].x;

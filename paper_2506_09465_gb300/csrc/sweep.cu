@@ -238,12 +238,12 @@ __global__ void __launch_bounds__(256) replay_kernel(SweepArgs A, StagedArgs S) 
   for (int k = 0; k < CNT_N; ++k) cnt.v[k] = 0;
   const int lane = threadIdx.x & 31;
   const unsigned n = min(*S.defer_n, S.defer_cap);
-  // Warps are numbered block-major (warp j of block b is warp j G + b, G blocks), and warp a
-  // takes entries E a .. E a + E - 1 (E = REPLAY_PER_WARP; then E (a + W) .., W warps in the
-  // grid): the queue is
-  // short, and numbering the warps block by block put all its work on a few SMs (measured: the
-  // busiest SM active 3.6 times as long as the average); this way the first warps to get work
-  // are the first warp of every block.
+  // Warp j of block b is warp a = j G + b (G blocks: warp j of every block comes before warp
+  // j + 1 of any), and warp a takes entries E a .. E a + E - 1 (E = REPLAY_PER_WARP; then E (a
+  // + W) .., W warps in the grid). The queue is short: numbered b 8 + j, the warps that got
+  // work were all in the first few blocks, on a few SMs (measured: the busiest SM active 3.6
+  // times as long as the average); this way the first warps to get work are the first warp of
+  // every block.
   const unsigned W = gridDim.x * blockDim.x >> 5;
   const unsigned wid = (threadIdx.x >> 5) * gridDim.x + blockIdx.x;
   // all lanes of a warp run the same rounds (the face items are tallied by the whole warp)
