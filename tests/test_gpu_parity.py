@@ -242,20 +242,27 @@ def test_adjoint_matches_dense_transpose(orc):
         assert ok, err
 
 
-def test_full_size_cavity_sampled_emitters(orc):
-    # The 128 x 128 cavity at the bench's particle count and launch configuration, with only
-    # a few cells hot (so the oracle traces only their particles): FP64 tallies agree.
-    inst = WL.cavity(128, 1.0).instances[0]
+@pytest.mark.parametrize("fast,kn", [(False, 1.0), (True, 0.01), (True, 1.0), (True, 10.0)])
+def test_full_size_cavity_sampled_emitters(orc, fast, kn):
+    # The 128 x 128 cavity at the bench's particle count, with only a few cells hot (so the
+    # oracle traces only their particles). Plain FP64 path: every tally agrees. Fast path in
+    # the bench's launch configuration (pass-synchronous kernel, two-group face tallies in the
+    # shared-memory window, FP64 replay of deferred flights): counters equal, R and W to
+    # summation order, faces and walls within the window's fixed-point rounding (each
+    # particle's weight rounded to 2^-26 of the largest).
+    inst = WL.cavity(128, kn).instances[0]
     inst.wall_T = np.zeros(4)
     T = np.zeros(inst.ncells)
     T[[0, 5000, 8256, 16383]] = [1.0, 0.5, -0.25, 2.0]
     N = 1024
     p = oracle_problem(inst, [1.0], [1.0], N, N, seed=0)
     r = orc.sweep(p, T, 0)
-    s = gpu_solver(inst, [1.0], [1.0], N, N, precision=0, tally=0, schedule=0, seed=0)
+    opt = {} if fast else dict(precision=0, tally=0, schedule=0)
+    s = gpu_solver(inst, [1.0], [1.0], N, N, seed=0, **opt)
     g = s.sweep(cuda_T(T), 0)
+    assert g["counters"].cpu().numpy().tolist() == r.counters.astype(np.int64).tolist()
     for key, ora in (("R", r.R), ("W", r.W), ("F", r.F), ("wall", r.wall)):
-        ok, err = normwise_close(g[key].cpu().numpy(), ora, RTOL64)
+        ok, err = normwise_close(g[key].cpu().numpy(), ora, 1e-6 if fast and key in ("F", "wall") else RTOL64)
         assert ok, (key, err)
 
 
