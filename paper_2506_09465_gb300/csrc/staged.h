@@ -4,6 +4,7 @@
 namespace iugkp {
 
 constexpr int STAGED_NT = 1024;                 // threads per persistent block
+constexpr int WALK_MIN_LANES = 8;               // 3D per-lane walk: fewest lanes worth a step
 
 // 3D face tallies: the warp tallies the items of the particles that ended together; per warp a
 // table of 64 item lists (the x- and y-faces of each lane's particle, 3 int4 of parameters

@@ -630,7 +630,10 @@ __global__ void __launch_bounds__(STAGED_NT, 1) sweep_staged_kernel(SweepArgs A,
       // ---- candidates (Sec. 3.2): up to walk_k per lane. The candidate lies at path length D
       // of the straight segment; its cell follows from the faces before D on each axis.
       // W tally, then acceptance with probability tau_maj / tau(x); a rejected candidate
-      // draws the next flight length and the particle goes on in the same direction ----
+      // draws the next flight length and the particle goes on in the same direction. In 3D
+      // the walk stops early once fewer than WALK_MIN_LANES lanes are still walking: the lanes
+      // whose particles ended get their items tallied and are refilled sooner, and the others go
+      // on in the next pass (16-box batch at refill 4, walk_k 8: 75.9 -> 74.6 ms) ----
       int nitem = 0;  // cooperative tallies: face items of the lane's particle ended in this pass
       int nx3 = 0, ny3 = 0;  // 3D: x- and y-face items of the lane's particle ended in this pass
       bool ended = false, wall_exit = false, deferred = false;
@@ -639,6 +642,7 @@ __global__ void __launch_bounds__(STAGED_NT, 1) sweep_staged_kernel(SweepArgs A,
       if (walking) {
 #pragma unroll 1
         for (int it = 0; it < S.walk_k; ++it) {
+          if (DIM == 3 && it > 0 && __popc(__activemask()) < WALK_MIN_LANES) break;
           // a decision within rounding of the FP64 walk's defers the particle to the FP64 replay
           const float base = fmaf(TIE_REL, f.D, eD);
           if (f.D - f.tex > base) {  // the segment reaches a wall first: absorbed there
